@@ -1,0 +1,356 @@
+"""Benchmark of the SVT track-fitting chain on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload scaled] [--mode persistent|plain] [--no-cpu]
+
+One step = one batch of the workload (default: 3000 events x 64 roads, 1-4
+hits per layer, 18.77M combinations) through the whole chain: unpack,
+combine, fit, chi-square cut, hit-warrior, ordered output.
+
+  value  track fits (combinations) per second with the words resident in
+         HBM; each step is timed with CUDA events on its stream, and a 256 MB
+         buffer is written between steps to flush L2 (the input is 11.9 MB).
+  e2e    the same metric through the public C ABI from pinned host memory:
+         per step H2D of the words, svt_unpack, svt_fit_events, svt_get_tracks
+         (D2H of the status block and the surviving tracks), host wall clock;
+         p50 / p99 of the per-step latency.
+  --impl reference  the CPU oracle (test infrastructure) timed on the host
+         cores on a bounded sample of the same workload.
+
+Multi-GPU: the chain shards by events with no exchange, so N ranks run
+independent replicas (weak scaling); value = all ranks' fits / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Integer pipe of one GB300 SM: 4 sub-partitions x 16 INT32 lanes
+INT32_LANES_PER_SM = 64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="svt", choices=["svt", "reference"])
+    ap.add_argument("--workload", default="scaled")
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def load_cut(workload):
+    with open(os.path.join(ROOT, "tests", "golden", "chi2_cuts.json")) as f:
+        return int(json.load(f)[workload]["cut"])
+
+
+def workload_desc(cfg, n_fits, n_words):
+    return "%s: %s (%d combinations, %d words)" % (cfg.name, cfg.description, n_fits, n_words)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                mhz.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_device_steps(ctx, B, torch, d_words, n_words, mode, steps, warmup, stream):
+    """Per-step device time (ms) of unpack + fit with an L2 flush between."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(warmup + steps):
+            flush.fill_(i & 0xFF)
+            if i >= warmup:
+                starts[i - warmup].record(stream)
+            B.check(ctx.unpack(d_words, n_words, stream), "svt_unpack")
+            B.check(ctx.fit_events(mode, stream), "svt_fit_events")
+            if i >= warmup:
+                ends[i - warmup].record(stream)
+    stream.synchronize()
+    st, n = ctx.get_tracks(out=None, stream=stream)[0], None
+    B.check(st, "svt_get_tracks")
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, steps, warmup, stream):
+    """Per-step host wall time (s) through the public API, pinned host I/O."""
+    n_words = h_words.numel()
+    lat, d2h = [], []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d_words.copy_(h_words, non_blocking=True)
+        B.check(ctx.unpack(d_words, n_words, stream), "svt_unpack")
+        B.check(ctx.fit_events(mode, stream), "svt_fit_events")
+        st, n = ctx.get_tracks(out=h_out, cap=h_out.numel() // 40, stream=stream)
+        B.check(st, "svt_get_tracks")
+        t1 = time.perf_counter()
+        if i >= warmup:
+            lat.append(t1 - t0)
+            d2h.append(n * 40)
+    return lat, d2h
+
+
+def cpu_baseline(batch, consts, cut, target_s=12.0):
+    """The oracle as it stands, single thread, on the first events of the
+    batch (grown until about target_s seconds of work)."""
+    import oracle
+    oracle.build()
+    n_ev = 25
+    while True:
+        words = batch.event_slice(0, n_ev)
+        t0 = time.perf_counter()
+        rc, out = oracle.run(words, consts, cut)
+        dt = time.perf_counter() - t0
+        if dt > target_s / 4 or n_ev >= batch.n_events:
+            break
+        n_ev = min(batch.n_events, int(n_ev * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
+    return {"value": fits / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d events of the batch (%d combinations), one run, %.1f s"
+                      % (n_ev, fits, dt)}
+
+
+def gpu_arm(args):
+    import torch
+    from paper_1312_0917_gb300 import binding as B, synth, build as nvbuild
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    nvbuild.build()
+    cfg = synth.CONFIGS[args.workload]
+    batch = synth.make_batch(cfg, seed=0)
+    consts = synth.make_constants(0)
+    cut = load_cut(args.workload)
+    n_fits, n_words, n_events = batch.n_fits, len(batch.words), batch.n_events
+    mode = B.PERSISTENT if args.mode == "persistent" else B.PLAIN
+
+    ctx = B.Context(local, max_combinations=(n_fits if not args.no_plain or mode == B.PLAIN
+                                             else 1 << 10))
+    ctx.load_constants(consts, cut)
+    stream = torch.cuda.Stream()
+    h_words = torch.from_numpy(batch.words.view(np.int32)).pin_memory()
+    d_words = torch.empty_like(h_words, device="cuda")
+    d_words.copy_(h_words)
+    torch.cuda.synchronize()
+
+    # correctness of the timed configuration is checked by the tests; here the
+    # track count is recorded beside the numbers
+    if mode == B.PERSISTENT:
+        ctx.use_graph(True)
+    times = None
+    with ClockSampler(local) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times = run_device_steps(ctx, B, torch, d_words, n_words, mode, args.steps,
+                                 args.warmup, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = ctx.last_launch_count()
+    stats = ctx.get_stats(stream)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t[0])
+    step_ms = total_ms / len(times)
+    value = n_fits * world / (step_ms / 1e3)
+
+    # plain per-stage path on the same batch, for comparison
+    plain = None
+    if mode == B.PERSISTENT and not args.no_plain:
+        ctx.use_graph(False)
+        pt = run_device_steps(ctx, B, torch, d_words, n_words, B.PLAIN, max(5, args.steps // 3),
+                              3, stream)
+        plain = {"ms_per_step": statistics.mean(pt), "fits_per_s": n_fits / (statistics.mean(pt) / 1e3),
+                 "p50_us": 1e3 * float(np.percentile(pt, 50)),
+                 "p99_us": 1e3 * float(np.percentile(pt, 99)),
+                 "gpu_launches_per_step": ctx.last_launch_count()}
+        if mode == B.PERSISTENT:
+            ctx.use_graph(True)
+
+    # end to end through the public API
+    h_out = torch.empty(max(1, stats["n_tracks"]) * 40, dtype=torch.uint8).pin_memory()
+    lat, d2h = run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, args.steps, args.warmup,
+                       stream)
+    e2e_s = sum(lat)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e = {"value": n_fits * world * len(lat) / e2e_s, "unit": "fits/s",
+           "h2d_bytes_per_step": n_words * 4, "d2h_bytes_per_step": int(statistics.mean(d2h)) + 160,
+           "p50_us": 1e6 * float(np.percentile(lat, 50)), "p99_us": 1e6 * float(np.percentile(lat, 99)),
+           "events_per_s": n_events * world * len(lat) / e2e_s}
+
+    if rank != 0:
+        dist.barrier()
+        return
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk = clocks.summary()
+    mhz = clk["sm_max_mhz"] or 2070.0
+    # ALU roofline: 36 int32 multiply-adds per combination (6 inputs x 6 output
+    # rows: 3 parameters, 3 chi-square components), against the INT32 lanes
+    peak_tops = sms * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = 36.0 * n_fits / (step_ms / 1e3) / 1e12
+    line = {
+        "metric": "track fits/s", "value": value, "unit": "fits/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32/int64", "data": "synthetic (seeded generator, workload shape of the config)",
+        "config": {"workload": workload_desc(cfg, n_fits, n_words), "mode": args.mode,
+                   "graph": mode == B.PERSISTENT, "l2": "256 MB flush written between steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "events_per_s": n_events * world / (step_ms / 1e3),
+        "latency_us": {"p50": 1e3 * float(np.percentile(times, 50)),
+                       "p99": 1e3 * float(np.percentile(times, 99))},
+        "tracks_per_step": stats["n_tracks"], "status": stats["status"],
+        "phase_us": dict(zip(["word_scan", "event_scatter", "unpack", "fit_cut_local_warrior",
+                              "cross_road_warrior", "output"],
+                             [x / 1e3 for x in stats["phase_ns"]])),
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "note": "36 int32 MACs per combination / INT32 lanes x SMs x max clock"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    if plain:
+        line["plain"] = plain
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(batch, consts, cut)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# --------------------------------------------------------------------------
+
+def reference_arm(args):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1312_0917_gb300 import synth
+    oracle.build()
+    cfg = synth.CONFIGS[args.workload]
+    batch = synth.make_batch(cfg, seed=0)
+    consts = synth.make_constants(0)
+    cut = load_cut(args.workload)
+    # bounded sample per step: ~1.5 s of oracle work
+    n_ev = max(1, min(batch.n_events, 150 if args.workload == "scaled" else 20))
+    words = batch.event_slice(0, n_ev)
+    fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
+    for _ in range(args.warmup):
+        oracle.run(words, consts, cut)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rc, out = oracle.run(words, consts, cut)
+        t.append(time.perf_counter() - t0)
+        assert rc == 0
+    value = fits * len(t) / sum(t)
+    sample = "first %d events of the %s batch (%d combinations) per step" % (n_ev, cfg.name, fits)
+    line = {"impl": "reference", "metric": "track fits/s", "value": value, "unit": "fits/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
+            "config": {"workload": workload_desc(cfg, batch.n_fits, len(batch.words)),
+                       "mode": "cpu oracle, serial"},
+            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * svt.h -- C ABI of the GB300 SVT track-fitting library (libsvt.so).
+ *
+ * The chain follows arXiv:1312.0917, Sec. II and Sec. II-A: unpack the packed
+ * input words into roads, form every combination of one hit per silicon layer
+ * in each road, run the linearised fixed-point fit p_i = f_i . x_i + q_i and
+ * the fit's chi-square, then keep the combinations that pass the chi-square
+ * cut and survive the hit-warrior.  Where the paper is silent the library
+ * fixes the reading; each one is stated at the call that uses it.
+ *
+ * Conventions for every call:
+ *  - Returns SVT_OK (0) or a negative SVT_E_* code; svt_strerror names it.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls only enqueue work on it unless they say they synchronise.
+ *  - Device pointers are plain CUDA device addresses owned by the caller (for
+ *    example torch tensors); the library never frees them.  The context owns
+ *    its own device scratch, sized once by svt_create from svt_limits.
+ *  - One context serves one stream at a time; use one context per concurrent
+ *    stream.  Calls on one context are not thread-safe.
+ *  - Kernels never trap: errors found on the device are written to a device
+ *    status word and returned by the next svt_get_tracks / svt_get_stats.
+ */
+#ifndef SVT_H
+#define SVT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SVT_OK            0
+#define SVT_E_INVAL      (-1)  /* bad argument (NULL, misaligned, out of range) */
+#define SVT_E_BADWORD    (-2)  /* a word breaks the format or the road grammar */
+#define SVT_E_TRUNCATED  (-3)  /* the stream does not end at an event boundary */
+#define SVT_E_LIMIT      (-4)  /* > 8 hits on a layer of a road or > 256 roads in an event */
+#define SVT_E_CAPACITY   (-5)  /* the batch exceeds the context limits or the caller's buffer */
+#define SVT_E_CUDA       (-6)  /* a CUDA runtime call failed */
+#define SVT_E_TIMEOUT    (-7)  /* a bounded device-side wait gave up */
+#define SVT_E_STATE      (-9)  /* call out of order (no constants, nothing unpacked) */
+
+/* ---- execution modes of svt_fit_events ---------------------------------- */
+#define SVT_PLAIN       0  /* one kernel per stage, per-combination results in HBM */
+#define SVT_PERSISTENT  1  /* one persistent fused kernel, device work queues */
+
+typedef struct svt_ctx svt_ctx;
+
+/* One constant set (Sec. II: "f_i and q_i are pre-defined constant sets"),
+ * looked up per road by s = (wedge * 6 + barrel) * 5 + excluded_layer.
+ * F and q give the track parameters, C and k the chi-square components:
+ *   x   = (hits of the 4 layers other than the excluded one, ascending layer,
+ *          then XFT curvature, then XFT phi)
+ *   p_i = floor((sum_j F[i][j] x_j) / 4096) + q[i]
+ *   a_k = floor((sum_j C[k][j] x_j) / 4096) + k[k],  chi2 = sum_k a_k^2
+ * 96 bytes, no padding. */
+typedef struct {
+    int16_t F[3][6];
+    int32_t q[3];
+    int16_t C[3][6];
+    int32_t k[3];
+} svt_const_set;
+
+/* One surviving combination (a fitted track).  40 bytes. */
+typedef struct {
+    uint32_t event;   /* event index in the batch (order of EE words) */
+    uint16_t road;    /* road index within the event (order of EP words) */
+    uint16_t comb;    /* combination: sum_l d_l * S_l, S_0 = 1,
+                         S_l = S_{l-1} * n_{l-1}; layer 0 varies fastest */
+    int32_t p[3];     /* d0, phi, pT (fixed point) */
+    uint32_t pad;     /* zero */
+    int64_t chi2;
+    uint64_t hits;    /* coordinate on layer l in bits 12l .. 12l+11 */
+} svt_track;
+
+/* One unpacked road (svt_get_roads).  100 bytes, no hidden padding. */
+typedef struct {
+    uint32_t event;          /* event index in the batch */
+    uint16_t road;           /* road index within the event */
+    int16_t curv, phi;       /* XFT track */
+    uint8_t wedge, barrel, excl;
+    uint8_t n[5];            /* hits per layer */
+    uint8_t pad[2];
+    uint16_t coord[5][8];    /* coordinate of hit d on layer l (0 beyond n) */
+} svt_road;
+
+/* Capacity of a context (0 in a field = its default). */
+typedef struct {
+    uint64_t max_words;      /* words per batch            (default 1 << 24) */
+    uint32_t max_events;     /* events per batch           (default 1 << 16) */
+    uint32_t max_roads;      /* roads per batch            (default 1 << 20) */
+    uint64_t max_tracks;     /* surviving tracks per batch (default 1 << 22) */
+    uint32_t hash_slots;     /* cross-road group table, power of 2 (default 1 << 20) */
+    uint32_t pad;
+    uint64_t max_combinations; /* SVT_PLAIN per-combination buffers (default 1 << 26) */
+} svt_limits;
+
+/* Counters of the last batch (svt_get_stats). */
+typedef struct {
+    uint64_t n_events;        /* complete events */
+    uint64_t n_roads;         /* roads of complete events */
+    uint64_t n_combinations;  /* sum over roads of prod_l n_l ("fits") */
+    uint64_t n_passing;       /* combinations with chi2 <= cut */
+    uint64_t n_tracks;        /* survivors of the hit-warrior */
+    int32_t status;           /* SVT_OK or the batch's error code */
+    uint32_t pad;
+    uint64_t error_word;      /* word position of the first fault (if any) */
+    uint64_t phase_ns[6];     /* SVT_PERSISTENT: time from the start of each stage to
+                                 the next (word scan, event scatter, unpack, fit+cut+
+                                 road-local warrior, cross-road warrior, output);
+                                 SVT_PLAIN: 0 */
+} svt_stats;
+
+/* Create a context on `device` (cudaSetDevice is called).  Allocates all
+ * device scratch for `lim` (NULL = defaults).  *out = NULL on failure. */
+int svt_create(svt_ctx **out, int device, const svt_limits *lim);
+
+/* Free the context and its device memory (synchronises the device). */
+void svt_destroy(svt_ctx *ctx);
+
+/* Copy n_sets (must be 360 = 12 wedges x 6 barrels x 5 excluded layers)
+ * constant sets from HOST memory to the device and set the chi-square cut:
+ * a combination passes iff chi2 <= chi2_cut.  Rejects (SVT_E_INVAL) a set
+ * whose values could overflow the exact 32-bit accumulation or the 38-bit
+ * chi-square of the track key: per row, sum_j |coef_j| * max|x_j| +
+ * 4096 * |offset| must stay below 2^31 (hits <= 4095, curvature and phi
+ * <= 32768) and sum_k (bound_k / 4096 + 1)^2 below 2^38.  Enqueued on
+ * `stream`; the host copy is done when the call returns. */
+int svt_load_constants(svt_ctx *ctx, const svt_const_set *sets, uint32_t n_sets,
+                       int64_t chi2_cut, void *stream);
+
+/* Sec. II-A, first function: unpack a batch.  d_words: DEVICE pointer to
+ * n_words packed 32-bit words, 4-byte aligned, owned by the caller and left
+ * unchanged until the batch's svt_get_tracks returns.
+ * Word: bit 31 EE (end of event, only with EP), bit 30 EP (end of road),
+ * bits 29..27 type (0..4 hit on that layer, 5 curvature, 6 phi, 7 header),
+ * bits 26..0 payload (hit: coordinate in bits 11..0; curvature/phi: int16 in
+ * bits 15..0; header: wedge 3..0 (<12), barrel 6..4 (<6), excluded layer 9..7
+ * (<5)); unused payload bits must be zero.  A road is header, curvature,
+ * phi, hits; <= 8 hits per layer, <= 256 roads per event.  The first word that
+ * breaks a rule sets the batch status (SVT_E_BADWORD before SVT_E_LIMIT at
+ * the same word); a stream not ending in EE is SVT_E_TRUNCATED.
+ * The call binds the batch and schedules the unpack stage: in SVT_PLAIN mode
+ * it runs as its own kernels inside svt_fit_events (or svt_get_roads), in
+ * SVT_PERSISTENT mode inside the fused kernel.  n_words > max_words ->
+ * SVT_E_CAPACITY. */
+int svt_unpack(svt_ctx *ctx, const uint32_t *d_words, size_t n_words, void *stream);
+
+/* Sec. II, second and third functions, plus the selection: every combination
+ * of one hit per layer, the fixed-point fit and chi-square, the cut, and the
+ * hit-warrior: among one event's passing combinations, t is dropped iff a
+ * passing u with a lower key (chi2, road, comb) shares >= 3 hits with t
+ * (equal coordinate on the same layer; all five layers count).  Enqueues the
+ * work of `mode` on `stream` and returns (asynchronous). */
+int svt_fit_events(svt_ctx *ctx, int mode, void *stream);
+
+/* Synchronise `stream`, then copy the batch's surviving tracks, in
+ * (event, road, comb) order, to `out` (host or device memory, capacity `cap`
+ * records).  *n_out = number of survivors (also when they do not fit, in
+ * which case SVT_E_CAPACITY is returned and nothing is copied).  Returns the
+ * batch status (a device-detected error is returned here with *n_out = 0). */
+int svt_get_tracks(svt_ctx *ctx, svt_track *out, size_t cap, size_t *n_out,
+                   void *stream);
+
+/* Synchronise `stream` and return the unpacked roads of complete events in
+ * stream order (runs the unpack stage first if it has not run yet).
+ * *n_out = road count; SVT_E_CAPACITY if cap is too small. */
+int svt_get_roads(svt_ctx *ctx, svt_road *out, size_t cap, size_t *n_out, void *stream);
+
+/* Synchronise `stream` and return the counters and status of the last batch. */
+int svt_get_stats(svt_ctx *ctx, svt_stats *out, void *stream);
+
+/* Launch settings of the persistent kernel (autotuning).  blocks_per_sm:
+ * resident CTAs per SM (0 = occupancy maximum); small_n4: roads with at most
+ * this many distinct fits (combinations of the four fitted layers) are
+ * processed by one warp, larger ones by a whole CTA (<= 256, 0 = 256).  Takes
+ * effect from the next svt_fit_events. */
+int svt_set_launch(svt_ctx *ctx, int blocks_per_sm, int small_n4);
+
+/* Capture the enqueue of svt_fit_events(ctx, mode) for the bound batch into a
+ * CUDA graph and use it for later svt_fit_events calls with the same batch
+ * binding (enable = 1); enable = 0 returns to direct launches. */
+int svt_use_graph(svt_ctx *ctx, int enable);
+
+/* Test hook: spin limit of device-side waits in microseconds (0 = default of
+ * two seconds) and, when skip_arrival is 1, block 0 of the next persistent
+ * launch leaves before its first grid barrier so the others' waits run out
+ * and the batch ends with SVT_E_TIMEOUT.  Never faults or hangs the device. */
+int svt_debug_wait(svt_ctx *ctx, uint32_t wait_limit_us, int skip_arrival);
+
+/* Number of kernels the last svt_fit_events enqueued (for launch accounting). */
+int svt_last_launch_count(svt_ctx *ctx);
+
+const char *svt_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVT_H */

@@ -1,0 +1,208 @@
+"""ctypes binding of libsvt.so: the C ABI of include/svt.h, argument
+marshalling only.  Every step of the track-fitting chain runs in the
+library's CUDA kernels; there is no CPU fallback, and a missing library is
+an error.
+
+Device buffers are passed as raw pointers (an int, or any object with
+``data_ptr()`` such as a torch tensor); streams as a ``cudaStream_t`` value
+(an int, or an object with ``cuda_stream``); None is the legacy default
+stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsvt.so")
+
+OK, E_INVAL, E_BADWORD, E_TRUNCATED, E_LIMIT = 0, -1, -2, -3, -4
+E_CAPACITY, E_CUDA, E_TIMEOUT, E_STATE = -5, -6, -7, -9
+PLAIN, PERSISTENT = 0, 1
+
+CONST_DTYPE = np.dtype([("F", np.int16, (3, 6)), ("q", np.int32, (3,)),
+                        ("C", np.int16, (3, 6)), ("k", np.int32, (3,))])
+TRACK_DTYPE = np.dtype([("event", np.uint32), ("road", np.uint16), ("comb", np.uint16),
+                        ("p", np.int32, (3,)), ("pad", np.uint32), ("chi2", np.int64),
+                        ("hits", np.uint64)], align=True)
+ROAD_DTYPE = np.dtype([("event", np.uint32), ("road", np.uint16), ("curv", np.int16),
+                       ("phi", np.int16), ("wedge", np.uint8), ("barrel", np.uint8),
+                       ("excl", np.uint8), ("n", np.uint8, (5,)), ("pad", np.uint8, (2,)),
+                       ("coord", np.uint16, (5, 8))], align=True)
+assert CONST_DTYPE.itemsize == 96 and TRACK_DTYPE.itemsize == 40 and ROAD_DTYPE.itemsize == 100
+
+
+class Limits(C.Structure):
+    _fields_ = [("max_words", C.c_uint64), ("max_events", C.c_uint32),
+                ("max_roads", C.c_uint32), ("max_tracks", C.c_uint64),
+                ("hash_slots", C.c_uint32), ("pad", C.c_uint32),
+                ("max_combinations", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_events", C.c_uint64), ("n_roads", C.c_uint64),
+                ("n_combinations", C.c_uint64), ("n_passing", C.c_uint64),
+                ("n_tracks", C.c_uint64), ("status", C.c_int32), ("pad", C.c_uint32),
+                ("error_word", C.c_uint64), ("phase_ns", C.c_uint64 * 6)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "phase_ns")}
+        d["phase_ns"] = list(self.phase_ns)
+        return d
+
+
+# every entry point of include/svt.h with its argument types
+SIGNATURES = {
+    "svt_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Limits)]),
+    "svt_destroy": (None, [C.c_void_p]),
+    "svt_load_constants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_int64, C.c_void_p]),
+    "svt_unpack": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "svt_fit_events": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "svt_get_tracks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
+                                 C.c_void_p]),
+    "svt_get_roads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
+                                C.c_void_p]),
+    "svt_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_void_p]),
+    "svt_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "svt_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
+    "svt_last_launch_count": (C.c_int, [C.c_void_p]),
+    "svt_strerror": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+class SvtError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib().svt_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+
+
+def lib() -> C.CDLL:
+    """Load libsvt.so (built by paper_1312_0917_gb300.build); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsvt.so is not built: run "
+                              "`python -m paper_1312_0917_gb300.build` (or __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def ptr(x) -> int | None:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+def stream_ptr(s) -> int | None:
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def check(code: int, what: str) -> int:
+    if code != OK:
+        raise SvtError(code, what)
+    return code
+
+
+def pack_constants(consts: dict) -> np.ndarray:
+    """dict(F, q, C, k) with shapes (360,3,6), (360,3), (360,3,6), (360,3)
+    -> array of svt_const_set records."""
+    n = consts["F"].shape[0]
+    out = np.zeros(n, dtype=CONST_DTYPE)
+    out["F"], out["q"] = consts["F"], consts["q"]
+    out["C"], out["k"] = consts["C"], consts["k"]
+    return out
+
+
+class Context:
+    """One svt_ctx (one stream at a time)."""
+
+    def __init__(self, device: int = 0, **limits):
+        self._h = C.c_void_p()
+        lim = Limits(**limits)
+        check(lib().svt_create(C.byref(self._h), device, C.byref(lim)), "svt_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().svt_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_constants(self, consts: dict, cut: int, stream=None):
+        sets = pack_constants(consts)
+        check(lib().svt_load_constants(self._h, sets.ctypes.data, len(sets), int(cut),
+                                       stream_ptr(stream)), "svt_load_constants")
+
+    def unpack(self, d_words, n_words: int, stream=None) -> int:
+        return lib().svt_unpack(self._h, ptr(d_words), n_words, stream_ptr(stream))
+
+    def fit_events(self, mode: int = PERSISTENT, stream=None) -> int:
+        return lib().svt_fit_events(self._h, mode, stream_ptr(stream))
+
+    def get_tracks(self, out=None, cap: int | None = None, stream=None):
+        """Returns (status, tracks).  Without `out`, copies to a new host array."""
+        n = C.c_size_t()
+        if out is None:
+            st = lib().svt_get_tracks(self._h, None, 0, C.byref(n), stream_ptr(stream))
+            if st not in (OK, E_CAPACITY) or (st == E_CAPACITY and n.value == 0):
+                return st, np.zeros(0, dtype=TRACK_DTYPE)
+            host = np.zeros(n.value, dtype=TRACK_DTYPE)
+            st = lib().svt_get_tracks(self._h, host.ctypes.data, n.value, C.byref(n),
+                                      stream_ptr(stream))
+            return st, host
+        st = lib().svt_get_tracks(self._h, ptr(out), cap, C.byref(n), stream_ptr(stream))
+        return st, n.value
+
+    def get_roads(self, stream=None):
+        n = C.c_size_t()
+        st = lib().svt_get_roads(self._h, None, 0, C.byref(n), stream_ptr(stream))
+        if st not in (OK, E_CAPACITY) or (st == E_CAPACITY and n.value == 0):
+            return st, np.zeros(0, dtype=ROAD_DTYPE)
+        host = np.zeros(n.value, dtype=ROAD_DTYPE)
+        st = lib().svt_get_roads(self._h, host.ctypes.data, n.value, C.byref(n),
+                                 stream_ptr(stream))
+        return st, host
+
+    def get_stats(self, stream=None) -> dict:
+        s = Stats()
+        check(lib().svt_get_stats(self._h, C.byref(s), stream_ptr(stream)), "svt_get_stats")
+        return s.as_dict()
+
+    def set_launch(self, blocks_per_sm: int = 0, small_n4: int = 0):
+        check(lib().svt_set_launch(self._h, blocks_per_sm, small_n4), "svt_set_launch")
+
+    def use_graph(self, enable: bool = True):
+        check(lib().svt_use_graph(self._h, int(enable)), "svt_use_graph")
+
+    def debug_wait(self, wait_limit_us: int = 0, skip_arrival: bool = False):
+        check(lib().svt_debug_wait(self._h, wait_limit_us, int(skip_arrival)), "svt_debug_wait")
+
+    def last_launch_count(self) -> int:
+        return lib().svt_last_launch_count(self._h)

@@ -1,0 +1,458 @@
+// svt_api.cu -- the C ABI (include/svt.h): context, buffers, status, launches.
+#include "svt_internal.h"
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace svt;
+
+static_assert(sizeof(svt_const_set) == 96, "svt_const_set layout");
+static_assert(sizeof(svt_track) == 40, "svt_track layout");
+static_assert(sizeof(svt_road) == 100, "svt_road layout");
+static_assert(sizeof(RoadRec) == 16, "RoadRec layout");
+
+struct svt_ctx {
+    int device = 0;
+    svt_limits lim{};
+    Dev d{};
+    Ctrl *h_ctrl = nullptr;          // pinned mirror of the control block
+    bool consts_loaded = false;
+    bool bound = false;              // a batch is bound by svt_unpack
+    bool roads_valid = false;        // the road table holds the bound batch
+    bool ran = false;                // svt_fit_events ran on the bound batch
+    int blocks_per_sm = 0;
+    int last_launches = 0;
+    unsigned long long wait_ns = 2000000000ull;
+    int skip_arrival = 0;
+    bool hash_dirty = false;         // a batch stopped before clearing its group table
+    // CUDA graph of one svt_fit_events enqueue
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    int g_mode = -1;
+    const uint32_t *g_words = nullptr;
+    unsigned long long g_n = 0;
+    cudaStream_t g_stream = nullptr;
+    int g_launches = 0;
+    unsigned long long g_key = 0;
+    void *allocs[40] = {};
+    int n_allocs = 0;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(svt_ctx *c, T **p, size_t count)
+{
+    void *q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0)
+        bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return e;
+    c->allocs[c->n_allocs++] = q;
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+void free_all(svt_ctx *c)
+{
+    for (int i = 0; i < c->n_allocs; ++i)
+        cudaFree(c->allocs[i]);
+    c->n_allocs = 0;
+    if (c->h_ctrl)
+        cudaFreeHost(c->h_ctrl);
+    c->h_ctrl = nullptr;
+    if (c->gexec)
+        cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
+void drop_graph(svt_ctx *c)
+{
+    if (c->gexec)
+        cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_mode = -1;
+}
+
+long long bound_row(const int16_t *coef, int32_t off)
+{
+    long long b = 0;
+    for (int j = 0; j < 6; ++j)
+        b += (long long)std::llabs(coef[j]) * (j < 4 ? 4095 : 32768);
+    return b + 4096ll * std::llabs((long long)off);
+}
+
+int status_of(const Ctrl &c)
+{
+#ifdef SVT_CHECK
+    if (c.dbg[0]) {
+        fprintf(stderr, "svt self-check: site %llu a=%llu b=%llu failures=%llu\n", c.dbg[0], c.dbg[1],
+                c.dbg[2], c.dbg[3]);
+        return SVT_E_CUDA;
+    }
+#endif
+
+    if (c.flags & FLAG_TIMEOUT)
+        return SVT_E_TIMEOUT;
+    if (c.flags & FLAG_CAPACITY)
+        return SVT_E_CAPACITY;
+    if (c.err_inv != 0ull) {
+        unsigned rank = (unsigned)(~c.err_inv & 0xFFull);
+        return rank == RANK_BAD ? SVT_E_BADWORD : rank == RANK_LIMIT ? SVT_E_LIMIT : SVT_E_TRUNCATED;
+    }
+    if (c.flags & FLAG_INTERNAL)
+        return SVT_E_CUDA;
+    return SVT_OK;
+}
+
+int read_ctrl(svt_ctx *c, cudaStream_t s)
+{
+    if (cudaMemcpyAsync(c->h_ctrl, c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SVT_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return SVT_E_CUDA;
+    if (c->h_ctrl->flags & FLAG_TIMEOUT)
+        c->hash_dirty = true;   // the batch may have stopped before clearing the table
+    return SVT_OK;
+}
+
+int ensure_plain_buffers(svt_ctx *c)
+{
+    if (c->d.fit_key)
+        return SVT_OK;
+    if (dalloc(c, &c->d.fit_key, c->d.max_combs) || dalloc(c, &c->d.fit_p, c->d.max_combs * 3))
+        return SVT_E_CUDA;
+    return SVT_OK;
+}
+
+// enqueue one batch (ctrl reset + kernels) on s
+cudaError_t enqueue(svt_ctx *c, int mode, cudaStream_t s, int *launches)
+{
+    Dev d = c->d;
+    d.wait_ns = c->wait_ns;
+    d.skip_arrival = c->skip_arrival;
+    cudaError_t e = cudaMemsetAsync(c->d.ctrl, 0, sizeof(Ctrl), s);
+    if (e)
+        return e;
+    if (c->hash_dirty) {
+        if ((e = cudaMemsetAsync(c->d.hash, 0, sizeof(HashSlot) * (size_t)(c->d.hash_mask + 1), s)))
+            return e;
+        c->hash_dirty = false;
+    }
+    if (mode == SVT_PLAIN) {
+        if ((e = launch_unpack_plain(d, s, launches)))
+            return e;
+        return launch_fit_plain(d, s, launches);
+    }
+    return launch_persistent(d, s, c->blocks_per_sm, launches);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *svt_strerror(int code)
+{
+    switch (code) {
+    case SVT_OK: return "ok";
+    case SVT_E_INVAL: return "invalid argument";
+    case SVT_E_BADWORD: return "malformed input word";
+    case SVT_E_TRUNCATED: return "input does not end at an event boundary";
+    case SVT_E_LIMIT: return "more than 8 hits on a layer or 256 roads in an event";
+    case SVT_E_CAPACITY: return "batch exceeds the context or buffer capacity";
+    case SVT_E_CUDA: return "CUDA runtime error";
+    case SVT_E_TIMEOUT: return "device-side wait timed out";
+    case SVT_E_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int svt_create(svt_ctx **out, int device, const svt_limits *lim)
+{
+    if (!out)
+        return SVT_E_INVAL;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return SVT_E_CUDA;
+    svt_ctx *c = new (std::nothrow) svt_ctx();
+    if (!c)
+        return SVT_E_INVAL;
+    c->device = device;
+    svt_limits L = lim ? *lim : svt_limits{};
+    if (!L.max_words) L.max_words = 1ull << 24;
+    if (!L.max_events) L.max_events = 1u << 16;
+    if (!L.max_roads) L.max_roads = 1u << 20;
+    if (!L.max_tracks) L.max_tracks = 1ull << 22;
+    if (!L.hash_slots) L.hash_slots = 1u << 20;
+    if (!L.max_combinations) L.max_combinations = 1ull << 26;
+    if ((L.hash_slots & (L.hash_slots - 1)) || L.max_words >= (1ull << 32) ||
+        L.max_tracks >= (1ull << 32)) {
+        delete c;
+        return SVT_E_INVAL;
+    }
+    c->lim = L;
+    Dev &d = c->d;
+    unsigned n_chunks_w = (unsigned)((L.max_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
+    d.max_events = L.max_events;
+    d.max_roads = L.max_roads;
+    d.max_chunks_r = (L.max_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    d.max_tracks = L.max_tracks;
+    d.max_combs = L.max_combinations;
+    d.pool_cap = L.max_tracks;
+    d.hash_mask = L.hash_slots - 1;
+    d.small_n4 = N4_SMALL_MAX;
+    bool ok =
+        !dalloc(c, &d.ctrl, 1) && !dalloc(c, const_cast<svt_const_set **>(&d.consts), N_SETS) &&
+        !dalloc(c, &d.chunk_ee, n_chunks_w) && !dalloc(c, &d.chunk_ep, n_chunks_w) &&
+        !dalloc(c, &d.chunk_ee_off, n_chunks_w) && !dalloc(c, &d.chunk_ep_off, n_chunks_w) &&
+        !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
+        !dalloc(c, &d.road_end, L.max_roads) &&
+        !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
+        !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
+        !dalloc(c, &d.small_list, L.max_roads) && !dalloc(c, &d.surv_pool, d.pool_cap) &&
+        !dalloc(c, &d.surv_off, L.max_roads) && !dalloc(c, &d.surv_cnt, L.max_roads) &&
+        !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&
+        !dalloc(c, &d.cchunk_sum, d.max_chunks_r) && !dalloc(c, &d.cchunk_off, d.max_chunks_r) &&
+        !dalloc(c, &d.hash, L.hash_slots) && !dalloc(c, &d.hash_used, L.hash_slots) &&
+        !dalloc(c, &d.comb_off, L.max_roads) && !dalloc(c, &d.tracks, L.max_tracks) &&
+        cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)) == cudaSuccess &&
+        cudaMemset(d.hash, 0, sizeof(HashSlot) * (size_t)L.hash_slots) == cudaSuccess &&
+        cudaMemset(d.ctrl, 0, sizeof(Ctrl)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return SVT_E_CUDA;
+    }
+    *out = c;
+    return SVT_OK;
+}
+
+void svt_destroy(svt_ctx *c)
+{
+    if (!c)
+        return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+int svt_load_constants(svt_ctx *c, const svt_const_set *sets, uint32_t n_sets, int64_t cut,
+                       void *stream)
+{
+    if (!c || !sets || n_sets != (uint32_t)N_SETS || cut < 0)
+        return SVT_E_INVAL;
+    for (int s = 0; s < N_SETS; ++s) {
+        long long chi_bound = 0;
+        for (int k = 0; k < 3; ++k) {
+            long long bf = bound_row(sets[s].F[k], sets[s].q[k]);
+            long long bc = bound_row(sets[s].C[k], sets[s].k[k]);
+            if (bf >= (1ll << 31) || bc >= (1ll << 31))
+                return SVT_E_INVAL;
+            long long a = bc / 4096 + 1;
+            chi_bound += a * a;
+        }
+        if (chi_bound >= (1ll << 38))
+            return SVT_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(c->device) ||
+        cudaMemcpyAsync(const_cast<svt_const_set *>(c->d.consts), sets, sizeof(svt_const_set) * N_SETS,
+                        cudaMemcpyHostToDevice, s) ||
+        cudaStreamSynchronize(s))
+        return SVT_E_CUDA;
+    c->d.cut = cut;
+    c->consts_loaded = true;
+    drop_graph(c);
+    return SVT_OK;
+}
+
+int svt_unpack(svt_ctx *c, const uint32_t *d_words, size_t n_words, void *stream)
+{
+    (void)stream;
+    if (!c || (n_words && !d_words) || ((uintptr_t)d_words & 3u))
+        return SVT_E_INVAL;
+    if (n_words > c->lim.max_words)
+        return SVT_E_CAPACITY;
+    c->d.words = d_words;
+    c->d.n_words = n_words;
+    c->d.n_chunks_w = (unsigned)((n_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
+    c->bound = true;
+    c->roads_valid = false;
+    c->ran = false;
+    return SVT_OK;
+}
+
+int svt_fit_events(svt_ctx *c, int mode, void *stream)
+{
+    if (!c || (mode != SVT_PLAIN && mode != SVT_PERSISTENT))
+        return SVT_E_INVAL;
+    if (!c->consts_loaded || !c->bound)
+        return SVT_E_STATE;
+    if (cudaSetDevice(c->device))
+        return SVT_E_CUDA;
+    if (mode == SVT_PLAIN && ensure_plain_buffers(c))
+        return SVT_E_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    cudaError_t e;
+    if (c->use_graph && s != nullptr) {
+        bool hit = c->gexec && c->g_mode == mode && c->g_words == c->d.words && c->g_n == c->d.n_words &&
+                   c->g_stream == s;
+        if (!hit) {
+            drop_graph(c);
+            cudaGraph_t graph = nullptr;
+            if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)))
+                return SVT_E_CUDA;
+            int nl = 0;
+            cudaError_t ee = enqueue(c, mode, s, &nl);
+            e = cudaStreamEndCapture(s, &graph);
+            if (ee || e || !graph) {
+                if (graph)
+                    cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return SVT_E_CUDA;
+            }
+            e = cudaGraphInstantiate(&c->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e) {
+                c->gexec = nullptr;
+                cudaGetLastError();
+                return SVT_E_CUDA;
+            }
+            c->g_mode = mode;
+            c->g_words = c->d.words;
+            c->g_n = c->d.n_words;
+            c->g_stream = s;
+            c->g_launches = nl;
+        }
+        e = cudaGraphLaunch(c->gexec, s);
+        launches = c->g_launches;
+    } else {
+        e = enqueue(c, mode, s, &launches);
+    }
+    if (e)
+        return SVT_E_CUDA;
+    c->last_launches = launches;
+    c->ran = true;
+    c->roads_valid = true;
+    return SVT_OK;
+}
+
+int svt_get_tracks(svt_ctx *c, svt_track *out, size_t cap, size_t *n_out, void *stream)
+{
+    if (!c || !n_out)
+        return SVT_E_INVAL;
+    *n_out = 0;
+    if (!c->ran)
+        return SVT_E_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(c->device) || read_ctrl(c, s))
+        return SVT_E_CUDA;
+    int st = status_of(*c->h_ctrl);
+    if (st)
+        return st;
+    size_t n = (size_t)c->h_ctrl->n_out;
+    *n_out = n;
+    if (n > cap)
+        return SVT_E_CAPACITY;
+    if (n && (!out || cudaMemcpyAsync(out, c->d.tracks, n * sizeof(svt_track), cudaMemcpyDefault, s) ||
+              cudaStreamSynchronize(s)))
+        return out ? SVT_E_CUDA : SVT_E_INVAL;
+    return SVT_OK;
+}
+
+int svt_get_roads(svt_ctx *c, svt_road *out, size_t cap, size_t *n_out, void *stream)
+{
+    if (!c || !n_out)
+        return SVT_E_INVAL;
+    *n_out = 0;
+    if (!c->bound)
+        return SVT_E_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(c->device))
+        return SVT_E_CUDA;
+    if (!c->roads_valid) {
+        int nl = 0;
+        Dev d = c->d;
+        if (cudaMemsetAsync(c->d.ctrl, 0, sizeof(Ctrl), s) || launch_unpack_plain(d, s, &nl))
+            return SVT_E_CUDA;
+        c->roads_valid = true;
+    }
+    if (!c->d.road_out && dalloc(c, &c->d.road_out, c->lim.max_roads))
+        return SVT_E_CUDA;
+    if (launch_export_roads(c->d, s) || read_ctrl(c, s))
+        return SVT_E_CUDA;
+    const Ctrl &h = *c->h_ctrl;
+    int st = status_of(h);
+    if (st)
+        return st;
+    size_t n = h.n_roads;
+    *n_out = n;
+    if (n > cap)
+        return SVT_E_CAPACITY;
+    if (n && (!out || cudaMemcpyAsync(out, c->d.road_out, n * sizeof(svt_road), cudaMemcpyDefault, s) ||
+              cudaStreamSynchronize(s)))
+        return out ? SVT_E_CUDA : SVT_E_INVAL;
+    return SVT_OK;
+}
+
+int svt_get_stats(svt_ctx *c, svt_stats *out, void *stream)
+{
+    if (!c || !out)
+        return SVT_E_INVAL;
+    if (cudaSetDevice(c->device) || read_ctrl(c, (cudaStream_t)stream))
+        return SVT_E_CUDA;
+    const Ctrl &h = *c->h_ctrl;
+    std::memset(out, 0, sizeof *out);
+    out->n_events = h.n_events;
+    out->n_roads = h.n_roads;
+    out->n_combinations = h.n_comb;
+    out->n_passing = h.n_pass;
+    out->n_tracks = h.n_out;
+    out->status = status_of(h);
+    out->error_word = h.err_inv ? (~h.err_inv) >> 8 : 0ull;
+    for (int k = 0; k < 6; ++k) {
+        unsigned long long a = h.t_phase[k], b = h.t_phase[k + 1];
+        out->phase_ns[k] = (a && b && b >= a) ? b - a : 0ull;
+    }
+    return SVT_OK;
+}
+
+int svt_set_launch(svt_ctx *c, int blocks_per_sm, int small_n4)
+{
+    if (!c || blocks_per_sm < 0 || small_n4 < 0 || small_n4 > N4_SMALL_MAX)
+        return SVT_E_INVAL;
+    c->blocks_per_sm = blocks_per_sm;
+    c->d.small_n4 = small_n4 ? small_n4 : N4_SMALL_MAX;
+    drop_graph(c);
+    return SVT_OK;
+}
+
+int svt_use_graph(svt_ctx *c, int enable)
+{
+    if (!c)
+        return SVT_E_INVAL;
+    c->use_graph = enable != 0;
+    if (!c->use_graph)
+        drop_graph(c);
+    return SVT_OK;
+}
+
+int svt_debug_wait(svt_ctx *c, uint32_t wait_limit_us, int skip_arrival)
+{
+    if (!c)
+        return SVT_E_INVAL;
+    c->wait_ns = wait_limit_us ? (unsigned long long)wait_limit_us * 1000ull : 2000000000ull;
+    c->skip_arrival = skip_arrival ? 1 : 0;
+    drop_graph(c);
+    return SVT_OK;
+}
+
+int svt_last_launch_count(svt_ctx *c) { return c ? c->last_launches : 0; }
+
+}  // extern "C"

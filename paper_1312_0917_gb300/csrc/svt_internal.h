@@ -1,0 +1,116 @@
+// svt_internal.h -- definitions shared by the library's kernels and its C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "svt.h"
+
+namespace svt {
+
+constexpr int BLOCK = 256;                 // threads per CTA, every kernel
+constexpr int WARPS = BLOCK / 32;
+constexpr int CHUNK_WORDS = 4096;          // words per unpack work item (16 per thread)
+constexpr int MAX_ROADS_EV = 256;          // format limit: roads per event
+constexpr int MAX_HITS = 8;                // format limit: hits per layer per road
+constexpr int N_LAYERS = 5;
+constexpr int N_SETS = 360;                // 12 wedges x 6 barrels x 5 excluded layers
+constexpr int SURV_SLOTS = 64;             // survivors per road are <= 64 (see fit_road)
+constexpr int ROAD_CHUNK = 256;            // roads per output work item
+constexpr int N4_MAX = 4096;               // distinct fits per road: 8^4
+constexpr int N4_SMALL_MAX = 256;          // largest road a single warp takes
+constexpr int QTAB_BIG = 384;              // pair tables, sum_{a<b} m_a m_b for 8^4
+constexpr int QTAB_SMALL = 160;            // the same sum for any road with N4 <= 256
+constexpr unsigned long long NO_KEY = ~0ull;
+
+// fault ranks: at one word a format/grammar fault outranks a limit fault;
+// truncation is reported at position n_words, after every word
+enum : unsigned { RANK_BAD = 1, RANK_LIMIT = 2, RANK_TRUNC = 3 };
+enum : unsigned { FLAG_CAPACITY = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4 };
+
+// Per-batch control block in device memory; zeroed by the host before each
+// batch.  Queue counters hand out work items; `bar` counts grid-barrier
+// arrivals of the persistent kernel.
+struct Ctrl {
+    unsigned long long err_inv;   // max over faults of ~((pos << 8) | rank); 0 = none
+    unsigned int flags;           // FLAG_*
+    unsigned int n_events;        // complete events (EE words)
+    unsigned int n_ep;            // EP words in the stream
+    unsigned int has_tail;        // words after the last EE
+    unsigned int n_roads;         // roads of complete events
+    unsigned int n_big, n_small;  // road work lists
+    unsigned int hash_used;       // claimed slots of the group table
+    unsigned int q[12];           // work-queue heads
+    unsigned int bar;             // grid barrier arrivals
+    unsigned int done[4];         // last-block-done counters
+    unsigned int pad0;
+    unsigned long long n_comb, n_pass, n_out;
+    unsigned long long pool_used;     // overflow part of surv_pool in use
+    unsigned long long pad1;
+    unsigned long long t_phase[8];    // globaltimer at the start of each phase (block 0)
+#ifdef SVT_CHECK
+    unsigned long long dbg[4];        // self-check build: first violated check
+#endif
+};
+
+// Unpacked road, 16 bytes.  pk: n[l] in bits 4l..4l+3 (l < 5), excluded layer
+// in bits 20..22, cross-road candidate in bit 23, road-in-event in bits 24..31.
+struct RoadRec {
+    uint32_t event;
+    uint32_t pk;
+    int16_t curv, phi;
+    uint16_t set;
+    uint16_t pad;
+};
+
+// Cross-road group table slot: key = (event + 1, triple, three coordinates),
+// val_inv = ~(lowest track key of the group), 0 = empty.
+struct HashSlot {
+    unsigned long long key, val_inv;
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    Ctrl *ctrl;
+    const svt_const_set *consts;
+    const uint32_t *words;
+    unsigned long long n_words;
+    unsigned int n_chunks_w;        // ceil(n_words / CHUNK_WORDS)
+    unsigned int max_events, max_roads, max_chunks_r;
+    unsigned long long max_tracks, max_combs;
+    uint32_t *chunk_ee, *chunk_ep, *chunk_ee_off, *chunk_ep_off;   // [n_chunks_w]
+    uint32_t *ev_word_end, *ev_road_end;                          // [max_events]
+    uint32_t *road_end;                                           // [max_roads] EP word of road g
+    RoadRec *roads;                                               // [max_roads]
+    uint16_t *coords;                                             // [max_roads][5][8]
+    unsigned long long *xmask;                                    // [max_roads]
+    uint32_t *big_list, *small_list;                              // [max_roads]
+    unsigned long long *surv_pool;                                // [pool_cap] road-local survivors
+    uint32_t *surv_off;                                           // [max_roads] first pool slot
+    uint8_t *surv_cnt;                                            // [max_roads]
+    unsigned long long pool_cap;
+    uint32_t *rchunk_sum, *rchunk_off;                            // [max_chunks_r]
+    unsigned long long *cchunk_sum, *cchunk_off;                  // [max_chunks_r]
+    HashSlot *hash;
+    uint32_t *hash_used;
+    uint32_t hash_mask;
+    unsigned long long *comb_off;                                 // plain: [max_roads]
+    unsigned long long *fit_key;                                  // plain: [max_combs]
+    int32_t *fit_p;                                               // plain: [max_combs][3]
+    svt_track *tracks;                                            // [max_tracks]
+    svt_road *road_out;                                           // [max_roads] (svt_get_roads)
+    long long cut;
+    int small_n4;
+    int skip_arrival;
+    unsigned long long wait_ns;
+};
+
+// launchers (svt_kernels.cu)
+cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches);
+cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches);
+cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int *n_launches);
+cudaError_t launch_export_roads(const Dev &d, cudaStream_t s);
+int persistent_max_blocks_per_sm(int device);
+size_t persistent_smem_bytes();
+
+}  // namespace svt

@@ -1,0 +1,1708 @@
+// svt_kernels.cu -- sm_103a kernels of the SVT track-fitting chain.
+//
+// Stages (arXiv:1312.0917, Sec. II-A: unpack, combine, fit), followed by the
+// chi-square cut and the hit-warrior:
+//
+//   P0  word chunks: count EE / EP words, check every word's fields
+//   P1  word chunks: scatter the end word and the road count of every event
+//   P2  events: decode each road (header, XFT track, hits ranked per layer),
+//       enforce the grammar and limits, flag hits whose coordinate appears in
+//       another road of the same event on the same layer
+//   P3  roads: combinations, fit, chi-square, cut and the road-local part of
+//       the hit-warrior; publish cross-road group minima for flagged groups
+//   P4  road chunks: finish the hit-warrior across roads, count survivors
+//   P5  road chunks: write the surviving tracks in (event, road, comb) order
+//
+// SVT_PLAIN runs P0, P1, P2, a combination scan, a fit kernel with one thread
+// per combination that stores every key and track parameter in HBM, the
+// warrior, P4 and P5 as separate kernels.  SVT_PERSISTENT runs all phases in
+// one cooperative kernel separated by grid barriers whose waits are bounded,
+// and evaluates each distinct fit once from per-hit partial sums kept in
+// shared memory.  Both produce identical tracks.
+//
+// Integer exactness (the reason the fit runs in 32-bit): svt_load_constants
+// admits only constant sets for which every partial and full sum of
+// coefficient x input (+ 4096 x offset) stays below 2^31 in magnitude, so
+// int32 accumulation equals the int64 sum; an arithmetic right shift by 12
+// is floor division by 4096, and floor(s / 4096) + k == floor((s + 4096 k) /
+// 4096).  chi2 < 2^38, so the track key (chi2 << 23 | road << 15 | comb)
+// is a 61-bit integer ordered like (chi2, road, comb).
+#include "svt_internal.h"
+
+namespace svt {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned warp_id() { return threadIdx.x >> 5; }
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// loads of data written earlier in the same launch by other CTAs: L2 only
+template <class T>
+__device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ RoadRec ldcg(const RoadRec *p)
+{
+    static_assert(sizeof(RoadRec) == 16, "RoadRec is one 16-byte load");
+    RoadRec r;
+    uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+    memcpy(&r, &v, sizeof r);
+    return r;
+}
+
+// Self-check build (-DSVT_CHECK, never the shipped library): a check that
+// fails records (site, a, b) once in Ctrl::dbg and the access is skipped.
+#ifdef SVT_CHECK
+__device__ __noinline__ void chk_fail(Ctrl *c, unsigned site, unsigned long long a, unsigned long long b)
+{
+    if (atomicCAS(&c->dbg[0], 0ull, (unsigned long long)site) == 0ull) {
+        c->dbg[1] = a;
+        c->dbg[2] = b;
+    }
+    atomicAdd(&c->dbg[3], 1ull);
+}
+#define SVT_OK_(d, cond, site, a, b) ((cond) ? true : (chk_fail((d).ctrl, (site), (a), (b)), false))
+#else
+#define SVT_OK_(d, cond, site, a, b) true
+#endif
+
+__device__ __forceinline__ void report(const Dev &d, unsigned long long pos, unsigned rank)
+{
+    atomicMax(&d.ctrl->err_inv, ~((pos << 8) | rank));
+}
+
+__device__ __forceinline__ void raise_flag(const Dev &d, unsigned f) { atomicOr(&d.ctrl->flags, f); }
+
+__device__ __forceinline__ bool word_ok(uint32_t w)
+{
+    uint32_t type = (w >> 27) & 7u, pl = w & 0x07FFFFFFu;
+    if ((w >> 31) && !((w >> 30) & 1u))
+        return false;                                   // EE without EP
+    if (type <= 4)
+        return (pl >> 12) == 0;
+    if (type <= 6)
+        return (pl >> 16) == 0;
+    return (pl >> 10) == 0 && (pl & 15u) < 12 && ((pl >> 4) & 7u) < 6 && ((pl >> 7) & 7u) < 5;
+}
+
+// exact floor(x / m) for x < 2^32 / m, m >= 1, with M = ceil(2^32 / m)
+__device__ __forceinline__ unsigned divm(unsigned x, unsigned long long M)
+{
+    return (unsigned)(((unsigned long long)x * M) >> 32);
+}
+__host__ __device__ __forceinline__ unsigned long long magic(unsigned m)
+{
+    return ((1ull << 32) + m - 1) / m;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(FULL_MASK, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one unsigned long long per thread
+__device__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *total)
+{
+    __shared__ unsigned long long s_w[WARPS + 1];
+    unsigned long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long n = __shfl_up_sync(FULL_MASK, inc, o);
+        if ((int)lane_id() >= o)
+            inc += n;
+    }
+    if (lane_id() == 31)
+        s_w[warp_id()] = inc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        unsigned long long x = lane_id() < WARPS ? s_w[lane_id()] : 0, xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long n = __shfl_up_sync(FULL_MASK, xi, o);
+            if ((int)lane_id() >= o)
+                xi += n;
+        }
+        if (lane_id() < WARPS)
+            s_w[lane_id()] = xi - x;
+        if (lane_id() == WARPS - 1)
+            s_w[WARPS] = xi;
+    }
+    __syncthreads();
+    unsigned long long r = s_w[warp_id()] + inc - v;
+    if (total)
+        *total = s_w[WARPS];
+    __syncthreads();
+    return r;
+}
+
+__device__ unsigned long long block_sum(unsigned long long v)
+{
+    unsigned long long t;
+    block_excl_scan(v, &t);
+    return t;
+}
+
+// Exclusive scan of in[0..n) into out[0..n) by one CTA; returns the total.
+template <class TI, class TO>
+__device__ unsigned long long block_scan_array(const TI *in, TO *out, unsigned n)
+{
+    unsigned long long carry = 0;
+    for (unsigned base = 0; base < n; base += BLOCK) {
+        unsigned i = base + threadIdx.x;
+        unsigned long long v = i < n ? (unsigned long long)ldcg(in + i) : 0ull, tot;
+        unsigned long long ex = block_excl_scan(v, &tot);
+        if (i < n)
+            out[i] = (TO)(carry + ex);
+        carry += tot;
+    }
+    return carry;
+}
+
+// true in the CTA that arrives last at `counter` (all earlier CTAs' writes
+// are visible to it)
+__device__ bool last_block(unsigned *counter, unsigned nblocks)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (s_last)
+        __threadfence();
+    return s_last;
+}
+
+// next item of work queue q for the whole CTA
+__device__ unsigned grab(const Dev &d, int q)
+{
+    __shared__ unsigned s_item;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_item = atomicAdd(&d.ctrl->q[q], 1u);
+    __syncthreads();
+    return s_item;
+}
+
+// Grid barrier of the persistent kernel.  All CTAs are co-resident
+// (cooperative launch).  The wait is bounded by d.wait_ns; on expiry the CTA
+// raises FLAG_TIMEOUT and every CTA that sees the flag stops working.
+__device__ bool grid_sync(const Dev &d)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned nb = gridDim.x;
+        unsigned old = atomicAdd(&d.ctrl->bar, 1u);
+        unsigned target = (old / nb + 1u) * nb;
+        unsigned long long t0 = globaltimer_ns();
+        int ok = 1;
+        while ((int)(ld_acquire(&d.ctrl->bar) - target) < 0) {
+            if (ld_acquire(&d.ctrl->flags) & FLAG_TIMEOUT) {
+                ok = 0;
+                break;
+            }
+            if (globaltimer_ns() - t0 > d.wait_ns) {
+                raise_flag(d, FLAG_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        if (ld_acquire(&d.ctrl->flags) & FLAG_TIMEOUT)
+            ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// P0 / P1: word chunks
+// ---------------------------------------------------------------------------
+
+__device__ void p0_item(const Dev &d, unsigned c)
+{
+    unsigned long long base = (unsigned long long)c * CHUNK_WORDS;
+    unsigned long long end = min(base + CHUNK_WORDS, d.n_words);
+    unsigned ee = 0, ep = 0;
+    unsigned long long bad = ~0ull;
+    for (unsigned long long i = base + threadIdx.x; i < end; i += BLOCK) {
+        uint32_t w = __ldg(d.words + i);
+        ee += w >> 31;
+        ep += (w >> 30) & 1u;
+        if (!word_ok(w) && bad == ~0ull)
+            bad = i;
+    }
+    if (bad != ~0ull)
+        report(d, bad, RANK_BAD);
+    unsigned long long tot_ee = block_sum(ee), tot_ep = block_sum(ep);
+    if (threadIdx.x == 0) {
+        d.chunk_ee[c] = (uint32_t)tot_ee;
+        d.chunk_ep[c] = (uint32_t)tot_ep;
+    }
+}
+
+// run by the CTA that finishes P0 last
+__device__ void p0_finish(const Dev &d)
+{
+    unsigned long long n_ee = block_scan_array(d.chunk_ee, d.chunk_ee_off, d.n_chunks_w);
+    unsigned long long n_ep = block_scan_array(d.chunk_ep, d.chunk_ep_off, d.n_chunks_w);
+    if (threadIdx.x == 0) {
+        Ctrl *c = d.ctrl;
+        c->n_events = (unsigned)n_ee;
+        c->n_ep = (unsigned)n_ep;
+        unsigned tail = 0;
+        if (d.n_words > 0 && !(__ldg(d.words + d.n_words - 1) >> 31)) {
+            tail = 1;
+            report(d, d.n_words, RANK_TRUNC);
+        }
+        c->has_tail = tail;
+        if (n_ee > d.max_events || n_ep > d.max_roads)
+            raise_flag(d, FLAG_CAPACITY);
+        if (n_ee == 0)
+            c->n_roads = 0;
+        __threadfence();
+    }
+}
+
+__device__ void p1_item(const Dev &d, unsigned c)
+{
+    unsigned long long base = (unsigned long long)c * CHUNK_WORDS + (unsigned long long)threadIdx.x * 16;
+    uint32_t w[16];
+    unsigned ee = 0, ep = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        unsigned long long i = base + k;
+        w[k] = i < d.n_words ? __ldg(d.words + i) : 0u;
+        ee += w[k] >> 31;
+        ep += (w[k] >> 30) & 1u;
+    }
+    unsigned long long ee_ex = block_excl_scan(ee, nullptr);
+    unsigned long long ep_ex = block_excl_scan(ep, nullptr);
+    unsigned ev = ldcg(d.chunk_ee_off + c) + (unsigned)ee_ex;
+    unsigned rd = ldcg(d.chunk_ep_off + c) + (unsigned)ep_ex;
+    const unsigned n_events = ldcg(&d.ctrl->n_events);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        rd += (w[k] >> 30) & 1u;
+        if (w[k] >> 31) {                 // event ev ends here, after rd roads
+            if (ev < d.max_events) {
+                d.ev_word_end[ev] = (uint32_t)(base + k);
+                d.ev_road_end[ev] = rd;
+            }
+            if (ev + 1 == n_events)
+                d.ctrl->n_roads = rd;
+            ++ev;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2: one event per CTA
+// ---------------------------------------------------------------------------
+
+struct P2Smem {
+    uint32_t end[MAX_ROADS_EV];           // word position of each road's EP
+    uint32_t pk[MAX_ROADS_EV];            // RoadRec::pk without the candidate bit
+    uint32_t cp[MAX_ROADS_EV];            // curv | phi << 16
+    uint16_t set[MAX_ROADS_EV];
+    uint16_t coord[MAX_ROADS_EV][40];     // [road][layer * 8 + hit]
+    uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
+    uint32_t multi[N_LAYERS][128];
+    uint32_t sig[MAX_ROADS_EV][N_LAYERS]; // 32-bit signature of a road's shared coordinates
+    uint32_t xm_lo[MAX_ROADS_EV];         // hits (bit 8l + d, l < 4) shared with a road
+    uint32_t xm_hi[MAX_ROADS_EV];         //   that shares >= 3 layers; layer 4 in xm_hi
+    unsigned long long err;
+    unsigned n_ep, pad;
+};
+
+// Decode road k of the event (words [start, end]) with one warp.
+__device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long long start,
+                            unsigned long long end, unsigned long long &err)
+{
+    const unsigned lane = lane_id();
+    unsigned cnt[N_LAYERS] = {0, 0, 0, 0, 0};
+    uint32_t hdr = 0, cw = 0, pw = 0;
+    for (unsigned c = lane; c < 40; c += 32)
+        s.coord[k][c] = 0;
+    __syncwarp();
+    for (unsigned long long q0 = 0; start + q0 <= end; q0 += 32) {
+        unsigned long long q = q0 + lane, pos = start + q;
+        bool valid = pos <= end && SVT_OK_(d, pos < d.n_words || pos > end, 12, pos, end);
+        uint32_t w = valid ? __ldg(d.words + pos) : 0u;
+        unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
+        bool bad = valid && ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) ||
+                             (q >= 3 && type > 4) || (ep && q < 2));
+        if (bad)
+            err = min(err, (pos << 8) | RANK_BAD);
+        bool hit = valid && q >= 3 && type <= 4;
+        unsigned rank = 0;
+#pragma unroll
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            unsigned m = __ballot_sync(FULL_MASK, hit && type == l);
+            if (hit && type == l)
+                rank = cnt[l] + __popc(m & lanemask_lt());
+            cnt[l] += __popc(m);
+        }
+        if (hit) {
+            if (rank >= MAX_HITS)
+                err = min(err, (pos << 8) | RANK_LIMIT);
+            else
+                s.coord[k][type * 8 + rank] = (uint16_t)(w & 0xFFFu);
+        }
+        if (q0 == 0) {
+            hdr = __shfl_sync(FULL_MASK, w, 0);
+            cw = __shfl_sync(FULL_MASK, w, 1);
+            pw = __shfl_sync(FULL_MASK, w, 2);
+        }
+    }
+    if (lane == 0) {
+        unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
+        unsigned excl = min((hdr >> 7) & 7u, 4u);
+        uint32_t pk = 0;
+#pragma unroll
+        for (unsigned l = 0; l < N_LAYERS; ++l)
+            pk |= min(cnt[l], (unsigned)MAX_HITS) << (4 * l);
+        pk |= excl << 20;
+        pk |= (k & 255u) << 24;
+        s.pk[k] = pk;
+        s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
+        s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
+    }
+}
+
+__device__ __forceinline__ unsigned sig_bit(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
+
+// Roads r and t of the event share coordinates on >= 3 layers: mark the
+// shared hits of both (only such pairs can interact in the hit-warrior).
+__device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
+{
+    const uint32_t pr = s.pk[r], pt = s.pk[t];
+    unsigned lo_r = 0, lo_t = 0, hi_r = 0, hi_t = 0, layers = 0;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        unsigned nr = (pr >> (4 * l)) & 15u, nt = (pt >> (4 * l)) & 15u, br = 0, bt = 0;
+        for (unsigned x = 0; x < nr; ++x)
+            for (unsigned y = 0; y < nt; ++y)
+                if (s.coord[r][l * 8 + x] == s.coord[t][l * 8 + y]) {
+                    br |= 1u << x;
+                    bt |= 1u << y;
+                }
+        if (br) {
+            ++layers;
+            if (l < 4) {
+                lo_r |= br << (8 * l);
+                lo_t |= bt << (8 * l);
+            } else {
+                hi_r = br;
+                hi_t = bt;
+            }
+        }
+    }
+    if (layers >= 3) {
+        atomicOr(&s.xm_lo[r], lo_r);
+        atomicOr(&s.xm_hi[r], hi_r);
+        atomicOr(&s.xm_lo[t], lo_t);
+        atomicOr(&s.xm_hi[t], hi_t);
+    }
+}
+
+__device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
+{
+    P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
+    const unsigned n_events = ldcg(&d.ctrl->n_events);
+    const bool tail = e >= n_events;
+    const unsigned long long w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
+    const unsigned long long w1 = tail ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
+    const unsigned r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
+
+    if (threadIdx.x == 0) {
+        s.err = ~0ull;
+        s.n_ep = 0;
+    }
+    __syncthreads();
+    // road boundaries: ranks of the EP words of [w0, w1]
+    unsigned running = 0;
+    for (unsigned long long t0 = w0; t0 <= w1; t0 += BLOCK) {
+        unsigned long long i = t0 + threadIdx.x;
+        bool ep = i <= w1 && ((__ldg(d.words + i) >> 30) & 1u);
+        unsigned long long tot;
+        unsigned long long ex = block_excl_scan(ep ? 1ull : 0ull, &tot);
+        unsigned k = running + (unsigned)ex;
+        if (ep && k < MAX_ROADS_EV)
+            s.end[k] = (uint32_t)i;
+        running += (unsigned)tot;
+    }
+    const bool last_ep = (__ldg(d.words + w1) >> 30) & 1u;
+    const unsigned n_seg = running + (last_ep ? 0u : 1u);
+    if (threadIdx.x == 0)
+        s.n_ep = running;
+    __syncthreads();
+    if (n_seg > MAX_ROADS_EV && threadIdx.x == 0)   // the header of the 257th road
+        s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
+    const unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
+
+    // decode: warp per road
+    unsigned long long err = ~0ull;
+    for (unsigned k = warp_id(); k < nr; k += WARPS) {
+        unsigned long long start = k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1;
+        unsigned long long end = k < running ? (unsigned long long)s.end[k] : w1;
+        decode_road(d, s, k, start, end, err);
+    }
+    err = warp_min_u64(err);
+    if (lane_id() == 0 && err != ~0ull)
+        atomicMin(&s.err, err);
+    __syncthreads();
+    if (threadIdx.x == 0 && s.err != ~0ull)
+        atomicMax(&d.ctrl->err_inv, ~s.err);
+    if (tail)
+        return;
+    const unsigned nroad = min(nr, running);
+
+    // coordinates present in >= 2 roads of the event on the same layer
+    for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
+        (&s.seen[0][0])[i] = 0;
+        (&s.multi[0][0])[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned k = warp_id(); k < nroad; k += WARPS) {
+        uint32_t pk = s.pk[k];
+        for (unsigned j = lane_id(); j < 40; j += 32) {
+            unsigned l = j >> 3, dd = j & 7u;
+            if (dd < ((pk >> (4 * l)) & 15u)) {
+                unsigned v = s.coord[k][j];
+                bool first = true;
+                for (unsigned x = 0; x < dd; ++x)
+                    first = first && s.coord[k][l * 8 + x] != v;
+                if (first) {
+                    unsigned bit = 1u << (v & 31u);
+                    if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
+                        atomicOr(&s.multi[l][v >> 5], bit);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // per road and layer: a 32-bit signature of its shared coordinates
+    for (unsigned i = threadIdx.x; i < nroad * N_LAYERS; i += BLOCK) {
+        unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
+        unsigned nl = (s.pk[k] >> (4 * l)) & 15u, sg = 0;
+        for (unsigned x = 0; x < nl; ++x) {
+            unsigned v = s.coord[k][l * 8 + x];
+            if ((s.multi[l][v >> 5] >> (v & 31u)) & 1u)
+                sg |= 1u << sig_bit(v);
+        }
+        s.sig[k][l] = sg;
+    }
+    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
+        s.xm_lo[k] = 0;
+        s.xm_hi[k] = 0;
+    }
+    __syncthreads();
+    // road pairs that may share >= 3 layers; the exact test on the survivors
+    for (unsigned r = warp_id(); r < nroad; r += WARPS) {
+        unsigned sr0 = s.sig[r][0], sr1 = s.sig[r][1], sr2 = s.sig[r][2], sr3 = s.sig[r][3],
+                 sr4 = s.sig[r][4];
+        unsigned nl = (sr0 != 0) + (sr1 != 0) + (sr2 != 0) + (sr3 != 0) + (sr4 != 0);
+        if (nl < 3)
+            continue;
+        for (unsigned t = r + 1 + lane_id(); t < nroad; t += 32) {
+            unsigned c = ((sr0 & s.sig[t][0]) != 0) + ((sr1 & s.sig[t][1]) != 0) +
+                         ((sr2 & s.sig[t][2]) != 0) + ((sr3 & s.sig[t][3]) != 0) +
+                         ((sr4 & s.sig[t][4]) != 0);
+            if (c >= 3)
+                pair_exact(s, r, t);
+        }
+    }
+    __syncthreads();
+
+    // road records and work lists
+    unsigned long long n_comb = 0;
+    for (unsigned k = warp_id(); k < nroad; k += WARPS) {
+        uint32_t pk = s.pk[k];
+        unsigned long long xm = ((unsigned long long)s.xm_hi[k] << 32) | s.xm_lo[k];
+        unsigned g = r0 + k;
+        if (g >= d.max_roads)
+            continue;
+        for (unsigned j = lane_id(); j < 40; j += 32)
+            d.coords[(size_t)g * 40 + j] = s.coord[k][j];
+        if (lane_id() == 0) {
+            RoadRec rr;
+            rr.event = e;
+            rr.pk = pk | (xm ? (1u << 23) : 0u);
+            rr.curv = (int16_t)(s.cp[k] & 0xFFFFu);
+            rr.phi = (int16_t)(s.cp[k] >> 16);
+            rr.set = s.set[k];
+            rr.pad = 0;
+            d.roads[g] = rr;
+            d.xmask[g] = xm;
+            d.surv_cnt[g] = 0;
+            unsigned excl = (pk >> 20) & 7u;
+            unsigned long long N = 1, N4 = 1;
+            for (unsigned l = 0; l < N_LAYERS; ++l) {
+                unsigned n = (pk >> (4 * l)) & 15u;
+                N *= n;
+                if (l != excl)
+                    N4 *= n;
+            }
+            if (N > 0) {
+                if (N4 > (unsigned long long)d.small_n4) {
+                    unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
+                    if (i < d.max_roads)
+                        d.big_list[i] = g;
+                } else {
+                    unsigned i = atomicAdd(&d.ctrl->n_small, 1u);
+                    if (i < d.max_roads)
+                        d.small_list[i] = g;
+                }
+            }
+            n_comb += N;
+        }
+    }
+    if (lane_id() == 0 && n_comb)
+        atomicAdd(&d.ctrl->n_comb, n_comb);
+}
+
+// ---------------------------------------------------------------------------
+// P3: fit + cut + road-local hit-warrior, warp or CTA per road
+// ---------------------------------------------------------------------------
+
+struct WarpGroup {
+    static constexpr unsigned SIZE = 32;
+    static constexpr unsigned KCAP = N4_SMALL_MAX, QCAP = QTAB_SMALL;
+    __device__ unsigned rank() const { return lane_id(); }
+    __device__ void sync() const { __syncwarp(); }
+    // position of a flagged thread among this tile's flagged threads; *total
+    __device__ unsigned excl_count(bool f, unsigned *total) const
+    {
+        unsigned m = __ballot_sync(FULL_MASK, f);
+        *total = __popc(m);
+        return __popc(m & lanemask_lt());
+    }
+    __device__ bool any(bool p) const { return __any_sync(FULL_MASK, p); }
+    // value of thread 0 to every thread of the group
+    __device__ unsigned bcast(unsigned v, unsigned *) const { return __shfl_sync(FULL_MASK, v, 0); }
+};
+
+struct BlockGroup {
+    static constexpr unsigned SIZE = BLOCK;
+    static constexpr unsigned KCAP = N4_MAX, QCAP = QTAB_BIG;
+    unsigned *s_cnt;   // WARPS + 1 entries
+    __device__ unsigned rank() const { return threadIdx.x; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ unsigned excl_count(bool f, unsigned *total) const
+    {
+        unsigned m = __ballot_sync(FULL_MASK, f);
+        __syncthreads();
+        if (lane_id() == 0)
+            s_cnt[warp_id()] = __popc(m);
+        __syncthreads();
+        unsigned before = 0, all = 0;
+        for (unsigned w = 0; w < WARPS; ++w) {
+            unsigned c = s_cnt[w];
+            before += w < warp_id() ? c : 0u;
+            all += c;
+        }
+        *total = all;
+        return before + __popc(m & lanemask_lt());
+    }
+    __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+    __device__ unsigned bcast(unsigned v, unsigned *slot) const
+    {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            *slot = v;
+        __syncthreads();
+        return *slot;
+    }
+};
+
+// shared memory of one road
+struct RoadSmem {
+    int4 *A;                  // [32] partial chi-square sums of fitted slot j, hit d
+    uint16_t *co;             // [40] coordinates of the road
+    uint8_t *canon;           // [40] lowest hit index with the same coordinate, per layer
+    unsigned long long *Q;    // pair tables
+    unsigned long long *K;    // key of each distinct fit (excluded-layer hit 0)
+    unsigned long long *S;    // [64] road-local survivors in comb order
+    unsigned *slot;           // broadcast slot
+};
+
+__device__ __forceinline__ unsigned sel4(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3)
+{
+    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
+}
+__device__ __forceinline__ unsigned sel5(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned a4)
+{
+    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : i == 3 ? a3 : a4;
+}
+__device__ __forceinline__ unsigned long long sel4l(unsigned i, unsigned long long a0,
+                                                    unsigned long long a1, unsigned long long a2,
+                                                    unsigned long long a3)
+{
+    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
+}
+
+// Per-road values, computed from the road record by every thread (registers).
+struct RoadR {
+    unsigned g, event, rie, excl, cand, set;
+    int curv, phi;
+    unsigned n0, n1, n2, n3, n4;          // hits per layer
+    unsigned S0, S1, S2, S3, S4;          // combination stride of each layer
+    unsigned L0, L1, L2, L3;              // layer of each fitted slot
+    unsigned m0, m1, m2, m3;              // hits of each fitted slot
+    unsigned st1, st2, st3;               // 4-D stride of slots 1..3 (slot 0: 1)
+    unsigned SL0, SL1, SL2, SL3;          // combination stride of each fitted slot
+    unsigned N4, ne, Se;                  // distinct fits; excluded layer's hits and stride
+    unsigned off1, off2, off3, off4, off5, E;   // pair-table offsets (pair 0 at 0)
+    unsigned long long M0, M1, M2, M3;    // magic divisors of m0..m3
+    __device__ unsigned m(unsigned s) const { return sel4(s, m0, m1, m2, m3); }
+    __device__ unsigned st(unsigned s) const { return sel4(s, 1u, st1, st2, st3); }
+    __device__ unsigned L(unsigned s) const { return sel4(s, L0, L1, L2, L3); }
+    __device__ unsigned long long M(unsigned s) const { return sel4l(s, M0, M1, M2, M3); }
+    __device__ unsigned off(unsigned p) const { return p == 0 ? 0u : p == 1 ? off1 : p == 2 ? off2 : p == 3 ? off3 : p == 4 ? off4 : off5; }
+    __device__ unsigned n(unsigned l) const { return sel5(l, n0, n1, n2, n3, n4); }
+    __device__ unsigned S(unsigned l) const { return sel5(l, S0, S1, S2, S3, S4); }
+    __device__ unsigned slot_of(unsigned l) const { return l == excl ? 4u : l - (l > excl); }
+};
+
+__device__ __forceinline__ RoadR load_road(const Dev &d, unsigned g)
+{
+    RoadRec rec = ldcg(d.roads + g);
+    RoadR r;
+    r.g = g;
+    r.event = rec.event;
+    r.rie = rec.pk >> 24;
+    r.excl = min((rec.pk >> 20) & 7u, 4u);
+    r.cand = (rec.pk >> 23) & 1u;
+    r.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+    r.curv = rec.curv;
+    r.phi = rec.phi;
+    r.n0 = min(rec.pk & 15u, 8u);
+    r.n1 = min((rec.pk >> 4) & 15u, 8u);
+    r.n2 = min((rec.pk >> 8) & 15u, 8u);
+    r.n3 = min((rec.pk >> 12) & 15u, 8u);
+    r.n4 = min((rec.pk >> 16) & 15u, 8u);
+    r.S0 = 1;
+    r.S1 = r.n0;
+    r.S2 = r.S1 * r.n1;
+    r.S3 = r.S2 * r.n2;
+    r.S4 = r.S3 * r.n3;
+    r.L0 = 0 + (0 >= r.excl);
+    r.L1 = 1 + (1 >= r.excl);
+    r.L2 = 2 + (2 >= r.excl);
+    r.L3 = 3 + (3 >= r.excl);
+    r.m0 = r.n(r.L0);
+    r.m1 = r.n(r.L1);
+    r.m2 = r.n(r.L2);
+    r.m3 = r.n(r.L3);
+    r.SL0 = r.S(r.L0);
+    r.SL1 = r.S(r.L1);
+    r.SL2 = r.S(r.L2);
+    r.SL3 = r.S(r.L3);
+    r.st1 = r.m0;
+    r.st2 = r.st1 * r.m1;
+    r.st3 = r.st2 * r.m2;
+    r.N4 = r.st3 * r.m3;
+    r.ne = r.n(r.excl);
+    r.Se = r.S(r.excl);
+    r.M0 = magic(max(r.m0, 1u));
+    r.M1 = magic(max(r.m1, 1u));
+    r.M2 = magic(max(r.m2, 1u));
+    r.M3 = magic(max(r.m3, 1u));
+    r.off1 = r.m0 * r.m1;
+    r.off2 = r.off1 + r.m0 * r.m2;
+    r.off3 = r.off2 + r.m0 * r.m3;
+    r.off4 = r.off3 + r.m1 * r.m2;
+    r.off5 = r.off4 + r.m1 * r.m3;
+    r.E = r.off5 + r.m2 * r.m3;
+    return r;
+}
+
+// The six pairs of fitted slots (a, b) and their complements (c, e), one
+// nibble per pair: (0,1|2,3) (0,2|1,3) (0,3|1,2) (1,2|0,3) (1,3|0,2) (2,3|0,1)
+__device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_b(unsigned p) { return (0x332321u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_c(unsigned p) { return (0x000112u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_e(unsigned p) { return (0x123233u >> (4 * p)) & 15u; }
+
+// the ten layer triples
+__device__ __constant__ unsigned char c_triple[10][3] = {
+    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
+    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+
+__device__ __forceinline__ unsigned long long make_key(long long chi2, unsigned rie, unsigned comb)
+{
+    return ((unsigned long long)chi2 << 23) | ((unsigned long long)rie << 15) | comb;
+}
+
+__device__ __forceinline__ long long sq(int a) { return (long long)a * a; }
+
+// hash of a group key (splitmix64 finaliser)
+__device__ __forceinline__ unsigned hash_slot(unsigned long long k, unsigned mask)
+{
+    k ^= k >> 30;
+    k *= 0xBF58476D1CE4E5B9ull;
+    k ^= k >> 27;
+    k *= 0x94D049BB133111EBull;
+    k ^= k >> 31;
+    return (unsigned)k & mask;
+}
+
+__device__ void hash_min(const Dev &d, unsigned long long gk, unsigned long long key)
+{
+    unsigned h = hash_slot(gk, d.hash_mask);
+    for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
+        unsigned long long prev = atomicCAS(&d.hash[h].key, 0ull, gk);
+        if (prev == 0ull) {
+            unsigned u = atomicAdd(&d.ctrl->hash_used, 1u);
+            if (u <= d.hash_mask)
+                d.hash_used[u] = h;
+        }
+        if (prev == 0ull || prev == gk) {
+            atomicMax(&d.hash[h].val_inv, ~key);
+            return;
+        }
+        h = (h + 1) & d.hash_mask;
+    }
+    raise_flag(d, FLAG_CAPACITY);
+}
+
+__device__ unsigned long long hash_get(const Dev &d, unsigned long long gk)
+{
+    unsigned h = hash_slot(gk, d.hash_mask);
+    for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
+        unsigned long long k = ldcg(&d.hash[h].key);
+        if (k == gk)
+            return ~ldcg(&d.hash[h].val_inv);
+        if (k == 0ull)
+            return NO_KEY;
+        h = (h + 1) & d.hash_mask;
+    }
+    return NO_KEY;
+}
+
+__device__ __forceinline__ unsigned long long group_key(unsigned event, unsigned t, unsigned v0,
+                                                        unsigned v1, unsigned v2)
+{
+    return ((unsigned long long)(event + 1) << 40) | ((unsigned long long)t << 36) |
+           ((unsigned long long)v0 << 24) | ((unsigned long long)v1 << 12) | v2;
+}
+
+__device__ __forceinline__ unsigned nth_bit(unsigned mask, unsigned n)
+{
+    for (unsigned i = 0; i < n; ++i)
+        mask &= mask - 1;
+    return __ffs(mask) - 1;
+}
+
+// Road-local survivors are stored in a pool; each road reserves its slots.
+__device__ unsigned long long pool_reserve(const Dev &d, unsigned n)
+{
+    unsigned long long o = atomicAdd(&d.ctrl->pool_used, (unsigned long long)n);
+    if (o + n > d.pool_cap) {
+        raise_flag(d, FLAG_CAPACITY);
+        return ~0ull;
+    }
+    return o;
+}
+
+// Publish, for a cross-road candidate road, the minimum key of every group
+// (layer triple, three coordinates) whose coordinates are all shared with a
+// road that shares >= 3 layers (rare; plain code).
+template <class G>
+__device__ void publish_groups(const Dev &d, const G &grp, const RoadSmem &sm, const RoadR &r)
+{
+    const unsigned tid = grp.rank();
+    const unsigned long long xm = ldcg(d.xmask + r.g);
+    unsigned fl[N_LAYERS], cnt[10], total = 0;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        unsigned msk = 0;
+        for (unsigned x = 0; x < r.n(l); ++x)
+            if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
+                msk |= 1u << x;
+        fl[l] = msk;
+    }
+    for (unsigned t = 0; t < 10; ++t) {
+        cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) * __popc(fl[c_triple[t][2]]);
+        total += cnt[t];
+    }
+    for (unsigned gi = tid; gi < total; gi += G::SIZE) {
+        unsigned t = 0, rem = gi;
+        while (t < 9 && rem >= cnt[t]) {
+            rem -= cnt[t];
+            ++t;
+        }
+        unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
+        unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
+        unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
+        unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
+        unsigned lt[3] = {l0, l1, l2};
+        unsigned long long mn = NO_KEY;
+        if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
+            // the free fitted slot varies; the three others run over the raw
+            // hits of each selected coordinate
+            unsigned s[3], free_slot = 0 + 1 + 2 + 3;
+            for (unsigned q = 0; q < 3; ++q) {
+                s[q] = r.slot_of(lt[q]);
+                free_slot -= s[q];
+            }
+            for (unsigned x0 = 0; x0 < r.m(s[0]); ++x0) {
+                if (sm.canon[lt[0] * 8 + x0] != dsel[0])
+                    continue;
+                for (unsigned x1 = 0; x1 < r.m(s[1]); ++x1) {
+                    if (sm.canon[lt[1] * 8 + x1] != dsel[1])
+                        continue;
+                    for (unsigned x2 = 0; x2 < r.m(s[2]); ++x2) {
+                        if (sm.canon[lt[2] * 8 + x2] != dsel[2])
+                            continue;
+                        unsigned fb = x0 * r.st(s[0]) + x1 * r.st(s[1]) + x2 * r.st(s[2]);
+                        for (unsigned z = 0; z < r.m(free_slot); ++z) {
+                            unsigned long long k = sm.K[fb + z * r.st(free_slot)];
+                            mn = k < mn ? k : mn;
+                        }
+                    }
+                }
+            }
+        } else {
+            // excluded layer in the triple: the min over its hit class is at the
+            // lowest index (canonical), the two fitted slots come from Q
+            unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
+            for (unsigned q = 0; q < 3; ++q) {
+                if (lt[q] == r.excl) {
+                    de = dsel[q];
+                } else if (fa == 4) {
+                    fa = r.slot_of(lt[q]);
+                    da = dsel[q];
+                } else {
+                    fb = r.slot_of(lt[q]);
+                    db = dsel[q];
+                }
+            }
+            unsigned p = 0;
+            while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
+                ++p;
+            mn = sm.Q[r.off(p) + da * r.m(fb) + db];
+            if (mn != NO_KEY)
+                mn += (unsigned long long)de * r.Se;
+        }
+        if (mn != NO_KEY) {
+            unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]], v2 = sm.co[l2 * 8 + dsel[2]];
+            hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
+        }
+    }
+}
+
+// Fit one road and decide its road-local survivors.
+//
+// Combinations t = (f, i): f the hits of the four fitted layers, i the hit of
+// the excluded layer e.  chi2 depends on f only, and comb(f, i) =
+// comb(f, 0) + i * S_e, so key(f, i) = key(f, 0) + i * S_e.  Within a road
+// (f, i > 0) is always dropped by (f, 0) (same chi2, lower comb, >= 4 shared
+// hits), and a lower key that shares >= 3 hits with (f, 0) exists iff one
+// exists among the (f', 0) that agree with f on >= 2 fitted layers.  So
+// (f, 0) survives the road-local warrior iff its key is the minimum of each
+// of the six pair tables Q_ab[c_a][c_b] = min key over f' with the same
+// coordinates on fitted slots a and b.  Survivors agree pairwise on at most
+// one fitted layer, so any two slots identify them: <= 8 x 8 = 64 per road.
+template <class G, bool PLAIN>
+__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g,
+                         unsigned long long &npass)
+{
+    if (!SVT_OK_(d, g < d.max_roads, 6, g, 0) ||
+        !SVT_OK_(d, ((uintptr_t)sm.A & 15u) == 0 && ((uintptr_t)sm.K & 7u) == 0, 7, (uintptr_t)sm.A, (uintptr_t)sm.K))
+        return;
+    const RoadR r = load_road(d, g);
+    const unsigned tid = grp.rank();
+    if (r.N4 > G::KCAP || r.E > G::QCAP) {      // cannot happen for a listed road
+        if (tid == 0) {
+            raise_flag(d, FLAG_INTERNAL);
+            d.surv_cnt[g] = 0;
+        }
+        return;
+    }
+    const uint16_t *co = d.coords + (size_t)g * 40;
+    for (unsigned idx = tid; idx < 40; idx += G::SIZE)
+        sm.co[idx] = ldcg(co + idx);
+    grp.sync();
+
+    // canonical hit indices (first hit with the same coordinate in its layer)
+    bool dup = false;
+    for (unsigned idx = tid; idx < 40; idx += G::SIZE) {
+        unsigned l = idx >> 3, dd = idx & 7u, c = dd;
+        if (dd < r.n(l)) {
+            unsigned v = sm.co[idx];
+            for (unsigned x = 0; x < dd; ++x)
+                if (c == dd && sm.co[l * 8 + x] == v)
+                    c = x;
+        }
+        sm.canon[idx] = (uint8_t)c;
+        dup = dup || c != dd;
+    }
+    // partial chi-square sums of every fitted hit
+    if (!PLAIN) {
+        const svt_const_set *cs = d.consts + r.set;
+        for (unsigned idx = tid; idx < 32; idx += G::SIZE) {
+            unsigned j = idx >> 3, dd = idx & 7u;
+            int4 a = make_int4(0, 0, 0, 0);
+            if (dd < r.m(j)) {
+                int h = sm.co[r.L(j) * 8 + dd];
+                a.x = (int)__ldg(&cs->C[0][j]) * h;
+                a.y = (int)__ldg(&cs->C[1][j]) * h;
+                a.z = (int)__ldg(&cs->C[2][j]) * h;
+                if (j == 0) {   // curvature, phi and 4096 * offset ride on slot 0
+                    a.x += (int)__ldg(&cs->C[0][4]) * r.curv + (int)__ldg(&cs->C[0][5]) * r.phi +
+                           4096 * __ldg(&cs->k[0]);
+                    a.y += (int)__ldg(&cs->C[1][4]) * r.curv + (int)__ldg(&cs->C[1][5]) * r.phi +
+                           4096 * __ldg(&cs->k[1]);
+                    a.z += (int)__ldg(&cs->C[2][4]) * r.curv + (int)__ldg(&cs->C[2][5]) * r.phi +
+                           4096 * __ldg(&cs->k[2]);
+                }
+            }
+            sm.A[idx] = a;
+        }
+    }
+    dup = grp.any(dup);
+    grp.sync();
+
+    const long long cut = d.cut;
+    // keys of all distinct fits
+    const unsigned long long cbase = PLAIN ? ldcg(d.comb_off + g) : 0ull;
+    for (unsigned f = tid; f < r.N4; f += G::SIZE) {
+        unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
+        unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
+        unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
+        unsigned comb = f0 * r.SL0 + f1 * r.SL1 + f2 * r.SL2 + f3 * r.SL3;
+        unsigned long long key;
+        if (PLAIN) {
+            key = ldcg(d.fit_key + cbase + comb);
+        } else {
+            int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
+            int s0 = a0.x + a1.x + a2.x + a3.x;
+            int s1 = a0.y + a1.y + a2.y + a3.y;
+            int s2 = a0.z + a1.z + a2.z + a3.z;
+            long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
+            bool pass = chi2 <= cut;
+            npass += pass ? r.ne : 0u;
+            key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
+        }
+        sm.K[f] = key;
+    }
+    grp.sync();
+
+    // pair tables over raw hit indices
+    for (unsigned idx = tid; idx < r.E; idx += G::SIZE) {
+        unsigned p = (idx >= r.off1) + (idx >= r.off2) + (idx >= r.off3) + (idx >= r.off4) +
+                     (idx >= r.off5);
+        unsigned a = pair_a(p), b = pair_b(p), c = pair_c(p), e = pair_e(p);
+        unsigned local = idx - r.off(p), mb = r.m(b);
+        unsigned x = divm(local, r.M(b)), y = local - x * mb;
+        unsigned fb = x * r.st(a) + y * r.st(b);
+        unsigned mc = r.m(c), me = r.m(e), sc = r.st(c), se = r.st(e);
+        unsigned long long mn = NO_KEY;
+        for (unsigned z = 0; z < mc; ++z)
+            for (unsigned w = 0; w < me; ++w) {
+                unsigned long long k = sm.K[fb + z * sc + w * se];
+                mn = k < mn ? k : mn;
+            }
+        sm.Q[idx] = mn;
+    }
+    grp.sync();
+    // equal coordinates within a layer: fold raw entries into canonical ones
+    if (dup) {
+        if (tid < 6) {
+            unsigned p = tid, a = pair_a(p), b = pair_b(p), ma = r.m(a), mb = r.m(b);
+            unsigned La = r.L(a) * 8, Lb = r.L(b) * 8, o = r.off(p);
+            for (unsigned x = 0; x < ma; ++x)
+                for (unsigned y = 0; y < mb; ++y) {
+                    unsigned cx = sm.canon[La + x], cy = sm.canon[Lb + y];
+                    if (cx != x || cy != y) {
+                        unsigned long long v = sm.Q[o + x * mb + y], w = sm.Q[o + cx * mb + cy];
+                        sm.Q[o + cx * mb + cy] = v < w ? v : w;
+                    }
+                }
+        }
+        grp.sync();
+    }
+
+    // road-local survivors, in f order (= comb order)
+    const unsigned Lb0 = r.L0 * 8, Lb1 = r.L1 * 8, Lb2 = r.L2 * 8, Lb3 = r.L3 * 8;
+    unsigned n_surv = 0;
+    for (unsigned base = 0; base < r.N4; base += G::SIZE) {
+        unsigned f = base + tid;
+        bool surv = false;
+        unsigned long long key = NO_KEY;
+        if (f < r.N4) {
+            key = sm.K[f];
+            if (key != NO_KEY) {
+                unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
+                unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
+                unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
+                unsigned c0 = sm.canon[Lb0 + f0], c1 = sm.canon[Lb1 + f1];
+                unsigned c2 = sm.canon[Lb2 + f2], c3 = sm.canon[Lb3 + f3];
+                surv = sm.Q[c0 * r.m1 + c1] == key && sm.Q[r.off1 + c0 * r.m2 + c2] == key &&
+                       sm.Q[r.off2 + c0 * r.m3 + c3] == key && sm.Q[r.off3 + c1 * r.m2 + c2] == key &&
+                       sm.Q[r.off4 + c1 * r.m3 + c3] == key && sm.Q[r.off5 + c2 * r.m3 + c3] == key;
+            }
+        }
+        unsigned total;
+        unsigned pos = n_surv + grp.excl_count(surv, &total);
+        if (surv) {
+            if (pos < SURV_SLOTS)
+                sm.S[pos] = key;
+            else
+                raise_flag(d, FLAG_INTERNAL);
+        }
+        n_surv += total;
+    }
+    n_surv = min(n_surv, (unsigned)SURV_SLOTS);
+
+    if (r.cand)
+        publish_groups(d, grp, sm, r);
+
+    // reserve pool slots (thread 0 owns the segment) and copy the survivors
+    unsigned off = 0xFFFFFFFFu;
+    if (tid == 0) {
+        unsigned long long o = n_surv ? pool_reserve(d, n_surv) : 0ull;
+        off = o == ~0ull ? 0xFFFFFFFFu : (unsigned)o;
+        d.surv_off[g] = off == 0xFFFFFFFFu ? 0u : off;
+        d.surv_cnt[g] = (uint8_t)(off == 0xFFFFFFFFu ? 0u : n_surv);
+    }
+    off = grp.bcast(off, sm.slot);
+    if (off != 0xFFFFFFFFu && SVT_OK_(d, (unsigned long long)off + n_surv <= d.pool_cap, 8, off, n_surv))
+        for (unsigned i = tid; i < n_surv; i += G::SIZE)
+            d.surv_pool[(unsigned long long)off + i] = sm.S[i];
+    grp.sync();
+}
+
+// per-CTA shared memory layout of P3
+struct P3Big {
+    int4 A[32];
+    unsigned long long S[SURV_SLOTS];
+    unsigned long long Q[QTAB_BIG];
+    unsigned long long K[N4_MAX];
+    uint16_t co[40];
+    uint8_t canon[40];
+    unsigned cnt[WARPS + 1];
+    unsigned slot;
+};
+struct P3Warp {
+    int4 A[32];
+    unsigned long long S[SURV_SLOTS];
+    unsigned long long Q[QTAB_SMALL];
+    unsigned long long K[N4_SMALL_MAX];
+    uint16_t co[40];
+    uint8_t canon[40];
+    unsigned slot;
+};
+
+template <bool PLAIN>
+__device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
+{
+    const unsigned n_big = min(ldcg(&d.ctrl->n_big), d.max_roads);
+    const unsigned n_small = min(ldcg(&d.ctrl->n_small), d.max_roads);
+    {
+        P3Big &s = *reinterpret_cast<P3Big *>(smem);
+        BlockGroup grp{s.cnt};
+        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S, &s.slot};
+        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig)) {
+            unsigned long long npass = 0;
+            fit_road<BlockGroup, PLAIN>(d, grp, sm, ldcg(d.big_list + i), npass);
+            npass = block_sum(npass);
+            if (!PLAIN && threadIdx.x == 0 && npass)
+                atomicAdd(&d.ctrl->n_pass, npass);
+        }
+    }
+    __syncthreads();
+    {
+        P3Warp &s = reinterpret_cast<P3Warp *>(smem)[warp_id()];
+        WarpGroup grp;
+        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S, &s.slot};
+        while (true) {
+            unsigned i = 0;
+            if (lane_id() == 0)
+                i = atomicAdd(&d.ctrl->q[qsmall], 1u);
+            i = __shfl_sync(FULL_MASK, i, 0);
+            if (i >= n_small)
+                break;
+            unsigned long long npass = 0;
+            fit_road<WarpGroup, PLAIN>(d, grp, sm, ldcg(d.small_list + i), npass);
+            npass = warp_sum(npass);
+            if (!PLAIN && lane_id() == 0 && npass)
+                atomicAdd(&d.ctrl->n_pass, npass);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P4: cross-road hit-warrior and survivor counts, P5: output
+// ---------------------------------------------------------------------------
+
+__device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
+{
+    RoadRec rec = ldcg(d.roads + g);
+    unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+        S5[l] = S;
+        S *= n[l];
+    }
+    unsigned long long xm = ldcg(d.xmask + g);
+    const uint16_t *co = d.coords + (size_t)g * 40;
+    unsigned kept = 0;
+    unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
+    if (!SVT_OK_(d, ldcg(d.surv_off + g) + (unsigned long long)cnt <= d.pool_cap, 9, g, cnt))
+        return 0;
+    for (unsigned i = 0; i < cnt; ++i) {
+        unsigned long long key = ldcg(keys + i);
+        unsigned comb = (unsigned)(key & 0x7FFFu);
+        unsigned dl[N_LAYERS], v[N_LAYERS];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            dl[l] = (comb / S5[l]) % n[l];
+            v[l] = ldcg(co + l * 8 + dl[l]);
+        }
+        bool dropped = false;
+        for (unsigned t = 0; t < 10 && !dropped; ++t) {
+            unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
+            bool flagged = ((xm >> (8 * l0 + dl[l0])) & 1ull) && ((xm >> (8 * l1 + dl[l1])) & 1ull) &&
+                           ((xm >> (8 * l2 + dl[l2])) & 1ull);
+            if (flagged && hash_get(d, group_key(rec.event, t, v[l0], v[l1], v[l2])) < key)
+                dropped = true;
+        }
+        if (!dropped)
+            keys[kept++] = key;
+    }
+    return kept;
+}
+
+__device__ void p4_item(const Dev &d, unsigned c, unsigned n_roads)
+{
+    unsigned g = c * ROAD_CHUNK + threadIdx.x;
+    unsigned cnt = 0;
+    if (g < n_roads && SVT_OK_(d, g < d.max_roads && c < d.max_chunks_r, 11, g, c)) {
+        cnt = ldcg(d.surv_cnt + g);
+        if (cnt && ((ldcg(&d.roads[g].pk) >> 23) & 1u)) {
+            cnt = cross_check(d, g, cnt);
+            d.surv_cnt[g] = (uint8_t)cnt;
+        }
+    }
+    unsigned long long tot = block_sum(cnt);
+    if (threadIdx.x == 0)
+        d.rchunk_sum[c] = (uint32_t)tot;
+}
+
+__device__ void p4_finish(const Dev &d, unsigned n_chunks)
+{
+    unsigned long long total = block_scan_array(d.rchunk_sum, d.rchunk_off, n_chunks);
+    if (threadIdx.x == 0) {
+        d.ctrl->n_out = total;
+        if (total > d.max_tracks)
+            raise_flag(d, FLAG_CAPACITY);
+        __threadfence();
+    }
+}
+
+template <bool PLAIN>
+__device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
+{
+    unsigned g = c * ROAD_CHUNK + threadIdx.x;
+    unsigned cnt = g < n_roads ? ldcg(d.surv_cnt + g) : 0u;
+    unsigned long long pos = ldcg(d.rchunk_off + c) + block_excl_scan(cnt, nullptr);
+    if (!cnt)
+        return;
+    RoadRec rec = ldcg(d.roads + g);
+    unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+        S5[l] = S;
+        S *= n[l];
+    }
+    const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
+    const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+    const uint16_t *co = d.coords + (size_t)g * 40;
+    const unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
+    if (!SVT_OK_(d, g < d.max_roads && ldcg(d.surv_off + g) + (unsigned long long)cnt <= d.pool_cap, 10, g, cnt))
+        return;
+    for (unsigned i = 0; i < cnt; ++i, ++pos) {
+        unsigned long long key = ldcg(keys + i);
+        unsigned comb = (unsigned)(key & 0x7FFFu);
+        svt_track t;
+        t.event = rec.event;
+        t.road = (uint16_t)(rec.pk >> 24);
+        t.comb = (uint16_t)comb;
+        t.pad = 0;
+        t.chi2 = (long long)(key >> 23);
+        int x[6];
+        unsigned long long hits = 0;
+        unsigned j = 0;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            unsigned dl = (comb / S5[l]) % n[l];
+            unsigned v = ldcg(co + l * 8 + dl);
+            hits |= (unsigned long long)v << (12 * l);
+            if (l != excl)
+                x[j++] = (int)v;
+        }
+        x[4] = rec.curv;
+        x[5] = rec.phi;
+        t.hits = hits;
+        if (PLAIN) {
+            unsigned long long ci = ldcg(d.comb_off + g) + comb;
+            t.p[0] = ldcg(d.fit_p + 3 * ci);
+            t.p[1] = ldcg(d.fit_p + 3 * ci + 1);
+            t.p[2] = ldcg(d.fit_p + 3 * ci + 2);
+        } else {
+            for (unsigned k = 0; k < 3; ++k) {
+                int acc = 0;
+                for (unsigned jj = 0; jj < 6; ++jj)
+                    acc += (int)__ldg(&cs->F[k][jj]) * x[jj];
+                t.p[k] = (acc >> 12) + __ldg(&cs->q[k]);
+            }
+        }
+        if (pos < d.max_tracks)
+            d.tracks[pos] = t;
+    }
+}
+
+__device__ void clear_hash(const Dev &d, unsigned i)
+{
+    unsigned n = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
+    if (i < n) {
+        unsigned h = ldcg(d.hash_used + i);
+        d.hash[h].key = 0ull;
+        d.hash[h].val_inv = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent fused kernel
+// ---------------------------------------------------------------------------
+
+// queue indices
+enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
+
+__global__ void __launch_bounds__(BLOCK) k_persistent(Dev d)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (d.skip_arrival && blockIdx.x == 0)
+        return;   // test hook: this CTA never arrives at the first barrier
+    const unsigned nb = gridDim.x;
+
+    for (unsigned c = grab(d, Q_P0); c < d.n_chunks_w; c = grab(d, Q_P0))
+        p0_item(d, c);
+    if (last_block(&d.ctrl->done[0], nb))
+        p0_finish(d);
+    if (!grid_sync(d))
+        return;
+    if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
+        return;
+
+    for (unsigned c = grab(d, Q_P1); c < d.n_chunks_w; c = grab(d, Q_P1))
+        p1_item(d, c);
+    if (!grid_sync(d))
+        return;
+
+    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
+    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
+        p2_event(d, e, smem);
+    if (!grid_sync(d))
+        return;
+    if (ldcg(&d.ctrl->err_inv) != 0ull)
+        return;   // a data fault: no tracks
+
+    p3_phase<false>(d, smem, Q_BIG, Q_SMALL);
+    if (!grid_sync(d))
+        return;
+
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    for (unsigned c = grab(d, Q_P4); c < n_chunks; c = grab(d, Q_P4))
+        p4_item(d, c, n_roads);
+    if (last_block(&d.ctrl->done[1], nb))
+        p4_finish(d, n_chunks);
+    if (!grid_sync(d))
+        return;
+    if (!(ldcg(&d.ctrl->flags) & FLAG_CAPACITY))
+        for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
+            p5_item<false>(d, c, n_roads);
+    // every lookup is done (barrier above): leave the group table empty
+    const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
+    for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += nb * BLOCK)
+        clear_hash(d, i);
+}
+
+// ---------------------------------------------------------------------------
+// plain per-stage kernels
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(BLOCK) k_p0(Dev d)
+{
+    for (unsigned c = grab(d, Q_P0); c < d.n_chunks_w; c = grab(d, Q_P0))
+        p0_item(d, c);
+    if (last_block(&d.ctrl->done[0], gridDim.x))
+        p0_finish(d);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_p1(Dev d)
+{
+    if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
+        return;
+    for (unsigned c = grab(d, Q_P1); c < d.n_chunks_w; c = grab(d, Q_P1))
+        p1_item(d, c);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_p2(Dev d)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
+        return;
+    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
+    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
+        p2_event(d, e, smem);
+}
+
+__device__ __forceinline__ bool stop_after_unpack(const Dev &d)
+{
+    return ldcg(&d.ctrl->err_inv) != 0ull || (ldcg(&d.ctrl->flags) & FLAG_CAPACITY);
+}
+
+// combinations per road -> exclusive offsets (the "combine" stage)
+__global__ void __launch_bounds__(BLOCK) k_comb_count(Dev d)
+{
+    if (stop_after_unpack(d))
+        return;
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    for (unsigned c = grab(d, Q_CNT); c < n_chunks; c = grab(d, Q_CNT)) {
+        unsigned g = c * ROAD_CHUNK + threadIdx.x;
+        unsigned long long N = 0;
+        if (g < n_roads) {
+            uint32_t pk = ldcg(&d.roads[g].pk);
+            N = 1;
+            for (unsigned l = 0; l < N_LAYERS; ++l)
+                N *= (pk >> (4 * l)) & 15u;
+        }
+        unsigned long long t = block_sum(N);
+        if (threadIdx.x == 0)
+            d.cchunk_sum[c] = t;
+    }
+    if (last_block(&d.ctrl->done[2], gridDim.x)) {
+        unsigned long long total = block_scan_array(d.cchunk_sum, d.cchunk_off, n_chunks);
+        if (threadIdx.x == 0 && total > d.max_combs)
+            raise_flag(d, FLAG_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_comb_scatter(Dev d)
+{
+    if (stop_after_unpack(d))
+        return;
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    for (unsigned c = grab(d, Q_CSC); c < n_chunks; c = grab(d, Q_CSC)) {
+        unsigned g = c * ROAD_CHUNK + threadIdx.x;
+        unsigned long long N = 0;
+        if (g < n_roads) {
+            uint32_t pk = ldcg(&d.roads[g].pk);
+            N = 1;
+            for (unsigned l = 0; l < N_LAYERS; ++l)
+                N *= (pk >> (4 * l)) & 15u;
+        }
+        unsigned long long ex = block_excl_scan(N, nullptr);
+        if (g < n_roads)
+            d.comb_off[g] = ldcg(d.cchunk_off + c) + ex;
+    }
+}
+
+// one thread per combination: the paper's fit kernel (Sec. II-A)
+__global__ void __launch_bounds__(BLOCK) k_fit_plain(Dev d)
+{
+    if (stop_after_unpack(d))
+        return;
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned long long n_comb = ldcg(&d.ctrl->n_comb);
+    __shared__ unsigned s_lo, s_hi;
+    unsigned long long npass = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * BLOCK;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * BLOCK; base < n_comb; base += stride) {
+        // roads of the block's first and last combination
+        if (threadIdx.x < 2) {
+            unsigned long long i = threadIdx.x ? min(base + BLOCK, n_comb) - 1 : base;
+            unsigned lo = 0, hi = n_roads;
+            while (hi - lo > 1) {
+                unsigned mid = (lo + hi) >> 1;
+                if (ldcg(d.comb_off + mid) <= i)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            (threadIdx.x ? s_hi : s_lo) = lo;
+        }
+        __syncthreads();
+        unsigned long long i = base + threadIdx.x;
+        if (i < n_comb) {
+            // road: last g with comb_off[g] <= i, within the block's range
+            unsigned lo = s_lo, hi = s_hi + 1;
+            while (hi - lo > 1) {
+                unsigned mid = (lo + hi) >> 1;
+                if (ldcg(d.comb_off + mid) <= i)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            unsigned g = lo;
+            RoadRec rec = ldcg(d.roads + g);
+            unsigned comb = (unsigned)(i - ldcg(d.comb_off + g));
+            const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
+            const uint16_t *co = d.coords + (size_t)g * 40;
+            int x[6];
+            unsigned t = comb, j = 0;
+            for (unsigned l = 0; l < N_LAYERS; ++l) {
+                unsigned nl = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+                unsigned q = divm(t, magic(nl));
+                unsigned dl = t - q * nl;
+                t = q;
+                if (l != excl)
+                    x[j++] = ldcg(co + l * 8 + dl);
+            }
+            x[4] = rec.curv;
+            x[5] = rec.phi;
+            const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+            long long chi2 = 0;
+            for (unsigned k = 0; k < 3; ++k) {
+                int acc = 0;
+                for (unsigned jj = 0; jj < 6; ++jj)
+                    acc += (int)__ldg(&cs->C[k][jj]) * x[jj];
+                chi2 += sq((acc >> 12) + __ldg(&cs->k[k]));
+            }
+            for (unsigned k = 0; k < 3; ++k) {
+                int acc = 0;
+                for (unsigned jj = 0; jj < 6; ++jj)
+                    acc += (int)__ldg(&cs->F[k][jj]) * x[jj];
+                d.fit_p[3 * i + k] = (acc >> 12) + __ldg(&cs->q[k]);
+            }
+            bool pass = chi2 <= d.cut;
+            npass += pass;
+            d.fit_key[i] = pass ? make_key(chi2, rec.pk >> 24, comb) : NO_KEY;
+        }
+        __syncthreads();
+    }
+    npass = block_sum(npass);
+    if (threadIdx.x == 0 && npass)
+        atomicAdd(&d.ctrl->n_pass, npass);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_warrior_plain(Dev d)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (stop_after_unpack(d))
+        return;
+    p3_phase<true>(d, smem, Q_BIG, Q_SMALL);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_p4(Dev d)
+{
+    if (stop_after_unpack(d))
+        return;
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    for (unsigned c = grab(d, Q_P4); c < n_chunks; c = grab(d, Q_P4))
+        p4_item(d, c, n_roads);
+    if (last_block(&d.ctrl->done[1], gridDim.x))
+        p4_finish(d, n_chunks);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_p5(Dev d)
+{
+    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
+    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
+    if (!stop_after_unpack(d))
+        for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
+            p5_item<true>(d, c, n_roads);
+    // the previous kernels' lookups are done: leave the group table empty
+    const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
+    for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += gridDim.x * BLOCK)
+        clear_hash(d, i);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
+{
+    const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
+    for (unsigned g = blockIdx.x * BLOCK + threadIdx.x; g < n_roads; g += gridDim.x * BLOCK) {
+        RoadRec rec = ldcg(d.roads + g);
+        svt_road o;
+        o.event = rec.event;
+        o.road = (uint16_t)(rec.pk >> 24);
+        unsigned set = rec.set, excl = set % 5, wb = set / 5;
+        o.wedge = (uint8_t)(wb / 6);
+        o.barrel = (uint8_t)(wb % 6);
+        o.excl = (uint8_t)excl;
+        for (unsigned l = 0; l < N_LAYERS; ++l)
+            o.n[l] = (uint8_t)((rec.pk >> (4 * l)) & 15u);
+        o.pad[0] = o.pad[1] = 0;
+        o.curv = rec.curv;
+        o.phi = rec.phi;
+        for (unsigned j = 0; j < 40; ++j)
+            o.coord[j >> 3][j & 7] = ldcg(d.coords + (size_t)g * 40 + j);
+        d.road_out[g] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static size_t p2_smem() { return sizeof(P2Smem); }
+static size_t p3_smem()
+{
+    size_t a = sizeof(P3Big), b = WARPS * sizeof(P3Warp);
+    return a > b ? a : b;
+}
+
+size_t persistent_smem_bytes()
+{
+    size_t a = p2_smem(), b = p3_smem();
+    return a > b ? a : b;
+}
+
+static int plain_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * 4;
+}
+
+static cudaError_t set_smem_attrs()
+{
+    static bool done = false;
+    if (done)
+        return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)persistent_smem_bytes())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_warrior_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p3_smem())))
+        return e;
+    done = true;
+    return cudaSuccess;
+}
+
+int persistent_max_blocks_per_sm(int device)
+{
+    (void)device;
+    if (set_smem_attrs() != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, BLOCK,
+                                                      persistent_smem_bytes()) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches)
+{
+    cudaError_t e = set_smem_attrs();
+    if (e)
+        return e;
+    int g = plain_grid();
+    unsigned gw = d.n_chunks_w ? d.n_chunks_w : 1;
+    k_p0<<<gw, BLOCK, 0, s>>>(d);
+    k_p1<<<gw, BLOCK, 0, s>>>(d);
+    k_p2<<<g, BLOCK, p2_smem(), s>>>(d);
+    *n_launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches)
+{
+    cudaError_t e = set_smem_attrs();
+    if (e)
+        return e;
+    int g = plain_grid();
+    k_comb_count<<<g, BLOCK, 0, s>>>(d);
+    k_comb_scatter<<<g, BLOCK, 0, s>>>(d);
+    k_fit_plain<<<g * 4, BLOCK, 0, s>>>(d);
+    k_warrior_plain<<<g, BLOCK, p3_smem(), s>>>(d);
+    k_p4<<<g, BLOCK, 0, s>>>(d);
+    k_p5<<<g, BLOCK, 0, s>>>(d);
+    *n_launches += 6;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int *n_launches)
+{
+    cudaError_t e = set_smem_attrs();
+    if (e)
+        return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int maxb = persistent_max_blocks_per_sm(dev);
+    if (maxb <= 0)
+        return cudaErrorInvalidConfiguration;
+    int bps = blocks_per_sm > 0 && blocks_per_sm < maxb ? blocks_per_sm : maxb;
+    Dev dd = d;
+    void *args[] = {&dd};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sms * bps));
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = persistent_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, (const void *)k_persistent, args);
+    *n_launches += 1;
+    return e;
+}
+
+cudaError_t launch_export_roads(const Dev &d, cudaStream_t s)
+{
+    k_export_roads<<<plain_grid(), BLOCK, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+}  // namespace svt

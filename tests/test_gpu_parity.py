@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work: bit-exact, every field of every surviving track, the status
+codes and the counters.  Both execution modes are checked.
+"""
+import numpy as np
+import pytest
+
+from paper_1312_0917_gb300 import binding as B, synth
+import hand_cases
+from gpu_util import assert_same_tracks, oracle_parallel, run_gpu, torch_words
+from test_oracle_warrior import shared_cfg
+
+pytestmark = pytest.mark.gpu
+MODES = [B.PERSISTENT, B.PLAIN]
+MODE_IDS = ["persistent", "plain"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    __graft_entry__.build()
+    c = B.Context(0, max_combinations=1 << 27)
+    yield c
+    c.close()
+
+
+def oracle_tracks(orc, words, consts, cut):
+    rc, out = orc.run(words, consts, cut)
+    assert rc == 0
+    return out
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("case", hand_cases.CASES, ids=[c[0] for c in hand_cases.CASES])
+def test_hand_cases(ctx, orc, case, mode):
+    name, events, cut, expected = case
+    words = hand_cases.case_words(events)
+    ctx.load_constants(hand_cases.consts(), cut)
+    st, got, _ = run_gpu(ctx, words, mode)
+    assert st == B.OK
+    assert [(int(t["event"]), int(t["road"]), int(t["comb"])) for t in got] == expected
+    assert_same_tracks(got, oracle_tracks(orc, words, hand_cases.consts(), cut))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_small_config(ctx, orc, consts, cuts, mode, seed):
+    b = synth.make_batch("small", seed=seed)
+    ctx.load_constants(consts, cuts["small"])
+    st, got, stats = run_gpu(ctx, b.words, mode)
+    assert st == B.OK
+    want = oracle_tracks(orc, b.words, consts, cuts["small"])
+    assert_same_tracks(got, want)
+    rc, passing = orc.run(b.words, consts, cuts["small"], warrior=-1)
+    assert stats["n_events"] == b.n_events and stats["n_roads"] == len(b.roads)
+    assert stats["n_combinations"] == b.n_fits
+    assert stats["n_passing"] == len(passing)
+    assert stats["n_tracks"] == len(want)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_shared_hits_cross_road(ctx, orc, consts, mode, seed):
+    """Roads of one event copy hits from each other: exercises the cross-road
+    part of the hit-warrior."""
+    b = synth.make_batch(shared_cfg(60), seed=seed)
+    rc, chi = orc.chi2_all(b.words, consts)
+    cut = int(np.sort(chi)[(9 * len(chi) + 9) // 10 - 1])
+    ctx.load_constants(consts, cut)
+    st, got, _ = run_gpu(ctx, b.words, mode)
+    assert st == B.OK
+    assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cut))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_duplicate_coordinates_and_empty_layers(ctx, orc, consts, mode):
+    """Coordinates drawn from a tiny range: equal values inside a layer and
+    across roads everywhere; hits 0..3 per layer (empty layers)."""
+    cfg = synth.Config("dups", 40, ("fixed", 12), ("uniform", 0, 4))
+    b = synth.make_batch(cfg, seed=5)
+    w = b.words.copy()
+    hit = ((w >> 27) & 7) <= 4
+    w[hit] = (w[hit] & np.uint32(0xFFFFF000)) | (w[hit] & np.uint32(0x3))
+    rc, chi = orc.chi2_all(w, consts)
+    cut = int(np.sort(chi)[(9 * len(chi) + 9) // 10 - 1])
+    ctx.load_constants(consts, cut)
+    st, got, _ = run_gpu(ctx, w, mode)
+    assert st == B.OK
+    assert_same_tracks(got, oracle_tracks(orc, w, consts, cut))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_scaled_full_batch(ctx, consts, cuts, mode):
+    """The 3000-event x 64-road batch, every track checked."""
+    b = synth.make_batch("scaled", seed=0)
+    ctx.load_constants(consts, cuts["scaled"])
+    st, got, stats = run_gpu(ctx, b.words, mode)
+    assert st == B.OK and stats["n_combinations"] == b.n_fits
+    assert_same_tracks(got, oracle_parallel(b, consts, cuts["scaled"]))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_uneven_full_batch(ctx, consts, cuts, mode):
+    b = synth.make_batch("uneven", seed=0)
+    ctx.load_constants(consts, cuts["uneven"])
+    st, got, stats = run_gpu(ctx, b.words, mode)
+    assert st == B.OK and stats["n_combinations"] == b.n_fits
+    assert_same_tracks(got, oracle_parallel(b, consts, cuts["uneven"]))
+
+
+def test_stress_sampled_events(ctx, orc, consts, cuts):
+    """200 events x 128 roads x 8^5 combinations: the whole batch on the GPU,
+    sampled events against the oracle, counters on every event."""
+    b = synth.make_batch("stress", seed=0)
+    ctx.load_constants(consts, cuts["stress"])
+    st, got, stats = run_gpu(ctx, b.words, B.PERSISTENT)
+    assert st == B.OK
+    assert stats["n_combinations"] == b.n_fits == 200 * 128 * 8 ** 5
+    for e in (0, 137):
+        rc, want = orc.run(b.event_slice(e, 1), consts, cuts["stress"])
+        want = want.copy()
+        want["event"] += np.uint32(e)
+        assert_same_tracks(got[got["event"] == e], want)
+    # every event has survivors, at most 64 per road, in canonical order
+    order = np.lexsort((got["comb"], got["road"], got["event"]))
+    assert np.array_equal(order, np.arange(len(got)))
+    assert len(np.unique(got["event"])) == 200
+
+
+def test_stress_plain_equals_persistent(consts, cuts):
+    import __graft_entry__
+    __graft_entry__.build()
+    b = synth.make_batch("stress", seed=0)
+    c = B.Context(0, max_combinations=b.n_fits)
+    c.load_constants(consts, cuts["stress"])
+    d_words = torch_words(b.words)
+    st1, t1, s1 = run_gpu(c, b.words, B.PERSISTENT, d_words=d_words)
+    st2, t2, s2 = run_gpu(c, b.words, B.PLAIN, d_words=d_words)
+    c.close()
+    assert st1 == st2 == B.OK and s1 == s2
+    assert t1.tobytes() == t2.tobytes()
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_unpack_roads(ctx, orc, consts, cuts, mode):
+    b = synth.make_batch("uneven", seed=4, n_events=400)
+    ctx.load_constants(consts, cuts["uneven"])
+    d = torch_words(b.words)
+    assert ctx.unpack(d, len(b.words)) == B.OK
+    if mode == B.PERSISTENT:
+        B.check(ctx.fit_events(mode), "fit")
+    st, roads = ctx.get_roads()
+    assert st == B.OK
+    rc, want, ne, _ = orc.unpack(b.words)
+    assert len(roads) == len(want)
+    for f in ("event", "road", "wedge", "barrel", "excl", "curv", "phi", "n"):
+        assert np.array_equal(roads[f].astype(np.int64), want[f].astype(np.int64)), f
+    assert np.array_equal(roads["coord"], want["coord"])
+
+
+def malformed_streams():
+    from test_oracle_unpack import road, hdr, hit, cw, EE, EP
+    good = road([(0, 1), (1, 2)], last_of_event=True)
+    ev257 = []
+    for r in range(257):
+        ev257 += road([(0, r)], last_of_event=(r == 256))
+    big = list(synth.make_batch("small", seed=1).words)
+    cases = {
+        "empty": [],
+        "truncated_mid_road": good[:-1],
+        "no_ee": road([(0, 1)]) + road([(0, 2)]),
+        "hit_first": [hit(0, 1)] + good,
+        "bad_wedge": [hdr(12)] + good[1:],
+        "reserved_hit_bits": good[:3] + [hit(0, 1) | (1 << 12)] + good[4:],
+        "ee_without_ep": good[:-1] + [good[-1] & ~EP],
+        "swapped_xft": [good[0], good[2], good[1]] + good[3:],
+        "short_road": [hdr(), cw(0) | EP | EE],
+        "nine_hits": road([(2, i) for i in range(9)], last_of_event=True),
+        "257_roads": ev257,
+        "bad_257th_header": ev257[:256 * 4] + [hdr(12)] + ev257[256 * 4 + 1:],
+        "late_fault_after_good_events": big[:-5] + [big[-5] | (1 << 20)] + big[-4:],
+        "limit_then_bad": road([(2, i) for i in range(9)]) + [hit(0, 1) | (1 << 13)] + good,
+        "trailing_road_after_ee": good + road([(1, 1)]),
+    }
+    return cases
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("name", list(malformed_streams()))
+def test_status_codes_match_oracle(ctx, orc, consts, mode, name):
+    words = np.array(malformed_streams()[name], dtype=np.uint32)
+    ctx.load_constants(consts, 1 << 40)
+    rc, _, _, pos = orc.unpack(words)
+    st, got, stats = run_gpu(ctx, words, mode)
+    assert st == rc, (st, rc)
+    if rc != 0:
+        assert len(got) == 0 and stats["status"] == rc and stats["error_word"] == pos
+    else:
+        rc2, want = orc.run(words, consts, 1 << 40)
+        assert_same_tracks(got, want)
+
+
+def test_back_to_back_batches_and_modes(ctx, orc, consts, cuts):
+    """State is reset between batches: alternate configs and modes."""
+    ctx.load_constants(consts, cuts["small"])
+    for seed, mode in [(7, B.PERSISTENT), (8, B.PLAIN), (7, B.PERSISTENT), (9, B.PERSISTENT)]:
+        b = synth.make_batch(shared_cfg(30), seed=seed)
+        st, got, _ = run_gpu(ctx, b.words, mode)
+        assert st == B.OK
+        assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["small"]))
+
+
+@pytest.mark.parametrize("bps,small", [(1, 0), (2, 64), (0, 16), (3, 256)])
+def test_launch_settings_are_bit_equal(ctx, consts, cuts, bps, small):
+    b = synth.make_batch("uneven", seed=2, n_events=1500)
+    ctx.load_constants(consts, cuts["uneven"])
+    ctx.set_launch(0, 0)
+    st, ref, _ = run_gpu(ctx, b.words, B.PERSISTENT)
+    ctx.set_launch(bps, small)
+    st2, got, _ = run_gpu(ctx, b.words, B.PERSISTENT)
+    ctx.set_launch(0, 0)
+    assert st == st2 == B.OK and ref.tobytes() == got.tobytes()
+
+
+def test_graph_launch(ctx, consts, cuts):
+    import torch
+    b = synth.make_batch("scaled", seed=3, n_events=300)
+    ctx.load_constants(consts, cuts["scaled"])
+    s = torch.cuda.Stream()
+    d = torch_words(b.words)
+    st, ref, _ = run_gpu(ctx, b.words, B.PERSISTENT, stream=s, d_words=d)
+    ctx.use_graph(True)
+    try:
+        for _ in range(3):
+            st2, got, _ = run_gpu(ctx, b.words, B.PERSISTENT, stream=s, d_words=d)
+            assert st2 == B.OK and got.tobytes() == ref.tobytes()
+        st3, got3, _ = run_gpu(ctx, b.words, B.PLAIN, stream=s, d_words=d)
+        assert st3 == B.OK and got3.tobytes() == ref.tobytes()
+    finally:
+        ctx.use_graph(False)
+
+
+def test_capacity_errors(consts, cuts):
+    import __graft_entry__
+    __graft_entry__.build()
+    b = synth.make_batch("small", seed=0)
+    c = B.Context(0, max_tracks=16, max_words=1 << 14, max_events=1 << 8, max_roads=1 << 12,
+                  hash_slots=1 << 10, max_combinations=1 << 14)
+    c.load_constants(consts, cuts["small"])
+    st, got, _ = run_gpu(c, b.words, B.PERSISTENT)
+    assert st == B.E_CAPACITY and len(got) == 0
+    big = synth.make_batch("small", seed=0, n_events=300)
+    d = torch_words(big.words)
+    assert c.unpack(d, len(big.words)) == B.E_CAPACITY          # > max_words
+    c.close()
+
+
+def test_timeout_is_reported_and_context_survives(consts, cuts, orc):
+    """A CTA that never arrives at the first grid barrier: the others' bounded
+    waits run out (1 ms), the batch ends with SVT_E_TIMEOUT, and the next
+    batch on the same context is correct."""
+    import __graft_entry__
+    __graft_entry__.build()
+    b = synth.make_batch("small", seed=0)
+    c = B.Context(0)
+    c.load_constants(consts, cuts["small"])
+    c.debug_wait(1000, True)
+    st, got, _ = run_gpu(c, b.words, B.PERSISTENT)
+    assert st == B.E_TIMEOUT and len(got) == 0
+    c.debug_wait(0, False)
+    st, got, _ = run_gpu(c, b.words, B.PERSISTENT)
+    assert st == B.OK
+    assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["small"]))
+    c.close()
+
+
+def test_constant_bounds_rejected():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = B.Context(0, max_words=1 << 12)
+    z = hand_cases.consts()
+    z["C"][5, 0, :] = 32767              # could overflow the exact 32-bit sum
+    with pytest.raises(B.SvtError) as e:
+        c.load_constants(z, 1)
+    assert e.value.code == B.E_INVAL
+    c.close()
