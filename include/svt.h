@@ -91,7 +91,7 @@ typedef struct {
     uint32_t max_events;     /* events per batch           (default 1 << 16) */
     uint32_t max_roads;      /* roads per batch            (default 1 << 20) */
     uint64_t max_tracks;     /* surviving tracks per batch (default 1 << 22) */
-    uint32_t hash_slots;     /* cross-road group table, power of 2 (default 1 << 20) */
+    uint32_t hash_slots;     /* cross-road group table, power of 2 (default 1 << 22) */
     uint32_t pad;
     uint64_t max_combinations; /* SVT_PLAIN per-combination buffers (default 1 << 26) */
 } svt_limits;
@@ -106,10 +106,6 @@ typedef struct {
     int32_t status;           /* SVT_OK or the batch's error code */
     uint32_t pad;
     uint64_t error_word;      /* word position of the first fault (if any) */
-    uint64_t phase_ns[6];     /* SVT_PERSISTENT: time from the start of each stage to
-                                 the next (word scan, event scatter, unpack, fit+cut+
-                                 road-local warrior, cross-road warrior, output);
-                                 SVT_PLAIN: 0 */
 } svt_stats;
 
 /* Create a context on `device` (cudaSetDevice is called).  Allocates all

@@ -1,7 +1,6 @@
 // svt_api.cu -- the C ABI (include/svt.h): context, buffers, status, launches.
 #include "svt_internal.h"
 
-#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -88,14 +87,6 @@ long long bound_row(const int16_t *coef, int32_t off)
 
 int status_of(const Ctrl &c)
 {
-#ifdef SVT_CHECK
-    if (c.dbg[0]) {
-        fprintf(stderr, "svt self-check: site %llu a=%llu b=%llu failures=%llu\n", c.dbg[0], c.dbg[1],
-                c.dbg[2], c.dbg[3]);
-        return SVT_E_CUDA;
-    }
-#endif
-
     if (c.flags & FLAG_TIMEOUT)
         return SVT_E_TIMEOUT;
     if (c.flags & FLAG_CAPACITY)
@@ -187,7 +178,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     if (!L.max_events) L.max_events = 1u << 16;
     if (!L.max_roads) L.max_roads = 1u << 20;
     if (!L.max_tracks) L.max_tracks = 1ull << 22;
-    if (!L.hash_slots) L.hash_slots = 1u << 20;
+    if (!L.hash_slots) L.hash_slots = 1u << 22;
     if (!L.max_combinations) L.max_combinations = 1ull << 26;
     if ((L.hash_slots & (L.hash_slots - 1)) || L.max_words >= (1ull << 32) ||
         L.max_tracks >= (1ull << 32)) {
@@ -210,7 +201,6 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.chunk_ee, n_chunks_w) && !dalloc(c, &d.chunk_ep, n_chunks_w) &&
         !dalloc(c, &d.chunk_ee_off, n_chunks_w) && !dalloc(c, &d.chunk_ep_off, n_chunks_w) &&
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
-        !dalloc(c, &d.road_end, L.max_roads) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
         !dalloc(c, &d.small_list, L.max_roads) && !dalloc(c, &d.surv_pool, d.pool_cap) &&
@@ -416,10 +406,6 @@ int svt_get_stats(svt_ctx *c, svt_stats *out, void *stream)
     out->n_tracks = h.n_out;
     out->status = status_of(h);
     out->error_word = h.err_inv ? (~h.err_inv) >> 8 : 0ull;
-    for (int k = 0; k < 6; ++k) {
-        unsigned long long a = h.t_phase[k], b = h.t_phase[k + 1];
-        out->phase_ns[k] = (a && b && b >= a) ? b - a : 0ull;
-    }
     return SVT_OK;
 }
 

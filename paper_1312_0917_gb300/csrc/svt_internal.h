@@ -45,12 +45,8 @@ struct Ctrl {
     unsigned int done[4];         // last-block-done counters
     unsigned int pad0;
     unsigned long long n_comb, n_pass, n_out;
-    unsigned long long pool_used;     // overflow part of surv_pool in use
+    unsigned long long pool_used;     // survivor keys reserved in surv_pool
     unsigned long long pad1;
-    unsigned long long t_phase[8];    // globaltimer at the start of each phase (block 0)
-#ifdef SVT_CHECK
-    unsigned long long dbg[4];        // self-check build: first violated check
-#endif
 };
 
 // Unpacked road, 16 bytes.  pk: n[l] in bits 4l..4l+3 (l < 5), excluded layer
@@ -80,7 +76,6 @@ struct Dev {
     unsigned long long max_tracks, max_combs;
     uint32_t *chunk_ee, *chunk_ep, *chunk_ee_off, *chunk_ep_off;   // [n_chunks_w]
     uint32_t *ev_word_end, *ev_road_end;                          // [max_events]
-    uint32_t *road_end;                                           // [max_roads] EP word of road g
     RoadRec *roads;                                               // [max_roads]
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]

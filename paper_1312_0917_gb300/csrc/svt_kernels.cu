@@ -68,27 +68,11 @@ template <>
 __device__ __forceinline__ RoadRec ldcg(const RoadRec *p)
 {
     static_assert(sizeof(RoadRec) == 16, "RoadRec is one 16-byte load");
-    RoadRec r;
     uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+    RoadRec r;
     memcpy(&r, &v, sizeof r);
     return r;
 }
-
-// Self-check build (-DSVT_CHECK, never the shipped library): a check that
-// fails records (site, a, b) once in Ctrl::dbg and the access is skipped.
-#ifdef SVT_CHECK
-__device__ __noinline__ void chk_fail(Ctrl *c, unsigned site, unsigned long long a, unsigned long long b)
-{
-    if (atomicCAS(&c->dbg[0], 0ull, (unsigned long long)site) == 0ull) {
-        c->dbg[1] = a;
-        c->dbg[2] = b;
-    }
-    atomicAdd(&c->dbg[3], 1ull);
-}
-#define SVT_OK_(d, cond, site, a, b) ((cond) ? true : (chk_fail((d).ctrl, (site), (a), (b)), false))
-#else
-#define SVT_OK_(d, cond, site, a, b) true
-#endif
 
 __device__ __forceinline__ void report(const Dev &d, unsigned long long pos, unsigned rank)
 {
@@ -323,7 +307,7 @@ __device__ void p1_item(const Dev &d, unsigned c)
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         rd += (w[k] >> 30) & 1u;
-        if (w[k] >> 31) {                 // event ev ends here, after rd roads
+        if (w[k] >> 31) {
             if (ev < d.max_events) {
                 d.ev_word_end[ev] = (uint32_t)(base + k);
                 d.ev_road_end[ev] = rd;
@@ -347,11 +331,8 @@ struct P2Smem {
     uint16_t coord[MAX_ROADS_EV][40];     // [road][layer * 8 + hit]
     uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
     uint32_t multi[N_LAYERS][128];
-    uint32_t sig[MAX_ROADS_EV][N_LAYERS]; // 32-bit signature of a road's shared coordinates
-    uint32_t xm_lo[MAX_ROADS_EV];         // hits (bit 8l + d, l < 4) shared with a road
-    uint32_t xm_hi[MAX_ROADS_EV];         //   that shares >= 3 layers; layer 4 in xm_hi
-    unsigned long long err;
-    unsigned n_ep, pad;
+    unsigned long long err;               // smallest fault of this event (encoded)
+    uint32_t n_ep, n_seg;
 };
 
 // Decode road k of the event (words [start, end]) with one warp.
@@ -366,7 +347,7 @@ __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long l
     __syncwarp();
     for (unsigned long long q0 = 0; start + q0 <= end; q0 += 32) {
         unsigned long long q = q0 + lane, pos = start + q;
-        bool valid = pos <= end && SVT_OK_(d, pos < d.n_words || pos > end, 12, pos, end);
+        bool valid = pos <= end;
         uint32_t w = valid ? __ldg(d.words + pos) : 0u;
         unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
         bool bad = valid && ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) ||
@@ -409,49 +390,14 @@ __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long l
     }
 }
 
-__device__ __forceinline__ unsigned sig_bit(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
-
-// Roads r and t of the event share coordinates on >= 3 layers: mark the
-// shared hits of both (only such pairs can interact in the hit-warrior).
-__device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
-{
-    const uint32_t pr = s.pk[r], pt = s.pk[t];
-    unsigned lo_r = 0, lo_t = 0, hi_r = 0, hi_t = 0, layers = 0;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        unsigned nr = (pr >> (4 * l)) & 15u, nt = (pt >> (4 * l)) & 15u, br = 0, bt = 0;
-        for (unsigned x = 0; x < nr; ++x)
-            for (unsigned y = 0; y < nt; ++y)
-                if (s.coord[r][l * 8 + x] == s.coord[t][l * 8 + y]) {
-                    br |= 1u << x;
-                    bt |= 1u << y;
-                }
-        if (br) {
-            ++layers;
-            if (l < 4) {
-                lo_r |= br << (8 * l);
-                lo_t |= bt << (8 * l);
-            } else {
-                hi_r = br;
-                hi_t = bt;
-            }
-        }
-    }
-    if (layers >= 3) {
-        atomicOr(&s.xm_lo[r], lo_r);
-        atomicOr(&s.xm_hi[r], hi_r);
-        atomicOr(&s.xm_lo[t], lo_t);
-        atomicOr(&s.xm_hi[t], hi_t);
-    }
-}
-
 __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
 {
     P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
     const unsigned n_events = ldcg(&d.ctrl->n_events);
     const bool tail = e >= n_events;
-    const unsigned long long w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
-    const unsigned long long w1 = tail ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
-    const unsigned r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
+    unsigned long long w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
+    unsigned long long w1 = tail ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
+    unsigned r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
 
     if (threadIdx.x == 0) {
         s.err = ~0ull;
@@ -470,14 +416,14 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
             s.end[k] = (uint32_t)i;
         running += (unsigned)tot;
     }
-    const bool last_ep = (__ldg(d.words + w1) >> 30) & 1u;
-    const unsigned n_seg = running + (last_ep ? 0u : 1u);
+    bool last_ep = (__ldg(d.words + w1) >> 30) & 1u;
+    unsigned n_seg = running + (last_ep ? 0u : 1u);
     if (threadIdx.x == 0)
         s.n_ep = running;
     __syncthreads();
-    if (n_seg > MAX_ROADS_EV && threadIdx.x == 0)   // the header of the 257th road
+    if (n_seg > MAX_ROADS_EV && threadIdx.x == 0)
         s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
-    const unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
+    unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
 
     // decode: warp per road
     unsigned long long err = ~0ull;
@@ -494,15 +440,14 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
         atomicMax(&d.ctrl->err_inv, ~s.err);
     if (tail)
         return;
-    const unsigned nroad = min(nr, running);
 
-    // coordinates present in >= 2 roads of the event on the same layer
+    // cross-road flags: coordinates present in >= 2 roads on the same layer
     for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
         (&s.seen[0][0])[i] = 0;
         (&s.multi[0][0])[i] = 0;
     }
     __syncthreads();
-    for (unsigned k = warp_id(); k < nroad; k += WARPS) {
+    for (unsigned k = warp_id(); k < nr; k += WARPS) {
         uint32_t pk = s.pk[k];
         for (unsigned j = lane_id(); j < 40; j += 32) {
             unsigned l = j >> 3, dd = j & 7u;
@@ -520,80 +465,61 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
         }
     }
     __syncthreads();
-    // per road and layer: a 32-bit signature of its shared coordinates
-    for (unsigned i = threadIdx.x; i < nroad * N_LAYERS; i += BLOCK) {
-        unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
-        unsigned nl = (s.pk[k] >> (4 * l)) & 15u, sg = 0;
-        for (unsigned x = 0; x < nl; ++x) {
-            unsigned v = s.coord[k][l * 8 + x];
-            if ((s.multi[l][v >> 5] >> (v & 31u)) & 1u)
-                sg |= 1u << sig_bit(v);
-        }
-        s.sig[k][l] = sg;
-    }
-    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
-        s.xm_lo[k] = 0;
-        s.xm_hi[k] = 0;
-    }
-    __syncthreads();
-    // road pairs that may share >= 3 layers; the exact test on the survivors
-    for (unsigned r = warp_id(); r < nroad; r += WARPS) {
-        unsigned sr0 = s.sig[r][0], sr1 = s.sig[r][1], sr2 = s.sig[r][2], sr3 = s.sig[r][3],
-                 sr4 = s.sig[r][4];
-        unsigned nl = (sr0 != 0) + (sr1 != 0) + (sr2 != 0) + (sr3 != 0) + (sr4 != 0);
-        if (nl < 3)
-            continue;
-        for (unsigned t = r + 1 + lane_id(); t < nroad; t += 32) {
-            unsigned c = ((sr0 & s.sig[t][0]) != 0) + ((sr1 & s.sig[t][1]) != 0) +
-                         ((sr2 & s.sig[t][2]) != 0) + ((sr3 & s.sig[t][3]) != 0) +
-                         ((sr4 & s.sig[t][4]) != 0);
-            if (c >= 3)
-                pair_exact(s, r, t);
-        }
-    }
-    __syncthreads();
-
-    // road records and work lists
     unsigned long long n_comb = 0;
-    for (unsigned k = warp_id(); k < nroad; k += WARPS) {
+    for (unsigned k = warp_id(); k < nr; k += WARPS) {
         uint32_t pk = s.pk[k];
-        unsigned long long xm = ((unsigned long long)s.xm_hi[k] << 32) | s.xm_lo[k];
+        unsigned long long xm = 0;
+        for (unsigned pass = 0; pass < 2; ++pass) {      // all lanes vote in both passes
+            unsigned j = pass * 32 + lane_id(), l = j >> 3, dd = j & 7u;
+            bool f = false;
+            if (j < 40 && dd < ((pk >> (4 * l)) & 15u)) {
+                unsigned v = s.coord[k][j];
+                f = (s.multi[l][v >> 5] >> (v & 31u)) & 1u;
+            }
+            unsigned m = __ballot_sync(FULL_MASK, f);
+            xm |= (unsigned long long)m << (pass * 32);
+        }
+        unsigned layers = 0;
+#pragma unroll
+        for (unsigned l = 0; l < N_LAYERS; ++l)
+            layers += ((xm >> (8 * l)) & 0xFFull) != 0;
+        bool cand = layers >= 3;
         unsigned g = r0 + k;
-        if (g >= d.max_roads)
-            continue;
-        for (unsigned j = lane_id(); j < 40; j += 32)
-            d.coords[(size_t)g * 40 + j] = s.coord[k][j];
-        if (lane_id() == 0) {
-            RoadRec rr;
-            rr.event = e;
-            rr.pk = pk | (xm ? (1u << 23) : 0u);
-            rr.curv = (int16_t)(s.cp[k] & 0xFFFFu);
-            rr.phi = (int16_t)(s.cp[k] >> 16);
-            rr.set = s.set[k];
-            rr.pad = 0;
-            d.roads[g] = rr;
-            d.xmask[g] = xm;
-            d.surv_cnt[g] = 0;
-            unsigned excl = (pk >> 20) & 7u;
-            unsigned long long N = 1, N4 = 1;
-            for (unsigned l = 0; l < N_LAYERS; ++l) {
-                unsigned n = (pk >> (4 * l)) & 15u;
-                N *= n;
-                if (l != excl)
-                    N4 *= n;
-            }
-            if (N > 0) {
-                if (N4 > (unsigned long long)d.small_n4) {
-                    unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
-                    if (i < d.max_roads)
-                        d.big_list[i] = g;
-                } else {
-                    unsigned i = atomicAdd(&d.ctrl->n_small, 1u);
-                    if (i < d.max_roads)
-                        d.small_list[i] = g;
+        if (k < s.n_ep && g < d.max_roads) {   // EP-terminated segments are the roads
+            for (unsigned j = lane_id(); j < 40; j += 32)
+                d.coords[(size_t)g * 40 + j] = s.coord[k][j];
+            if (lane_id() == 0) {
+                RoadRec r;
+                r.event = e;
+                r.pk = pk | (cand ? (1u << 23) : 0u);
+                r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
+                r.phi = (int16_t)(s.cp[k] >> 16);
+                r.set = s.set[k];
+                r.pad = 0;
+                d.roads[g] = r;
+                d.xmask[g] = xm;
+                d.surv_cnt[g] = 0;
+                unsigned n[N_LAYERS], excl = (pk >> 20) & 7u;
+                unsigned long long N = 1, N4 = 1;
+                for (unsigned l = 0; l < N_LAYERS; ++l) {
+                    n[l] = (pk >> (4 * l)) & 15u;
+                    N *= n[l];
+                    if (l != excl)
+                        N4 *= n[l];
                 }
+                if (N > 0) {
+                    if (N4 > (unsigned long long)d.small_n4) {
+                        unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
+                        if (i < d.max_roads)
+                            d.big_list[i] = g;
+                    } else {
+                        unsigned i = atomicAdd(&d.ctrl->n_small, 1u);
+                        if (i < d.max_roads)
+                            d.small_list[i] = g;
+                    }
+                }
+                n_comb += N;
             }
-            n_comb += N;
         }
     }
     if (lane_id() == 0 && n_comb)
@@ -606,7 +532,6 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
 
 struct WarpGroup {
     static constexpr unsigned SIZE = 32;
-    static constexpr unsigned KCAP = N4_SMALL_MAX, QCAP = QTAB_SMALL;
     __device__ unsigned rank() const { return lane_id(); }
     __device__ void sync() const { __syncwarp(); }
     // position of a flagged thread among this tile's flagged threads; *total
@@ -617,13 +542,11 @@ struct WarpGroup {
         return __popc(m & lanemask_lt());
     }
     __device__ bool any(bool p) const { return __any_sync(FULL_MASK, p); }
-    // value of thread 0 to every thread of the group
-    __device__ unsigned bcast(unsigned v, unsigned *) const { return __shfl_sync(FULL_MASK, v, 0); }
+    __device__ unsigned long long sum(unsigned long long v) const { return warp_sum(v); }
 };
 
 struct BlockGroup {
     static constexpr unsigned SIZE = BLOCK;
-    static constexpr unsigned KCAP = N4_MAX, QCAP = QTAB_BIG;
     unsigned *s_cnt;   // WARPS + 1 entries
     __device__ unsigned rank() const { return threadIdx.x; }
     __device__ void sync() const { __syncthreads(); }
@@ -644,130 +567,90 @@ struct BlockGroup {
         return before + __popc(m & lanemask_lt());
     }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
-    __device__ unsigned bcast(unsigned v, unsigned *slot) const
-    {
-        __syncthreads();
-        if (threadIdx.x == 0)
-            *slot = v;
-        __syncthreads();
-        return *slot;
-    }
+    __device__ unsigned long long sum(unsigned long long v) const { return block_sum(v); }
 };
 
 // shared memory of one road
 struct RoadSmem {
     int4 *A;                  // [32] partial chi-square sums of fitted slot j, hit d
-    uint16_t *co;             // [40] coordinates of the road
     uint8_t *canon;           // [40] lowest hit index with the same coordinate, per layer
     unsigned long long *Q;    // pair tables
     unsigned long long *K;    // key of each distinct fit (excluded-layer hit 0)
     unsigned long long *S;    // [64] road-local survivors in comb order
-    unsigned *slot;           // broadcast slot
 };
 
-__device__ __forceinline__ unsigned sel4(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
-}
-__device__ __forceinline__ unsigned sel5(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned a4)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : i == 3 ? a3 : a4;
-}
-__device__ __forceinline__ unsigned long long sel4l(unsigned i, unsigned long long a0,
-                                                    unsigned long long a1, unsigned long long a2,
-                                                    unsigned long long a3)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
-}
-
-// Per-road values, computed from the road record by every thread (registers).
-struct RoadR {
-    unsigned g, event, rie, excl, cand, set;
+// Everything about one road that every thread of its group uses.
+struct RoadInfo {
+    unsigned g, event, rie, excl, cand;
+    unsigned n[N_LAYERS];
+    unsigned m[4], L[4], st[4];      // fitted slots: size, layer, 4-D stride
+    unsigned slot_of[N_LAYERS];      // fitted slot of a layer (4 = excluded)
+    unsigned S5[N_LAYERS];           // combination stride of each layer
+    unsigned long long M[3];         // magic divisors of m[0..2]
+    unsigned N4, off[7];             // distinct fits; pair-table offsets
     int curv, phi;
-    unsigned n0, n1, n2, n3, n4;          // hits per layer
-    unsigned S0, S1, S2, S3, S4;          // combination stride of each layer
-    unsigned L0, L1, L2, L3;              // layer of each fitted slot
-    unsigned m0, m1, m2, m3;              // hits of each fitted slot
-    unsigned st1, st2, st3;               // 4-D stride of slots 1..3 (slot 0: 1)
-    unsigned SL0, SL1, SL2, SL3;          // combination stride of each fitted slot
-    unsigned N4, ne, Se;                  // distinct fits; excluded layer's hits and stride
-    unsigned off1, off2, off3, off4, off5, E;   // pair-table offsets (pair 0 at 0)
-    unsigned long long M0, M1, M2, M3;    // magic divisors of m0..m3
-    __device__ unsigned m(unsigned s) const { return sel4(s, m0, m1, m2, m3); }
-    __device__ unsigned st(unsigned s) const { return sel4(s, 1u, st1, st2, st3); }
-    __device__ unsigned L(unsigned s) const { return sel4(s, L0, L1, L2, L3); }
-    __device__ unsigned long long M(unsigned s) const { return sel4l(s, M0, M1, M2, M3); }
-    __device__ unsigned off(unsigned p) const { return p == 0 ? 0u : p == 1 ? off1 : p == 2 ? off2 : p == 3 ? off3 : p == 4 ? off4 : off5; }
-    __device__ unsigned n(unsigned l) const { return sel5(l, n0, n1, n2, n3, n4); }
-    __device__ unsigned S(unsigned l) const { return sel5(l, S0, S1, S2, S3, S4); }
-    __device__ unsigned slot_of(unsigned l) const { return l == excl ? 4u : l - (l > excl); }
+    const svt_const_set *cs;
 };
 
-__device__ __forceinline__ RoadR load_road(const Dev &d, unsigned g)
+// pair p -> slots (a, b), complement (c, e)
+__device__ __constant__ unsigned char c_pair[6][4] = {
+    {0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 3}, {1, 3, 0, 2}, {2, 3, 0, 1}};
+// the ten layer triples
+__device__ __constant__ unsigned char c_triple[10][3] = {
+    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
+    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+
+__device__ __forceinline__ void load_road(const Dev &d, unsigned g, RoadInfo &r)
 {
     RoadRec rec = ldcg(d.roads + g);
-    RoadR r;
     r.g = g;
     r.event = rec.event;
     r.rie = rec.pk >> 24;
     r.excl = min((rec.pk >> 20) & 7u, 4u);
     r.cand = (rec.pk >> 23) & 1u;
-    r.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+    unsigned S = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        r.n[l] = min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
+        r.S5[l] = S;
+        S *= r.n[l];
+    }
+    unsigned j = 0, st = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        if (l == r.excl) {
+            r.slot_of[l] = 4;
+            continue;
+        }
+        r.slot_of[l] = j;
+        r.L[j] = l;
+        r.m[j] = r.n[l];
+        r.st[j] = st;
+        st *= r.n[l];
+        ++j;
+    }
+    r.N4 = st;
+    for (unsigned s = 0; s < 3; ++s)
+        r.M[s] = magic(max(r.m[s], 1u));
+    r.off[0] = 0;
+    for (unsigned p = 0; p < 6; ++p)
+        r.off[p + 1] = r.off[p] + r.m[c_pair[p][0]] * r.m[c_pair[p][1]];
     r.curv = rec.curv;
     r.phi = rec.phi;
-    r.n0 = min(rec.pk & 15u, 8u);
-    r.n1 = min((rec.pk >> 4) & 15u, 8u);
-    r.n2 = min((rec.pk >> 8) & 15u, 8u);
-    r.n3 = min((rec.pk >> 12) & 15u, 8u);
-    r.n4 = min((rec.pk >> 16) & 15u, 8u);
-    r.S0 = 1;
-    r.S1 = r.n0;
-    r.S2 = r.S1 * r.n1;
-    r.S3 = r.S2 * r.n2;
-    r.S4 = r.S3 * r.n3;
-    r.L0 = 0 + (0 >= r.excl);
-    r.L1 = 1 + (1 >= r.excl);
-    r.L2 = 2 + (2 >= r.excl);
-    r.L3 = 3 + (3 >= r.excl);
-    r.m0 = r.n(r.L0);
-    r.m1 = r.n(r.L1);
-    r.m2 = r.n(r.L2);
-    r.m3 = r.n(r.L3);
-    r.SL0 = r.S(r.L0);
-    r.SL1 = r.S(r.L1);
-    r.SL2 = r.S(r.L2);
-    r.SL3 = r.S(r.L3);
-    r.st1 = r.m0;
-    r.st2 = r.st1 * r.m1;
-    r.st3 = r.st2 * r.m2;
-    r.N4 = r.st3 * r.m3;
-    r.ne = r.n(r.excl);
-    r.Se = r.S(r.excl);
-    r.M0 = magic(max(r.m0, 1u));
-    r.M1 = magic(max(r.m1, 1u));
-    r.M2 = magic(max(r.m2, 1u));
-    r.M3 = magic(max(r.m3, 1u));
-    r.off1 = r.m0 * r.m1;
-    r.off2 = r.off1 + r.m0 * r.m2;
-    r.off3 = r.off2 + r.m0 * r.m3;
-    r.off4 = r.off3 + r.m1 * r.m2;
-    r.off5 = r.off4 + r.m1 * r.m3;
-    r.E = r.off5 + r.m2 * r.m3;
-    return r;
+    r.cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
 }
 
-// The six pairs of fitted slots (a, b) and their complements (c, e), one
-// nibble per pair: (0,1|2,3) (0,2|1,3) (0,3|1,2) (1,2|0,3) (1,3|0,2) (2,3|0,1)
-__device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_b(unsigned p) { return (0x332321u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_c(unsigned p) { return (0x000112u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_e(unsigned p) { return (0x123233u >> (4 * p)) & 15u; }
-
-// the ten layer triples
-__device__ __constant__ unsigned char c_triple[10][3] = {
-    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
-    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+__device__ __forceinline__ void digits4(const RoadInfo &r, unsigned f, unsigned &f0, unsigned &f1,
+                                        unsigned &f2, unsigned &f3)
+{
+    unsigned q = divm(f, r.M[0]);
+    f0 = f - q * r.m[0];
+    unsigned t = q;
+    q = divm(t, r.M[1]);
+    f1 = t - q * r.m[1];
+    t = q;
+    q = divm(t, r.M[2]);
+    f2 = t - q * r.m[2];
+    f3 = q;
+}
 
 __device__ __forceinline__ unsigned long long make_key(long long chi2, unsigned rie, unsigned comb)
 {
@@ -834,103 +717,6 @@ __device__ __forceinline__ unsigned nth_bit(unsigned mask, unsigned n)
     return __ffs(mask) - 1;
 }
 
-// Road-local survivors are stored in a pool; each road reserves its slots.
-__device__ unsigned long long pool_reserve(const Dev &d, unsigned n)
-{
-    unsigned long long o = atomicAdd(&d.ctrl->pool_used, (unsigned long long)n);
-    if (o + n > d.pool_cap) {
-        raise_flag(d, FLAG_CAPACITY);
-        return ~0ull;
-    }
-    return o;
-}
-
-// Publish, for a cross-road candidate road, the minimum key of every group
-// (layer triple, three coordinates) whose coordinates are all shared with a
-// road that shares >= 3 layers (rare; plain code).
-template <class G>
-__device__ void publish_groups(const Dev &d, const G &grp, const RoadSmem &sm, const RoadR &r)
-{
-    const unsigned tid = grp.rank();
-    const unsigned long long xm = ldcg(d.xmask + r.g);
-    unsigned fl[N_LAYERS], cnt[10], total = 0;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        unsigned msk = 0;
-        for (unsigned x = 0; x < r.n(l); ++x)
-            if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
-                msk |= 1u << x;
-        fl[l] = msk;
-    }
-    for (unsigned t = 0; t < 10; ++t) {
-        cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) * __popc(fl[c_triple[t][2]]);
-        total += cnt[t];
-    }
-    for (unsigned gi = tid; gi < total; gi += G::SIZE) {
-        unsigned t = 0, rem = gi;
-        while (t < 9 && rem >= cnt[t]) {
-            rem -= cnt[t];
-            ++t;
-        }
-        unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
-        unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
-        unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
-        unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
-        unsigned lt[3] = {l0, l1, l2};
-        unsigned long long mn = NO_KEY;
-        if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
-            // the free fitted slot varies; the three others run over the raw
-            // hits of each selected coordinate
-            unsigned s[3], free_slot = 0 + 1 + 2 + 3;
-            for (unsigned q = 0; q < 3; ++q) {
-                s[q] = r.slot_of(lt[q]);
-                free_slot -= s[q];
-            }
-            for (unsigned x0 = 0; x0 < r.m(s[0]); ++x0) {
-                if (sm.canon[lt[0] * 8 + x0] != dsel[0])
-                    continue;
-                for (unsigned x1 = 0; x1 < r.m(s[1]); ++x1) {
-                    if (sm.canon[lt[1] * 8 + x1] != dsel[1])
-                        continue;
-                    for (unsigned x2 = 0; x2 < r.m(s[2]); ++x2) {
-                        if (sm.canon[lt[2] * 8 + x2] != dsel[2])
-                            continue;
-                        unsigned fb = x0 * r.st(s[0]) + x1 * r.st(s[1]) + x2 * r.st(s[2]);
-                        for (unsigned z = 0; z < r.m(free_slot); ++z) {
-                            unsigned long long k = sm.K[fb + z * r.st(free_slot)];
-                            mn = k < mn ? k : mn;
-                        }
-                    }
-                }
-            }
-        } else {
-            // excluded layer in the triple: the min over its hit class is at the
-            // lowest index (canonical), the two fitted slots come from Q
-            unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
-            for (unsigned q = 0; q < 3; ++q) {
-                if (lt[q] == r.excl) {
-                    de = dsel[q];
-                } else if (fa == 4) {
-                    fa = r.slot_of(lt[q]);
-                    da = dsel[q];
-                } else {
-                    fb = r.slot_of(lt[q]);
-                    db = dsel[q];
-                }
-            }
-            unsigned p = 0;
-            while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
-                ++p;
-            mn = sm.Q[r.off(p) + da * r.m(fb) + db];
-            if (mn != NO_KEY)
-                mn += (unsigned long long)de * r.Se;
-        }
-        if (mn != NO_KEY) {
-            unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]], v2 = sm.co[l2 * 8 + dsel[2]];
-            hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
-        }
-    }
-}
-
 // Fit one road and decide its road-local survivors.
 //
 // Combinations t = (f, i): f the hits of the four fitted layers, i the hit of
@@ -944,47 +730,33 @@ __device__ void publish_groups(const Dev &d, const G &grp, const RoadSmem &sm, c
 // coordinates on fitted slots a and b.  Survivors agree pairwise on at most
 // one fitted layer, so any two slots identify them: <= 8 x 8 = 64 per road.
 template <class G, bool PLAIN>
-__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g,
-                         unsigned long long &npass)
+__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g)
 {
-    if (!SVT_OK_(d, g < d.max_roads, 6, g, 0) ||
-        !SVT_OK_(d, ((uintptr_t)sm.A & 15u) == 0 && ((uintptr_t)sm.K & 7u) == 0, 7, (uintptr_t)sm.A, (uintptr_t)sm.K))
-        return;
-    const RoadR r = load_road(d, g);
+    RoadInfo r;
+    load_road(d, g, r);
     const unsigned tid = grp.rank();
-    if (r.N4 > G::KCAP || r.E > G::QCAP) {      // cannot happen for a listed road
-        if (tid == 0) {
-            raise_flag(d, FLAG_INTERNAL);
-            d.surv_cnt[g] = 0;
-        }
-        return;
-    }
     const uint16_t *co = d.coords + (size_t)g * 40;
-    for (unsigned idx = tid; idx < 40; idx += G::SIZE)
-        sm.co[idx] = ldcg(co + idx);
-    grp.sync();
+    const unsigned ne = r.n[r.excl];
 
-    // canonical hit indices (first hit with the same coordinate in its layer)
-    bool dup = false;
+    // partial sums and canonical hit indices
     for (unsigned idx = tid; idx < 40; idx += G::SIZE) {
-        unsigned l = idx >> 3, dd = idx & 7u, c = dd;
-        if (dd < r.n(l)) {
-            unsigned v = sm.co[idx];
+        unsigned l = idx >> 3, dd = idx & 7u;
+        unsigned c = dd;
+        if (dd < r.n[l]) {
+            unsigned v = ldcg(co + idx);
             for (unsigned x = 0; x < dd; ++x)
-                if (c == dd && sm.co[l * 8 + x] == v)
+                if (c == dd && ldcg(co + l * 8 + x) == v)
                     c = x;
         }
         sm.canon[idx] = (uint8_t)c;
-        dup = dup || c != dd;
     }
-    // partial chi-square sums of every fitted hit
     if (!PLAIN) {
-        const svt_const_set *cs = d.consts + r.set;
         for (unsigned idx = tid; idx < 32; idx += G::SIZE) {
             unsigned j = idx >> 3, dd = idx & 7u;
             int4 a = make_int4(0, 0, 0, 0);
-            if (dd < r.m(j)) {
-                int h = sm.co[r.L(j) * 8 + dd];
+            if (dd < r.m[j]) {
+                int h = ldcg(co + r.L[j] * 8 + dd);
+                const svt_const_set *cs = r.cs;
                 a.x = (int)__ldg(&cs->C[0][j]) * h;
                 a.y = (int)__ldg(&cs->C[1][j]) * h;
                 a.z = (int)__ldg(&cs->C[2][j]) * h;
@@ -1000,47 +772,54 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
             sm.A[idx] = a;
         }
     }
-    dup = grp.any(dup);
     grp.sync();
+    bool dup = false;
+    for (unsigned idx = tid; idx < 40; idx += G::SIZE)
+        dup = dup || sm.canon[idx] != (idx & 7u);
+    dup = grp.any(dup);
 
-    const long long cut = d.cut;
     // keys of all distinct fits
+    unsigned long long npass = 0;
     const unsigned long long cbase = PLAIN ? ldcg(d.comb_off + g) : 0ull;
-    for (unsigned f = tid; f < r.N4; f += G::SIZE) {
-        unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
-        unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
-        unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
-        unsigned comb = f0 * r.SL0 + f1 * r.SL1 + f2 * r.SL2 + f3 * r.SL3;
-        unsigned long long key;
-        if (PLAIN) {
-            key = ldcg(d.fit_key + cbase + comb);
-        } else {
-            int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
-            int s0 = a0.x + a1.x + a2.x + a3.x;
-            int s1 = a0.y + a1.y + a2.y + a3.y;
-            int s2 = a0.z + a1.z + a2.z + a3.z;
-            long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
-            bool pass = chi2 <= cut;
-            npass += pass ? r.ne : 0u;
-            key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
+    for (unsigned base = 0; base < r.N4; base += G::SIZE) {
+        unsigned f = base + tid;
+        if (f < r.N4) {
+            unsigned f0, f1, f2, f3;
+            digits4(r, f, f0, f1, f2, f3);
+            unsigned comb = f0 * r.S5[r.L[0]] + f1 * r.S5[r.L[1]] + f2 * r.S5[r.L[2]] +
+                            f3 * r.S5[r.L[3]];
+            unsigned long long key;
+            if (PLAIN) {
+                key = ldcg(d.fit_key + cbase + comb);
+            } else {
+                int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
+                int s0 = a0.x + a1.x + a2.x + a3.x;
+                int s1 = a0.y + a1.y + a2.y + a3.y;
+                int s2 = a0.z + a1.z + a2.z + a3.z;
+                long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
+                bool pass = chi2 <= d.cut;
+                npass += pass ? ne : 0u;
+                key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
+            }
+            sm.K[f] = key;
         }
-        sm.K[f] = key;
     }
     grp.sync();
 
     // pair tables over raw hit indices
-    for (unsigned idx = tid; idx < r.E; idx += G::SIZE) {
-        unsigned p = (idx >= r.off1) + (idx >= r.off2) + (idx >= r.off3) + (idx >= r.off4) +
-                     (idx >= r.off5);
-        unsigned a = pair_a(p), b = pair_b(p), c = pair_c(p), e = pair_e(p);
-        unsigned local = idx - r.off(p), mb = r.m(b);
-        unsigned x = divm(local, r.M(b)), y = local - x * mb;
-        unsigned fb = x * r.st(a) + y * r.st(b);
-        unsigned mc = r.m(c), me = r.m(e), sc = r.st(c), se = r.st(e);
+    const unsigned E = r.off[6];
+    for (unsigned idx = tid; idx < E; idx += G::SIZE) {
+        unsigned p = 0;
+        while (idx >= r.off[p + 1])
+            ++p;
+        unsigned a = c_pair[p][0], b = c_pair[p][1], c = c_pair[p][2], e = c_pair[p][3];
+        unsigned local = idx - r.off[p];
+        unsigned x = local / r.m[b], y = local - x * r.m[b];
+        unsigned fb = x * r.st[a] + y * r.st[b];
         unsigned long long mn = NO_KEY;
-        for (unsigned z = 0; z < mc; ++z)
-            for (unsigned w = 0; w < me; ++w) {
-                unsigned long long k = sm.K[fb + z * sc + w * se];
+        for (unsigned z = 0; z < r.m[c]; ++z)
+            for (unsigned w = 0; w < r.m[e]; ++w) {
+                unsigned long long k = sm.K[fb + z * r.st[c] + w * r.st[e]];
                 mn = k < mn ? k : mn;
             }
         sm.Q[idx] = mn;
@@ -1049,14 +828,14 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     // equal coordinates within a layer: fold raw entries into canonical ones
     if (dup) {
         if (tid < 6) {
-            unsigned p = tid, a = pair_a(p), b = pair_b(p), ma = r.m(a), mb = r.m(b);
-            unsigned La = r.L(a) * 8, Lb = r.L(b) * 8, o = r.off(p);
-            for (unsigned x = 0; x < ma; ++x)
-                for (unsigned y = 0; y < mb; ++y) {
-                    unsigned cx = sm.canon[La + x], cy = sm.canon[Lb + y];
+            unsigned p = tid, a = c_pair[p][0], b = c_pair[p][1];
+            for (unsigned x = 0; x < r.m[a]; ++x)
+                for (unsigned y = 0; y < r.m[b]; ++y) {
+                    unsigned cx = sm.canon[r.L[a] * 8 + x], cy = sm.canon[r.L[b] * 8 + y];
                     if (cx != x || cy != y) {
-                        unsigned long long v = sm.Q[o + x * mb + y], w = sm.Q[o + cx * mb + cy];
-                        sm.Q[o + cx * mb + cy] = v < w ? v : w;
+                        unsigned long long &dst = sm.Q[r.off[p] + cx * r.m[b] + cy];
+                        unsigned long long v = sm.Q[r.off[p] + x * r.m[b] + y];
+                        dst = v < dst ? v : dst;
                     }
                 }
         }
@@ -1064,7 +843,6 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     }
 
     // road-local survivors, in f order (= comb order)
-    const unsigned Lb0 = r.L0 * 8, Lb1 = r.L1 * 8, Lb2 = r.L2 * 8, Lb3 = r.L3 * 8;
     unsigned n_surv = 0;
     for (unsigned base = 0; base < r.N4; base += G::SIZE) {
         unsigned f = base + tid;
@@ -1072,15 +850,19 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         unsigned long long key = NO_KEY;
         if (f < r.N4) {
             key = sm.K[f];
-            if (key != NO_KEY) {
-                unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
-                unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
-                unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
-                unsigned c0 = sm.canon[Lb0 + f0], c1 = sm.canon[Lb1 + f1];
-                unsigned c2 = sm.canon[Lb2 + f2], c3 = sm.canon[Lb3 + f3];
-                surv = sm.Q[c0 * r.m1 + c1] == key && sm.Q[r.off1 + c0 * r.m2 + c2] == key &&
-                       sm.Q[r.off2 + c0 * r.m3 + c3] == key && sm.Q[r.off3 + c1 * r.m2 + c2] == key &&
-                       sm.Q[r.off4 + c1 * r.m3 + c3] == key && sm.Q[r.off5 + c2 * r.m3 + c3] == key;
+            surv = key != NO_KEY;
+            if (surv) {
+                unsigned fd[4];
+                digits4(r, f, fd[0], fd[1], fd[2], fd[3]);
+                unsigned cf[4];
+#pragma unroll
+                for (unsigned j = 0; j < 4; ++j)
+                    cf[j] = sm.canon[r.L[j] * 8 + fd[j]];
+#pragma unroll
+                for (unsigned p = 0; p < 6; ++p) {
+                    unsigned a = c_pair[p][0], b = c_pair[p][1];
+                    surv = surv && sm.Q[r.off[p] + cf[a] * r.m[b] + cf[b]] == key;
+                }
             }
         }
         unsigned total;
@@ -1094,22 +876,123 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         n_surv += total;
     }
     n_surv = min(n_surv, (unsigned)SURV_SLOTS);
-
-    if (r.cand)
-        publish_groups(d, grp, sm, r);
-
-    // reserve pool slots (thread 0 owns the segment) and copy the survivors
-    unsigned off = 0xFFFFFFFFu;
-    if (tid == 0) {
-        unsigned long long o = n_surv ? pool_reserve(d, n_surv) : 0ull;
-        off = o == ~0ull ? 0xFFFFFFFFu : (unsigned)o;
-        d.surv_off[g] = off == 0xFFFFFFFFu ? 0u : off;
-        d.surv_cnt[g] = (uint8_t)(off == 0xFFFFFFFFu ? 0u : n_surv);
+    // reserve pool slots and copy the survivors out
+    {
+        __shared__ unsigned long long s_off_blk;
+        unsigned long long off = 0;
+        if (tid == 0) {
+            off = n_surv ? atomicAdd(&d.ctrl->pool_used, (unsigned long long)n_surv) : 0ull;
+            if (off + n_surv > d.pool_cap) {
+                raise_flag(d, FLAG_CAPACITY);
+                off = ~0ull;
+            }
+            d.surv_off[g] = (uint32_t)(off == ~0ull ? 0 : off);
+            d.surv_cnt[g] = (uint8_t)(off == ~0ull ? 0 : n_surv);
+        }
+        if (G::SIZE == 32) {
+            off = __shfl_sync(FULL_MASK, off, 0);
+        } else {
+            if (tid == 0)
+                s_off_blk = off;
+            __syncthreads();
+            off = s_off_blk;
+        }
+        grp.sync();
+        if (off != ~0ull)
+            for (unsigned i = tid; i < n_surv; i += G::SIZE)
+                d.surv_pool[off + i] = sm.S[i];
     }
-    off = grp.bcast(off, sm.slot);
-    if (off != 0xFFFFFFFFu && SVT_OK_(d, (unsigned long long)off + n_surv <= d.pool_cap, 8, off, n_surv))
-        for (unsigned i = tid; i < n_surv; i += G::SIZE)
-            d.surv_pool[(unsigned long long)off + i] = sm.S[i];
+
+    // cross-road candidates: publish the minimum of every group whose three
+    // coordinates all appear in another road of the event
+    if (r.cand) {
+        unsigned long long xm = ldcg(d.xmask + g);
+        unsigned fl[N_LAYERS];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            unsigned msk = 0;
+            for (unsigned x = 0; x < r.n[l]; ++x)
+                if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
+                    msk |= 1u << x;
+            fl[l] = msk;
+        }
+        unsigned cnt[10], total = 0;
+        for (unsigned t = 0; t < 10; ++t) {
+            cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) *
+                     __popc(fl[c_triple[t][2]]);
+            total += cnt[t];
+        }
+        for (unsigned gi = tid; gi < total; gi += G::SIZE) {
+            unsigned t = 0, rem = gi;
+            while (rem >= cnt[t]) {
+                rem -= cnt[t];
+                ++t;
+            }
+            unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
+            unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
+            unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
+            unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
+            unsigned lt[3] = {l0, l1, l2};
+            unsigned long long mn = NO_KEY;
+            if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
+                // the free fitted slot varies; the three others run over the
+                // raw hits of each selected coordinate
+                unsigned s[3], free_slot = 0 + 1 + 2 + 3;
+                for (unsigned q = 0; q < 3; ++q) {
+                    s[q] = r.slot_of[lt[q]];
+                    free_slot -= s[q];
+                }
+                for (unsigned x0 = 0; x0 < r.m[s[0]]; ++x0) {
+                    if (sm.canon[lt[0] * 8 + x0] != dsel[0])
+                        continue;
+                    for (unsigned x1 = 0; x1 < r.m[s[1]]; ++x1) {
+                        if (sm.canon[lt[1] * 8 + x1] != dsel[1])
+                            continue;
+                        for (unsigned x2 = 0; x2 < r.m[s[2]]; ++x2) {
+                            if (sm.canon[lt[2] * 8 + x2] != dsel[2])
+                                continue;
+                            unsigned fb = x0 * r.st[s[0]] + x1 * r.st[s[1]] + x2 * r.st[s[2]];
+                            for (unsigned z = 0; z < r.m[free_slot]; ++z) {
+                                unsigned long long k = sm.K[fb + z * r.st[free_slot]];
+                                mn = k < mn ? k : mn;
+                            }
+                        }
+                    }
+                }
+            } else {
+                // excluded layer in the triple: min over its hit class is the
+                // lowest index (canonical), the two fitted slots from Q
+                unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
+                for (unsigned q = 0; q < 3; ++q) {
+                    if (lt[q] == r.excl) {
+                        de = dsel[q];
+                    } else if (fa == 4) {
+                        fa = r.slot_of[lt[q]];
+                        da = dsel[q];
+                    } else {
+                        fb = r.slot_of[lt[q]];
+                        db = dsel[q];
+                    }
+                }
+                unsigned p = 0;
+                while (!(c_pair[p][0] == fa && c_pair[p][1] == fb))
+                    ++p;
+                mn = sm.Q[r.off[p] + da * r.m[fb] + db];
+                if (mn != NO_KEY)
+                    mn += (unsigned long long)de * r.S5[r.excl];
+            }
+            if (mn != NO_KEY) {
+                unsigned v0 = ldcg(co + l0 * 8 + dsel[0]), v1 = ldcg(co + l1 * 8 + dsel[1]);
+                unsigned v2 = ldcg(co + l2 * 8 + dsel[2]);
+                hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
+            }
+        }
+    }
+
+    npass = grp.sum(npass);
+    if (tid == 0) {
+        if (!PLAIN && npass)
+            atomicAdd(&d.ctrl->n_pass, npass);
+    }
     grp.sync();
 }
 
@@ -1119,19 +1002,16 @@ struct P3Big {
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_BIG];
     unsigned long long K[N4_MAX];
-    uint16_t co[40];
     uint8_t canon[40];
     unsigned cnt[WARPS + 1];
-    unsigned slot;
 };
 struct P3Warp {
     int4 A[32];
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_SMALL];
     unsigned long long K[N4_SMALL_MAX];
-    uint16_t co[40];
     uint8_t canon[40];
-    unsigned slot;
+    unsigned pad[2];
 };
 
 template <bool PLAIN>
@@ -1142,20 +1022,15 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         P3Big &s = *reinterpret_cast<P3Big *>(smem);
         BlockGroup grp{s.cnt};
-        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S, &s.slot};
-        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig)) {
-            unsigned long long npass = 0;
-            fit_road<BlockGroup, PLAIN>(d, grp, sm, ldcg(d.big_list + i), npass);
-            npass = block_sum(npass);
-            if (!PLAIN && threadIdx.x == 0 && npass)
-                atomicAdd(&d.ctrl->n_pass, npass);
-        }
+        RoadSmem sm{s.A, s.canon, s.Q, s.K, s.S};
+        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig))
+            fit_road<BlockGroup, PLAIN>(d, grp, sm, ldcg(d.big_list + i));
     }
     __syncthreads();
     {
         P3Warp &s = reinterpret_cast<P3Warp *>(smem)[warp_id()];
         WarpGroup grp;
-        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S, &s.slot};
+        RoadSmem sm{s.A, s.canon, s.Q, s.K, s.S};
         while (true) {
             unsigned i = 0;
             if (lane_id() == 0)
@@ -1163,11 +1038,7 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
             i = __shfl_sync(FULL_MASK, i, 0);
             if (i >= n_small)
                 break;
-            unsigned long long npass = 0;
-            fit_road<WarpGroup, PLAIN>(d, grp, sm, ldcg(d.small_list + i), npass);
-            npass = warp_sum(npass);
-            if (!PLAIN && lane_id() == 0 && npass)
-                atomicAdd(&d.ctrl->n_pass, npass);
+            fit_road<WarpGroup, PLAIN>(d, grp, sm, ldcg(d.small_list + i));
         }
     }
 }
@@ -1189,8 +1060,6 @@ __device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
     const uint16_t *co = d.coords + (size_t)g * 40;
     unsigned kept = 0;
     unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
-    if (!SVT_OK_(d, ldcg(d.surv_off + g) + (unsigned long long)cnt <= d.pool_cap, 9, g, cnt))
-        return 0;
     for (unsigned i = 0; i < cnt; ++i) {
         unsigned long long key = ldcg(keys + i);
         unsigned comb = (unsigned)(key & 0x7FFFu);
@@ -1217,7 +1086,7 @@ __device__ void p4_item(const Dev &d, unsigned c, unsigned n_roads)
 {
     unsigned g = c * ROAD_CHUNK + threadIdx.x;
     unsigned cnt = 0;
-    if (g < n_roads && SVT_OK_(d, g < d.max_roads && c < d.max_chunks_r, 11, g, c)) {
+    if (g < n_roads) {
         cnt = ldcg(d.surv_cnt + g);
         if (cnt && ((ldcg(&d.roads[g].pk) >> 23) & 1u)) {
             cnt = cross_check(d, g, cnt);
@@ -1259,8 +1128,6 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
     const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
     const uint16_t *co = d.coords + (size_t)g * 40;
     const unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
-    if (!SVT_OK_(d, g < d.max_roads && ldcg(d.surv_off + g) + (unsigned long long)cnt <= d.pool_cap, 10, g, cnt))
-        return;
     for (unsigned i = 0; i < cnt; ++i, ++pos) {
         unsigned long long key = ldcg(keys + i);
         unsigned comb = (unsigned)(key & 0x7FFFu);
@@ -1458,28 +1325,13 @@ __global__ void __launch_bounds__(BLOCK) k_fit_plain(Dev d)
         return;
     const unsigned n_roads = ldcg(&d.ctrl->n_roads);
     const unsigned long long n_comb = ldcg(&d.ctrl->n_comb);
-    __shared__ unsigned s_lo, s_hi;
     unsigned long long npass = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * BLOCK;
     for (unsigned long long base = (unsigned long long)blockIdx.x * BLOCK; base < n_comb; base += stride) {
-        // roads of the block's first and last combination
-        if (threadIdx.x < 2) {
-            unsigned long long i = threadIdx.x ? min(base + BLOCK, n_comb) - 1 : base;
-            unsigned lo = 0, hi = n_roads;
-            while (hi - lo > 1) {
-                unsigned mid = (lo + hi) >> 1;
-                if (ldcg(d.comb_off + mid) <= i)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            (threadIdx.x ? s_hi : s_lo) = lo;
-        }
-        __syncthreads();
         unsigned long long i = base + threadIdx.x;
         if (i < n_comb) {
-            // road: last g with comb_off[g] <= i, within the block's range
-            unsigned lo = s_lo, hi = s_hi + 1;
+            // road: last g with comb_off[g] <= i
+            unsigned lo = 0, hi = n_roads;
             while (hi - lo > 1) {
                 unsigned mid = (lo + hi) >> 1;
                 if (ldcg(d.comb_off + mid) <= i)
@@ -1522,7 +1374,6 @@ __global__ void __launch_bounds__(BLOCK) k_fit_plain(Dev d)
             npass += pass;
             d.fit_key[i] = pass ? make_key(chi2, rec.pk >> 24, comb) : NO_KEY;
         }
-        __syncthreads();
     }
     npass = block_sum(npass);
     if (threadIdx.x == 0 && npass)
