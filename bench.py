@@ -164,9 +164,10 @@ def run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, steps, warmup, stream)
     return lat, d2h
 
 
-def cpu_baseline(batch, consts, cut, target_s=12.0):
+def cpu_baseline(batch, consts, cut, target_s=20.0):
     """The oracle as it stands, single thread, on the first events of the
-    batch (grown until about target_s seconds of work)."""
+    batch (grown until one run takes about target_s / 2 seconds, or the
+    whole batch)."""
     import oracle
     oracle.build()
     n_ev = 25
@@ -175,9 +176,9 @@ def cpu_baseline(batch, consts, cut, target_s=12.0):
         t0 = time.perf_counter()
         rc, out = oracle.run(words, consts, cut)
         dt = time.perf_counter() - t0
-        if dt > target_s / 4 or n_ev >= batch.n_events:
+        if dt > target_s / 2 or n_ev >= batch.n_events:
             break
-        n_ev = min(batch.n_events, int(n_ev * max(2.0, target_s / 4 / max(dt, 1e-3))))
+        n_ev = min(batch.n_events, int(n_ev * max(2.0, 1.1 * target_s / 2 / max(dt, 1e-3))))
     fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
     return {"value": fits / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
             "sample": "first %d events of the batch (%d combinations), one run, %.1f s"
