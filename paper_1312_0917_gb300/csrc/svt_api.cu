@@ -193,7 +193,6 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     d.max_chunks_r = (L.max_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
     d.max_tracks = L.max_tracks;
     d.max_combs = L.max_combinations;
-    d.pool_cap = L.max_tracks;
     d.hash_mask = L.hash_slots - 1;
     d.small_n4 = N4_SMALL_MAX;
     bool ok =
@@ -203,8 +202,8 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
-        !dalloc(c, &d.small_list, L.max_roads) && !dalloc(c, &d.surv_pool, d.pool_cap) &&
-        !dalloc(c, &d.surv_off, L.max_roads) && !dalloc(c, &d.surv_cnt, L.max_roads) &&
+        !dalloc(c, &d.surv_pool, (size_t)L.max_roads * SURV_SLOTS) &&
+        !dalloc(c, &d.surv_cnt, L.max_roads) &&
         !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&
         !dalloc(c, &d.cchunk_sum, d.max_chunks_r) && !dalloc(c, &d.cchunk_off, d.max_chunks_r) &&
         !dalloc(c, &d.hash, L.hash_slots) && !dalloc(c, &d.hash_used, L.hash_slots) &&

@@ -17,6 +17,7 @@ constexpr int N_LAYERS = 5;
 constexpr int N_SETS = 360;                // 12 wedges x 6 barrels x 5 excluded layers
 constexpr int SURV_SLOTS = 64;             // survivors per road are <= 64 (see fit_road)
 constexpr int ROAD_CHUNK = 256;            // roads per output work item
+constexpr int WARP_ROADS = 8;              // roads per work item of a fitting warp
 constexpr int N4_MAX = 4096;               // distinct fits per road: 8^4
 constexpr int N4_SMALL_MAX = 256;          // largest road a single warp takes
 constexpr int QTAB_BIG = 384;              // pair tables, sum_{a<b} m_a m_b for 8^4
@@ -38,15 +39,15 @@ struct Ctrl {
     unsigned int n_ep;            // EP words in the stream
     unsigned int has_tail;        // words after the last EE
     unsigned int n_roads;         // roads of complete events
-    unsigned int n_big, n_small;  // road work lists
+    unsigned int n_big;           // roads fitted by a whole CTA (list length)
+    unsigned int pad_q;
     unsigned int hash_used;       // claimed slots of the group table
     unsigned int q[12];           // work-queue heads
     unsigned int bar;             // grid barrier arrivals
     unsigned int done[4];         // last-block-done counters
     unsigned int pad0;
     unsigned long long n_comb, n_pass, n_out;
-    unsigned long long pool_used;     // survivor keys reserved in surv_pool
-    unsigned long long pad1;
+    unsigned long long pad1[2];
 };
 
 // Unpacked road, 16 bytes.  pk: n[l] in bits 4l..4l+3 (l < 5), excluded layer
@@ -79,11 +80,9 @@ struct Dev {
     RoadRec *roads;                                               // [max_roads]
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]
-    uint32_t *big_list, *small_list;                              // [max_roads]
-    unsigned long long *surv_pool;                                // [pool_cap] road-local survivors
-    uint32_t *surv_off;                                           // [max_roads] first pool slot
+    uint32_t *big_list;                                           // [max_roads]
+    unsigned long long *surv_pool;                                // [max_roads][SURV_SLOTS] road survivors
     uint8_t *surv_cnt;                                            // [max_roads]
-    unsigned long long pool_cap;
     uint32_t *rchunk_sum, *rchunk_off;                            // [max_chunks_r]
     unsigned long long *cchunk_sum, *cchunk_off;                  // [max_chunks_r]
     HashSlot *hash;

@@ -93,6 +93,22 @@ __device__ __forceinline__ bool word_ok(uint32_t w)
     return (pl >> 10) == 0 && (pl & 15u) < 12 && ((pl >> 4) & 7u) < 6 && ((pl >> 7) & 7u) < 5;
 }
 
+// combinations of a road (product of its five hit counts) and its distinct
+// fits (product over the four fitted layers: the excluded layer's hit does not
+// enter the fit), from RoadRec::pk
+__device__ __forceinline__ void road_sizes(uint32_t pk, unsigned long long &N, unsigned &N4)
+{
+    const unsigned excl = (pk >> 20) & 7u;
+    N = 1;
+    N4 = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        const unsigned n = (pk >> (4 * l)) & 15u;
+        N *= n;
+        if (l != excl)
+            N4 *= n;
+    }
+}
+
 // exact floor(x / m) for x < 2^32 / m, m >= 1, with M = ceil(2^32 / m)
 __device__ __forceinline__ unsigned divm(unsigned x, unsigned long long M)
 {
@@ -499,24 +515,13 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
                 d.roads[g] = r;
                 d.xmask[g] = xm;
                 d.surv_cnt[g] = 0;
-                unsigned n[N_LAYERS], excl = (pk >> 20) & 7u;
-                unsigned long long N = 1, N4 = 1;
-                for (unsigned l = 0; l < N_LAYERS; ++l) {
-                    n[l] = (pk >> (4 * l)) & 15u;
-                    N *= n[l];
-                    if (l != excl)
-                        N4 *= n[l];
-                }
-                if (N > 0) {
-                    if (N4 > (unsigned long long)d.small_n4) {
-                        unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
-                        if (i < d.max_roads)
-                            d.big_list[i] = g;
-                    } else {
-                        unsigned i = atomicAdd(&d.ctrl->n_small, 1u);
-                        if (i < d.max_roads)
-                            d.small_list[i] = g;
-                    }
+                unsigned long long N;
+                unsigned N4;
+                road_sizes(pk, N, N4);
+                if (N > 0 && N4 > (unsigned)d.small_n4) {   // fitted by a whole CTA
+                    unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
+                    if (i < d.max_roads)
+                        d.big_list[i] = g;
                 }
                 n_comb += N;
             }
@@ -542,7 +547,6 @@ struct WarpGroup {
         return __popc(m & lanemask_lt());
     }
     __device__ bool any(bool p) const { return __any_sync(FULL_MASK, p); }
-    __device__ unsigned long long sum(unsigned long long v) const { return warp_sum(v); }
 };
 
 struct BlockGroup {
@@ -567,12 +571,12 @@ struct BlockGroup {
         return before + __popc(m & lanemask_lt());
     }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
-    __device__ unsigned long long sum(unsigned long long v) const { return block_sum(v); }
 };
 
 // shared memory of one road
 struct RoadSmem {
     int4 *A;                  // [32] partial chi-square sums of fitted slot j, hit d
+    uint16_t *co;             // [40] coordinates of the road (layer * 8 + hit)
     uint8_t *canon;           // [40] lowest hit index with the same coordinate, per layer
     unsigned long long *Q;    // pair tables
     unsigned long long *K;    // key of each distinct fit (excluded-layer hit 0)
@@ -600,9 +604,8 @@ __device__ __constant__ unsigned char c_triple[10][3] = {
     {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
     {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
 
-__device__ __forceinline__ void load_road(const Dev &d, unsigned g, RoadInfo &r)
+__device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRec &rec, RoadInfo &r)
 {
-    RoadRec rec = ldcg(d.roads + g);
     r.g = g;
     r.event = rec.event;
     r.rie = rec.pk >> 24;
@@ -729,13 +732,16 @@ __device__ __forceinline__ unsigned nth_bit(unsigned mask, unsigned n)
 // of the six pair tables Q_ab[c_a][c_b] = min key over f' with the same
 // coordinates on fitted slots a and b.  Survivors agree pairwise on at most
 // one fitted layer, so any two slots identify them: <= 8 x 8 = 64 per road.
+//
+// On entry sm.co holds the road's 40 coordinates, visible to the whole group;
+// `rec` is the road's record.  Adds the road's passing combinations to npass.
 template <class G, bool PLAIN>
-__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g)
+__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g, const RoadRec &rec,
+                         unsigned long long &npass)
 {
     RoadInfo r;
-    load_road(d, g, r);
+    load_road(d, g, rec, r);
     const unsigned tid = grp.rank();
-    const uint16_t *co = d.coords + (size_t)g * 40;
     const unsigned ne = r.n[r.excl];
 
     // partial sums and canonical hit indices
@@ -743,9 +749,9 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         unsigned l = idx >> 3, dd = idx & 7u;
         unsigned c = dd;
         if (dd < r.n[l]) {
-            unsigned v = ldcg(co + idx);
+            unsigned v = sm.co[idx];
             for (unsigned x = 0; x < dd; ++x)
-                if (c == dd && ldcg(co + l * 8 + x) == v)
+                if (c == dd && sm.co[l * 8 + x] == v)
                     c = x;
         }
         sm.canon[idx] = (uint8_t)c;
@@ -755,7 +761,7 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
             unsigned j = idx >> 3, dd = idx & 7u;
             int4 a = make_int4(0, 0, 0, 0);
             if (dd < r.m[j]) {
-                int h = ldcg(co + r.L[j] * 8 + dd);
+                int h = sm.co[r.L[j] * 8 + dd];
                 const svt_const_set *cs = r.cs;
                 a.x = (int)__ldg(&cs->C[0][j]) * h;
                 a.y = (int)__ldg(&cs->C[1][j]) * h;
@@ -779,7 +785,6 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     dup = grp.any(dup);
 
     // keys of all distinct fits
-    unsigned long long npass = 0;
     const unsigned long long cbase = PLAIN ? ldcg(d.comb_off + g) : 0ull;
     for (unsigned base = 0; base < r.N4; base += G::SIZE) {
         unsigned f = base + tid;
@@ -876,32 +881,13 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         n_surv += total;
     }
     n_surv = min(n_surv, (unsigned)SURV_SLOTS);
-    // reserve pool slots and copy the survivors out
-    {
-        __shared__ unsigned long long s_off_blk;
-        unsigned long long off = 0;
-        if (tid == 0) {
-            off = n_surv ? atomicAdd(&d.ctrl->pool_used, (unsigned long long)n_surv) : 0ull;
-            if (off + n_surv > d.pool_cap) {
-                raise_flag(d, FLAG_CAPACITY);
-                off = ~0ull;
-            }
-            d.surv_off[g] = (uint32_t)(off == ~0ull ? 0 : off);
-            d.surv_cnt[g] = (uint8_t)(off == ~0ull ? 0 : n_surv);
-        }
-        if (G::SIZE == 32) {
-            off = __shfl_sync(FULL_MASK, off, 0);
-        } else {
-            if (tid == 0)
-                s_off_blk = off;
-            __syncthreads();
-            off = s_off_blk;
-        }
-        grp.sync();
-        if (off != ~0ull)
-            for (unsigned i = tid; i < n_surv; i += G::SIZE)
-                d.surv_pool[off + i] = sm.S[i];
-    }
+    // the road's own survivor slots
+    grp.sync();
+    unsigned long long *slots = d.surv_pool + (size_t)g * SURV_SLOTS;
+    for (unsigned i = tid; i < n_surv; i += G::SIZE)
+        slots[i] = sm.S[i];
+    if (tid == 0)
+        d.surv_cnt[g] = (uint8_t)n_surv;
 
     // cross-road candidates: publish the minimum of every group whose three
     // coordinates all appear in another road of the event
@@ -981,18 +967,13 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
                     mn += (unsigned long long)de * r.S5[r.excl];
             }
             if (mn != NO_KEY) {
-                unsigned v0 = ldcg(co + l0 * 8 + dsel[0]), v1 = ldcg(co + l1 * 8 + dsel[1]);
-                unsigned v2 = ldcg(co + l2 * 8 + dsel[2]);
+                unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]];
+                unsigned v2 = sm.co[l2 * 8 + dsel[2]];
                 hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
             }
         }
     }
 
-    npass = grp.sum(npass);
-    if (tid == 0) {
-        if (!PLAIN && npass)
-            atomicAdd(&d.ctrl->n_pass, npass);
-    }
     grp.sync();
 }
 
@@ -1002,6 +983,7 @@ struct P3Big {
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_BIG];
     unsigned long long K[N4_MAX];
+    uint16_t co[40];
     uint8_t canon[40];
     unsigned cnt[WARPS + 1];
 };
@@ -1010,37 +992,75 @@ struct P3Warp {
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_SMALL];
     unsigned long long K[N4_SMALL_MAX];
+    uint16_t co[40];
     uint8_t canon[40];
-    unsigned pad[2];
 };
 
+// Roads with more than small_n4 distinct fits (listed in P2) are fitted by a
+// whole CTA; then every warp takes runs of WARP_ROADS consecutive roads and
+// fits the others itself, loading the next road's record and coordinates
+// while it fits the current one.
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
     const unsigned n_big = min(ldcg(&d.ctrl->n_big), d.max_roads);
-    const unsigned n_small = min(ldcg(&d.ctrl->n_small), d.max_roads);
+    const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
+    unsigned long long npass = 0;
     {
         P3Big &s = *reinterpret_cast<P3Big *>(smem);
         BlockGroup grp{s.cnt};
-        RoadSmem sm{s.A, s.canon, s.Q, s.K, s.S};
-        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig))
-            fit_road<BlockGroup, PLAIN>(d, grp, sm, ldcg(d.big_list + i));
+        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S};
+        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig)) {
+            const unsigned g = min(ldcg(d.big_list + i), d.max_roads - 1);
+            if (threadIdx.x < 40)
+                s.co[threadIdx.x] = ldcg(d.coords + (size_t)g * 40 + threadIdx.x);
+            const RoadRec rec = ldcg(d.roads + g);
+            __syncthreads();
+            fit_road<BlockGroup, PLAIN>(d, grp, sm, g, rec, npass);
+        }
     }
     __syncthreads();
     {
         P3Warp &s = reinterpret_cast<P3Warp *>(smem)[warp_id()];
         WarpGroup grp;
-        RoadSmem sm{s.A, s.canon, s.Q, s.K, s.S};
+        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S};
+        const unsigned lane = lane_id();
+        const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
         while (true) {
-            unsigned i = 0;
-            if (lane_id() == 0)
-                i = atomicAdd(&d.ctrl->q[qsmall], 1u);
-            i = __shfl_sync(FULL_MASK, i, 0);
-            if (i >= n_small)
+            unsigned c = 0;
+            if (lane == 0)
+                c = atomicAdd(&d.ctrl->q[qsmall], 1u);
+            c = __shfl_sync(FULL_MASK, c, 0);
+            if (c >= n_runs)
                 break;
-            fit_road<WarpGroup, PLAIN>(d, grp, sm, ldcg(d.small_list + i));
+            const unsigned g0 = c * WARP_ROADS, g1 = min(g0 + WARP_ROADS, n_roads);
+            RoadRec next = ldcg(d.roads + g0);
+            uint16_t nco0 = ldcg(d.coords + (size_t)g0 * 40 + lane);
+            uint16_t nco1 = lane < 8 ? ldcg(d.coords + (size_t)g0 * 40 + 32 + lane) : (uint16_t)0;
+            for (unsigned g = g0; g < g1; ++g) {
+                const RoadRec rec = next;
+                s.co[lane] = nco0;
+                if (lane < 8)
+                    s.co[32 + lane] = nco1;
+                if (g + 1 < g1) {
+                    next = ldcg(d.roads + g + 1);
+                    nco0 = ldcg(d.coords + (size_t)(g + 1) * 40 + lane);
+                    if (lane < 8)
+                        nco1 = ldcg(d.coords + (size_t)(g + 1) * 40 + 32 + lane);
+                }
+                unsigned long long N;
+                unsigned N4;
+                road_sizes(rec.pk, N, N4);
+                if (N == 0 || N4 > (unsigned)d.small_n4)
+                    continue;   // no combinations, or fitted by a CTA above
+                __syncwarp();
+                fit_road<WarpGroup, PLAIN>(d, grp, sm, g, rec, npass);
+            }
         }
     }
+    npass = block_sum(npass);
+    if (!PLAIN && threadIdx.x == 0 && npass)
+        atomicAdd(&d.ctrl->n_pass, npass);
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,7 +1079,7 @@ __device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
     unsigned long long xm = ldcg(d.xmask + g);
     const uint16_t *co = d.coords + (size_t)g * 40;
     unsigned kept = 0;
-    unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
+    unsigned long long *keys = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = 0; i < cnt; ++i) {
         unsigned long long key = ldcg(keys + i);
         unsigned comb = (unsigned)(key & 0x7FFFu);
@@ -1127,7 +1147,7 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
     const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
     const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
     const uint16_t *co = d.coords + (size_t)g * 40;
-    const unsigned long long *keys = d.surv_pool + ldcg(d.surv_off + g);
+    const unsigned long long *keys = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = 0; i < cnt; ++i, ++pos) {
         unsigned long long key = ldcg(keys + i);
         unsigned comb = (unsigned)(key & 0x7FFFu);
