@@ -537,7 +537,6 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
 
 struct WarpGroup {
     static constexpr unsigned SIZE = 32;
-    static constexpr unsigned KCAP = N4_SMALL_MAX, QCAP = QTAB_SMALL;
     __device__ unsigned rank() const { return lane_id(); }
     __device__ void sync() const { __syncwarp(); }
     // position of a flagged thread among this tile's flagged threads; *total
@@ -552,7 +551,6 @@ struct WarpGroup {
 
 struct BlockGroup {
     static constexpr unsigned SIZE = BLOCK;
-    static constexpr unsigned KCAP = N4_MAX, QCAP = QTAB_BIG;
     unsigned *s_cnt;   // WARPS + 1 entries
     __device__ unsigned rank() const { return threadIdx.x; }
     __device__ void sync() const { __syncthreads(); }
@@ -585,108 +583,77 @@ struct RoadSmem {
     unsigned long long *S;    // [64] road-local survivors in comb order
 };
 
-__device__ __forceinline__ unsigned sel4(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
-}
-__device__ __forceinline__ unsigned sel5(unsigned i, unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned a4)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : i == 3 ? a3 : a4;
-}
-__device__ __forceinline__ unsigned long long sel4l(unsigned i, unsigned long long a0,
-                                                    unsigned long long a1, unsigned long long a2,
-                                                    unsigned long long a3)
-{
-    return i == 0 ? a0 : i == 1 ? a1 : i == 2 ? a2 : a3;
-}
-
-// Per-road values, computed from the road record by every thread (registers).
-struct RoadR {
-    unsigned g, event, rie, excl, cand, set;
+// Everything about one road that every thread of its group uses.
+struct RoadInfo {
+    unsigned g, event, rie, excl, cand;
+    unsigned n[N_LAYERS];
+    unsigned m[4], L[4], st[4];      // fitted slots: size, layer, 4-D stride
+    unsigned slot_of[N_LAYERS];      // fitted slot of a layer (4 = excluded)
+    unsigned S5[N_LAYERS];           // combination stride of each layer
+    unsigned long long M[3];         // magic divisors of m[0..2]
+    unsigned N4, off[7];             // distinct fits; pair-table offsets
     int curv, phi;
-    unsigned n0, n1, n2, n3, n4;          // hits per layer
-    unsigned S0, S1, S2, S3, S4;          // combination stride of each layer
-    unsigned L0, L1, L2, L3;              // layer of each fitted slot
-    unsigned m0, m1, m2, m3;              // hits of each fitted slot
-    unsigned st1, st2, st3;               // 4-D stride of slots 1..3 (slot 0: 1)
-    unsigned SL0, SL1, SL2, SL3;          // combination stride of each fitted slot
-    unsigned N4, ne, Se;                  // distinct fits; excluded layer's hits and stride
-    unsigned off1, off2, off3, off4, off5, E;   // pair-table offsets (pair 0 at 0)
-    unsigned long long M0, M1, M2, M3;    // magic divisors of m0..m3
-    __device__ unsigned m(unsigned s) const { return sel4(s, m0, m1, m2, m3); }
-    __device__ unsigned st(unsigned s) const { return sel4(s, 1u, st1, st2, st3); }
-    __device__ unsigned L(unsigned s) const { return sel4(s, L0, L1, L2, L3); }
-    __device__ unsigned long long M(unsigned s) const { return sel4l(s, M0, M1, M2, M3); }
-    __device__ unsigned off(unsigned p) const { return p == 0 ? 0u : p == 1 ? off1 : p == 2 ? off2 : p == 3 ? off3 : p == 4 ? off4 : off5; }
-    __device__ unsigned n(unsigned l) const { return sel5(l, n0, n1, n2, n3, n4); }
-    __device__ unsigned S(unsigned l) const { return sel5(l, S0, S1, S2, S3, S4); }
-    __device__ unsigned slot_of(unsigned l) const { return l == excl ? 4u : l - (l > excl); }
+    const svt_const_set *cs;
 };
 
-__device__ __forceinline__ RoadR load_road(unsigned g, const RoadRec &rec)
+// pair p -> slots (a, b), complement (c, e)
+__device__ __constant__ unsigned char c_pair[6][4] = {
+    {0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 3}, {1, 3, 0, 2}, {2, 3, 0, 1}};
+// the ten layer triples
+__device__ __constant__ unsigned char c_triple[10][3] = {
+    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
+    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+
+__device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRec &rec, RoadInfo &r)
 {
-    RoadR r;
     r.g = g;
     r.event = rec.event;
     r.rie = rec.pk >> 24;
     r.excl = min((rec.pk >> 20) & 7u, 4u);
     r.cand = (rec.pk >> 23) & 1u;
-    r.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+    unsigned S = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        r.n[l] = min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
+        r.S5[l] = S;
+        S *= r.n[l];
+    }
+    unsigned j = 0, st = 1;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        if (l == r.excl) {
+            r.slot_of[l] = 4;
+            continue;
+        }
+        r.slot_of[l] = j;
+        r.L[j] = l;
+        r.m[j] = r.n[l];
+        r.st[j] = st;
+        st *= r.n[l];
+        ++j;
+    }
+    r.N4 = st;
+    for (unsigned s = 0; s < 3; ++s)
+        r.M[s] = magic(max(r.m[s], 1u));
+    r.off[0] = 0;
+    for (unsigned p = 0; p < 6; ++p)
+        r.off[p + 1] = r.off[p] + r.m[c_pair[p][0]] * r.m[c_pair[p][1]];
     r.curv = rec.curv;
     r.phi = rec.phi;
-    r.n0 = min(rec.pk & 15u, 8u);
-    r.n1 = min((rec.pk >> 4) & 15u, 8u);
-    r.n2 = min((rec.pk >> 8) & 15u, 8u);
-    r.n3 = min((rec.pk >> 12) & 15u, 8u);
-    r.n4 = min((rec.pk >> 16) & 15u, 8u);
-    r.S0 = 1;
-    r.S1 = r.n0;
-    r.S2 = r.S1 * r.n1;
-    r.S3 = r.S2 * r.n2;
-    r.S4 = r.S3 * r.n3;
-    r.L0 = 0 + (0 >= r.excl);
-    r.L1 = 1 + (1 >= r.excl);
-    r.L2 = 2 + (2 >= r.excl);
-    r.L3 = 3 + (3 >= r.excl);
-    r.m0 = r.n(r.L0);
-    r.m1 = r.n(r.L1);
-    r.m2 = r.n(r.L2);
-    r.m3 = r.n(r.L3);
-    r.SL0 = r.S(r.L0);
-    r.SL1 = r.S(r.L1);
-    r.SL2 = r.S(r.L2);
-    r.SL3 = r.S(r.L3);
-    r.st1 = r.m0;
-    r.st2 = r.st1 * r.m1;
-    r.st3 = r.st2 * r.m2;
-    r.N4 = r.st3 * r.m3;
-    r.ne = r.n(r.excl);
-    r.Se = r.S(r.excl);
-    r.M0 = magic(max(r.m0, 1u));
-    r.M1 = magic(max(r.m1, 1u));
-    r.M2 = magic(max(r.m2, 1u));
-    r.M3 = magic(max(r.m3, 1u));
-    r.off1 = r.m0 * r.m1;
-    r.off2 = r.off1 + r.m0 * r.m2;
-    r.off3 = r.off2 + r.m0 * r.m3;
-    r.off4 = r.off3 + r.m1 * r.m2;
-    r.off5 = r.off4 + r.m1 * r.m3;
-    r.E = r.off5 + r.m2 * r.m3;
-    return r;
+    r.cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
 }
 
-// The six pairs of fitted slots (a, b) and their complements (c, e), one
-// nibble per pair: (0,1|2,3) (0,2|1,3) (0,3|1,2) (1,2|0,3) (1,3|0,2) (2,3|0,1)
-__device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_b(unsigned p) { return (0x332321u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_c(unsigned p) { return (0x000112u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_e(unsigned p) { return (0x123233u >> (4 * p)) & 15u; }
-
-// the ten layer triples
-__device__ __constant__ unsigned char c_triple[10][3] = {
-    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
-    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+__device__ __forceinline__ void digits4(const RoadInfo &r, unsigned f, unsigned &f0, unsigned &f1,
+                                        unsigned &f2, unsigned &f3)
+{
+    unsigned q = divm(f, r.M[0]);
+    f0 = f - q * r.m[0];
+    unsigned t = q;
+    q = divm(t, r.M[1]);
+    f1 = t - q * r.m[1];
+    t = q;
+    q = divm(t, r.M[2]);
+    f2 = t - q * r.m[2];
+    f3 = q;
+}
 
 __device__ __forceinline__ unsigned long long make_key(long long chi2, unsigned rie, unsigned comb)
 {
@@ -753,92 +720,6 @@ __device__ __forceinline__ unsigned nth_bit(unsigned mask, unsigned n)
     return __ffs(mask) - 1;
 }
 
-// Publish, for a cross-road candidate road, the minimum key of every group
-// (layer triple, three coordinates) whose coordinates are all shared with a
-// road that shares >= 3 layers (rare; plain code).
-template <class G>
-__device__ void publish_groups(const Dev &d, const G &grp, const RoadSmem &sm, const RoadR &r)
-{
-    const unsigned tid = grp.rank();
-    const unsigned long long xm = ldcg(d.xmask + r.g);
-    unsigned fl[N_LAYERS], cnt[10], total = 0;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        unsigned msk = 0;
-        for (unsigned x = 0; x < r.n(l); ++x)
-            if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
-                msk |= 1u << x;
-        fl[l] = msk;
-    }
-    for (unsigned t = 0; t < 10; ++t) {
-        cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) * __popc(fl[c_triple[t][2]]);
-        total += cnt[t];
-    }
-    for (unsigned gi = tid; gi < total; gi += G::SIZE) {
-        unsigned t = 0, rem = gi;
-        while (t < 9 && rem >= cnt[t]) {
-            rem -= cnt[t];
-            ++t;
-        }
-        unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
-        unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
-        unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
-        unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
-        unsigned lt[3] = {l0, l1, l2};
-        unsigned long long mn = NO_KEY;
-        if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
-            // the free fitted slot varies; the three others run over the raw
-            // hits of each selected coordinate
-            unsigned s[3], free_slot = 0 + 1 + 2 + 3;
-            for (unsigned q = 0; q < 3; ++q) {
-                s[q] = r.slot_of(lt[q]);
-                free_slot -= s[q];
-            }
-            for (unsigned x0 = 0; x0 < r.m(s[0]); ++x0) {
-                if (sm.canon[lt[0] * 8 + x0] != dsel[0])
-                    continue;
-                for (unsigned x1 = 0; x1 < r.m(s[1]); ++x1) {
-                    if (sm.canon[lt[1] * 8 + x1] != dsel[1])
-                        continue;
-                    for (unsigned x2 = 0; x2 < r.m(s[2]); ++x2) {
-                        if (sm.canon[lt[2] * 8 + x2] != dsel[2])
-                            continue;
-                        unsigned fb = x0 * r.st(s[0]) + x1 * r.st(s[1]) + x2 * r.st(s[2]);
-                        for (unsigned z = 0; z < r.m(free_slot); ++z) {
-                            unsigned long long k = sm.K[fb + z * r.st(free_slot)];
-                            mn = k < mn ? k : mn;
-                        }
-                    }
-                }
-            }
-        } else {
-            // excluded layer in the triple: the min over its hit class is at the
-            // lowest index (canonical), the two fitted slots come from Q
-            unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
-            for (unsigned q = 0; q < 3; ++q) {
-                if (lt[q] == r.excl) {
-                    de = dsel[q];
-                } else if (fa == 4) {
-                    fa = r.slot_of(lt[q]);
-                    da = dsel[q];
-                } else {
-                    fb = r.slot_of(lt[q]);
-                    db = dsel[q];
-                }
-            }
-            unsigned p = 0;
-            while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
-                ++p;
-            mn = sm.Q[r.off(p) + da * r.m(fb) + db];
-            if (mn != NO_KEY)
-                mn += (unsigned long long)de * r.Se;
-        }
-        if (mn != NO_KEY) {
-            unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]], v2 = sm.co[l2 * 8 + dsel[2]];
-            hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
-        }
-    }
-}
-
 // Fit one road and decide its road-local survivors.
 //
 // Combinations t = (f, i): f the hits of the four fitted layers, i the hit of
@@ -858,38 +739,30 @@ template <class G, bool PLAIN>
 __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g, const RoadRec &rec,
                          unsigned long long &npass)
 {
-    const RoadR r = load_road(g, rec);
+    RoadInfo r;
+    load_road(d, g, rec, r);
     const unsigned tid = grp.rank();
-    if (r.N4 > G::KCAP || r.E > G::QCAP) {      // a road is fitted by a group that holds it
-        if (tid == 0) {
-            raise_flag(d, FLAG_INTERNAL);
-            d.surv_cnt[g] = 0;
-        }
-        grp.sync();
-        return;
-    }
+    const unsigned ne = r.n[r.excl];
 
-    // canonical hit indices (first hit with the same coordinate in its layer)
-    bool dup = false;
+    // partial sums and canonical hit indices
     for (unsigned idx = tid; idx < 40; idx += G::SIZE) {
-        unsigned l = idx >> 3, dd = idx & 7u, c = dd;
-        if (dd < r.n(l)) {
+        unsigned l = idx >> 3, dd = idx & 7u;
+        unsigned c = dd;
+        if (dd < r.n[l]) {
             unsigned v = sm.co[idx];
             for (unsigned x = 0; x < dd; ++x)
                 if (c == dd && sm.co[l * 8 + x] == v)
                     c = x;
         }
         sm.canon[idx] = (uint8_t)c;
-        dup = dup || c != dd;
     }
-    // partial chi-square sums of every fitted hit
     if (!PLAIN) {
-        const svt_const_set *cs = d.consts + r.set;
         for (unsigned idx = tid; idx < 32; idx += G::SIZE) {
             unsigned j = idx >> 3, dd = idx & 7u;
             int4 a = make_int4(0, 0, 0, 0);
-            if (dd < r.m(j)) {
-                int h = sm.co[r.L(j) * 8 + dd];
+            if (dd < r.m[j]) {
+                int h = sm.co[r.L[j] * 8 + dd];
+                const svt_const_set *cs = r.cs;
                 a.x = (int)__ldg(&cs->C[0][j]) * h;
                 a.y = (int)__ldg(&cs->C[1][j]) * h;
                 a.z = (int)__ldg(&cs->C[2][j]) * h;
@@ -905,47 +778,53 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
             sm.A[idx] = a;
         }
     }
-    dup = grp.any(dup);
     grp.sync();
+    bool dup = false;
+    for (unsigned idx = tid; idx < 40; idx += G::SIZE)
+        dup = dup || sm.canon[idx] != (idx & 7u);
+    dup = grp.any(dup);
 
-    const long long cut = d.cut;
     // keys of all distinct fits
     const unsigned long long cbase = PLAIN ? ldcg(d.comb_off + g) : 0ull;
-    for (unsigned f = tid; f < r.N4; f += G::SIZE) {
-        unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
-        unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
-        unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
-        unsigned comb = f0 * r.SL0 + f1 * r.SL1 + f2 * r.SL2 + f3 * r.SL3;
-        unsigned long long key;
-        if (PLAIN) {
-            key = ldcg(d.fit_key + cbase + comb);
-        } else {
-            int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
-            int s0 = a0.x + a1.x + a2.x + a3.x;
-            int s1 = a0.y + a1.y + a2.y + a3.y;
-            int s2 = a0.z + a1.z + a2.z + a3.z;
-            long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
-            bool pass = chi2 <= cut;
-            npass += pass ? r.ne : 0u;
-            key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
+    for (unsigned base = 0; base < r.N4; base += G::SIZE) {
+        unsigned f = base + tid;
+        if (f < r.N4) {
+            unsigned f0, f1, f2, f3;
+            digits4(r, f, f0, f1, f2, f3);
+            unsigned comb = f0 * r.S5[r.L[0]] + f1 * r.S5[r.L[1]] + f2 * r.S5[r.L[2]] +
+                            f3 * r.S5[r.L[3]];
+            unsigned long long key;
+            if (PLAIN) {
+                key = ldcg(d.fit_key + cbase + comb);
+            } else {
+                int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
+                int s0 = a0.x + a1.x + a2.x + a3.x;
+                int s1 = a0.y + a1.y + a2.y + a3.y;
+                int s2 = a0.z + a1.z + a2.z + a3.z;
+                long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
+                bool pass = chi2 <= d.cut;
+                npass += pass ? ne : 0u;
+                key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
+            }
+            sm.K[f] = key;
         }
-        sm.K[f] = key;
     }
     grp.sync();
 
     // pair tables over raw hit indices
-    for (unsigned idx = tid; idx < r.E; idx += G::SIZE) {
-        unsigned p = (idx >= r.off1) + (idx >= r.off2) + (idx >= r.off3) + (idx >= r.off4) +
-                     (idx >= r.off5);
-        unsigned a = pair_a(p), b = pair_b(p), c = pair_c(p), e = pair_e(p);
-        unsigned local = idx - r.off(p), mb = r.m(b);
-        unsigned x = divm(local, r.M(b)), y = local - x * mb;
-        unsigned fb = x * r.st(a) + y * r.st(b);
-        unsigned mc = r.m(c), me = r.m(e), sc = r.st(c), se = r.st(e);
+    const unsigned E = r.off[6];
+    for (unsigned idx = tid; idx < E; idx += G::SIZE) {
+        unsigned p = 0;
+        while (idx >= r.off[p + 1])
+            ++p;
+        unsigned a = c_pair[p][0], b = c_pair[p][1], c = c_pair[p][2], e = c_pair[p][3];
+        unsigned local = idx - r.off[p];
+        unsigned x = local / r.m[b], y = local - x * r.m[b];
+        unsigned fb = x * r.st[a] + y * r.st[b];
         unsigned long long mn = NO_KEY;
-        for (unsigned z = 0; z < mc; ++z)
-            for (unsigned w = 0; w < me; ++w) {
-                unsigned long long k = sm.K[fb + z * sc + w * se];
+        for (unsigned z = 0; z < r.m[c]; ++z)
+            for (unsigned w = 0; w < r.m[e]; ++w) {
+                unsigned long long k = sm.K[fb + z * r.st[c] + w * r.st[e]];
                 mn = k < mn ? k : mn;
             }
         sm.Q[idx] = mn;
@@ -954,14 +833,14 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     // equal coordinates within a layer: fold raw entries into canonical ones
     if (dup) {
         if (tid < 6) {
-            unsigned p = tid, a = pair_a(p), b = pair_b(p), ma = r.m(a), mb = r.m(b);
-            unsigned La = r.L(a) * 8, Lb = r.L(b) * 8, o = r.off(p);
-            for (unsigned x = 0; x < ma; ++x)
-                for (unsigned y = 0; y < mb; ++y) {
-                    unsigned cx = sm.canon[La + x], cy = sm.canon[Lb + y];
+            unsigned p = tid, a = c_pair[p][0], b = c_pair[p][1];
+            for (unsigned x = 0; x < r.m[a]; ++x)
+                for (unsigned y = 0; y < r.m[b]; ++y) {
+                    unsigned cx = sm.canon[r.L[a] * 8 + x], cy = sm.canon[r.L[b] * 8 + y];
                     if (cx != x || cy != y) {
-                        unsigned long long v = sm.Q[o + x * mb + y], w = sm.Q[o + cx * mb + cy];
-                        sm.Q[o + cx * mb + cy] = v < w ? v : w;
+                        unsigned long long &dst = sm.Q[r.off[p] + cx * r.m[b] + cy];
+                        unsigned long long v = sm.Q[r.off[p] + x * r.m[b] + y];
+                        dst = v < dst ? v : dst;
                     }
                 }
         }
@@ -969,7 +848,6 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     }
 
     // road-local survivors, in f order (= comb order)
-    const unsigned Lb0 = r.L0 * 8, Lb1 = r.L1 * 8, Lb2 = r.L2 * 8, Lb3 = r.L3 * 8;
     unsigned n_surv = 0;
     for (unsigned base = 0; base < r.N4; base += G::SIZE) {
         unsigned f = base + tid;
@@ -977,15 +855,19 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         unsigned long long key = NO_KEY;
         if (f < r.N4) {
             key = sm.K[f];
-            if (key != NO_KEY) {
-                unsigned q0 = divm(f, r.M0), f0 = f - q0 * r.m0;
-                unsigned q1 = divm(q0, r.M1), f1 = q0 - q1 * r.m1;
-                unsigned f3 = divm(q1, r.M2), f2 = q1 - f3 * r.m2;
-                unsigned c0 = sm.canon[Lb0 + f0], c1 = sm.canon[Lb1 + f1];
-                unsigned c2 = sm.canon[Lb2 + f2], c3 = sm.canon[Lb3 + f3];
-                surv = sm.Q[c0 * r.m1 + c1] == key && sm.Q[r.off1 + c0 * r.m2 + c2] == key &&
-                       sm.Q[r.off2 + c0 * r.m3 + c3] == key && sm.Q[r.off3 + c1 * r.m2 + c2] == key &&
-                       sm.Q[r.off4 + c1 * r.m3 + c3] == key && sm.Q[r.off5 + c2 * r.m3 + c3] == key;
+            surv = key != NO_KEY;
+            if (surv) {
+                unsigned fd[4];
+                digits4(r, f, fd[0], fd[1], fd[2], fd[3]);
+                unsigned cf[4];
+#pragma unroll
+                for (unsigned j = 0; j < 4; ++j)
+                    cf[j] = sm.canon[r.L[j] * 8 + fd[j]];
+#pragma unroll
+                for (unsigned p = 0; p < 6; ++p) {
+                    unsigned a = c_pair[p][0], b = c_pair[p][1];
+                    surv = surv && sm.Q[r.off[p] + cf[a] * r.m[b] + cf[b]] == key;
+                }
             }
         }
         unsigned total;
@@ -999,7 +881,6 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
         n_surv += total;
     }
     n_surv = min(n_surv, (unsigned)SURV_SLOTS);
-
     // the road's own survivor slots
     grp.sync();
     unsigned long long *slots = d.surv_pool + (size_t)g * SURV_SLOTS;
@@ -1008,8 +889,91 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     if (tid == 0)
         d.surv_cnt[g] = (uint8_t)n_surv;
 
-    if (r.cand)
-        publish_groups(d, grp, sm, r);
+    // cross-road candidates: publish the minimum of every group whose three
+    // coordinates all appear in another road of the event
+    if (r.cand) {
+        unsigned long long xm = ldcg(d.xmask + g);
+        unsigned fl[N_LAYERS];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            unsigned msk = 0;
+            for (unsigned x = 0; x < r.n[l]; ++x)
+                if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
+                    msk |= 1u << x;
+            fl[l] = msk;
+        }
+        unsigned cnt[10], total = 0;
+        for (unsigned t = 0; t < 10; ++t) {
+            cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) *
+                     __popc(fl[c_triple[t][2]]);
+            total += cnt[t];
+        }
+        for (unsigned gi = tid; gi < total; gi += G::SIZE) {
+            unsigned t = 0, rem = gi;
+            while (rem >= cnt[t]) {
+                rem -= cnt[t];
+                ++t;
+            }
+            unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
+            unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
+            unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
+            unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
+            unsigned lt[3] = {l0, l1, l2};
+            unsigned long long mn = NO_KEY;
+            if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
+                // the free fitted slot varies; the three others run over the
+                // raw hits of each selected coordinate
+                unsigned s[3], free_slot = 0 + 1 + 2 + 3;
+                for (unsigned q = 0; q < 3; ++q) {
+                    s[q] = r.slot_of[lt[q]];
+                    free_slot -= s[q];
+                }
+                for (unsigned x0 = 0; x0 < r.m[s[0]]; ++x0) {
+                    if (sm.canon[lt[0] * 8 + x0] != dsel[0])
+                        continue;
+                    for (unsigned x1 = 0; x1 < r.m[s[1]]; ++x1) {
+                        if (sm.canon[lt[1] * 8 + x1] != dsel[1])
+                            continue;
+                        for (unsigned x2 = 0; x2 < r.m[s[2]]; ++x2) {
+                            if (sm.canon[lt[2] * 8 + x2] != dsel[2])
+                                continue;
+                            unsigned fb = x0 * r.st[s[0]] + x1 * r.st[s[1]] + x2 * r.st[s[2]];
+                            for (unsigned z = 0; z < r.m[free_slot]; ++z) {
+                                unsigned long long k = sm.K[fb + z * r.st[free_slot]];
+                                mn = k < mn ? k : mn;
+                            }
+                        }
+                    }
+                }
+            } else {
+                // excluded layer in the triple: min over its hit class is the
+                // lowest index (canonical), the two fitted slots from Q
+                unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
+                for (unsigned q = 0; q < 3; ++q) {
+                    if (lt[q] == r.excl) {
+                        de = dsel[q];
+                    } else if (fa == 4) {
+                        fa = r.slot_of[lt[q]];
+                        da = dsel[q];
+                    } else {
+                        fb = r.slot_of[lt[q]];
+                        db = dsel[q];
+                    }
+                }
+                unsigned p = 0;
+                while (!(c_pair[p][0] == fa && c_pair[p][1] == fb))
+                    ++p;
+                mn = sm.Q[r.off[p] + da * r.m[fb] + db];
+                if (mn != NO_KEY)
+                    mn += (unsigned long long)de * r.S5[r.excl];
+            }
+            if (mn != NO_KEY) {
+                unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]];
+                unsigned v2 = sm.co[l2 * 8 + dsel[2]];
+                hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
+            }
+        }
+    }
+
     grp.sync();
 }
 
@@ -1241,7 +1205,7 @@ __device__ void clear_hash(const Dev &d, unsigned i)
 // queue indices
 enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
 
-__global__ void __launch_bounds__(BLOCK, 3) k_persistent(Dev d)
+__global__ void __launch_bounds__(BLOCK) k_persistent(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if (d.skip_arrival && blockIdx.x == 0)
