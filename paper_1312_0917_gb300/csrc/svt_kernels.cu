@@ -114,10 +114,13 @@ __device__ __forceinline__ unsigned divm(unsigned x, unsigned long long M)
 {
     return (unsigned)(((unsigned long long)x * M) >> 32);
 }
-__host__ __device__ __forceinline__ unsigned long long magic(unsigned m)
+__host__ __device__ constexpr unsigned long long magic(unsigned m)
 {
     return ((1ull << 32) + m - 1) / m;
 }
+// magic(m) for the hit counts m = 1..8 (entry 0 repeats m = 1)
+__device__ __constant__ unsigned long long c_magic[MAX_HITS + 1] = {
+    magic(1), magic(1), magic(2), magic(3), magic(4), magic(5), magic(6), magic(7), magic(8)};
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v)
@@ -632,7 +635,7 @@ __device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRe
     }
     r.N4 = st;
     for (unsigned s = 0; s < 3; ++s)
-        r.M[s] = magic(max(r.m[s], 1u));
+        r.M[s] = c_magic[r.m[s]];
     r.off[0] = 0;
     for (unsigned p = 0; p < 6; ++p)
         r.off[p + 1] = r.off[p] + r.m[c_pair[p][0]] * r.m[c_pair[p][1]];
@@ -1205,7 +1208,7 @@ __device__ void clear_hash(const Dev &d, unsigned i)
 // queue indices
 enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
 
-__global__ void __launch_bounds__(BLOCK) k_persistent(Dev d)
+__global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if (d.skip_arrival && blockIdx.x == 0)
@@ -1368,7 +1371,7 @@ __global__ void __launch_bounds__(BLOCK) k_fit_plain(Dev d)
             unsigned t = comb, j = 0;
             for (unsigned l = 0; l < N_LAYERS; ++l) {
                 unsigned nl = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-                unsigned q = divm(t, magic(nl));
+                unsigned q = divm(t, c_magic[nl]);
                 unsigned dl = t - q * nl;
                 t = q;
                 if (l != excl)
