@@ -257,6 +257,9 @@ __device__ bool grid_sync(const Dev &d)
     return s_ok != 0;
 }
 
+// work-queue indices (Ctrl::q)
+enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
+
 // ---------------------------------------------------------------------------
 // P0 / P1: word chunks
 // ---------------------------------------------------------------------------
@@ -354,9 +357,10 @@ struct P2Smem {
     uint32_t n_ep, n_seg;
 };
 
-// Decode road k of the event (words [start, end]) with one warp.
+// Decode road k of the event (words [start, end]) with one warp; `w_first`
+// is word start + lane (0 past the end), loaded by the caller.
 __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long long start,
-                            unsigned long long end, unsigned long long &err)
+                            unsigned long long end, uint32_t w_first, unsigned long long &err)
 {
     const unsigned lane = lane_id();
     unsigned cnt[N_LAYERS] = {0, 0, 0, 0, 0};
@@ -367,7 +371,7 @@ __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long l
     for (unsigned long long q0 = 0; start + q0 <= end; q0 += 32) {
         unsigned long long q = q0 + lane, pos = start + q;
         bool valid = pos <= end;
-        uint32_t w = valid ? __ldg(d.words + pos) : 0u;
+        uint32_t w = q0 == 0 ? w_first : valid ? __ldg(d.words + pos) : 0u;
         unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
         bool bad = valid && ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) ||
                              (q >= 3 && type > 4) || (ep && q < 2));
@@ -409,7 +413,15 @@ __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long l
     }
 }
 
-__device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
+// Word `start + lane` of a road (0 past its last word).
+__device__ __forceinline__ uint32_t first_word(const Dev &d, unsigned long long start, unsigned long long end)
+{
+    const unsigned long long pos = start + lane_id();
+    return pos <= end ? __ldg(d.words + pos) : 0u;
+}
+
+// Unpack event e (CTA-wide); adds the event's combinations to n_comb.
+__device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned long long &n_comb)
 {
     P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
     const unsigned n_events = ldcg(&d.ctrl->n_events);
@@ -423,16 +435,24 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
         s.n_ep = 0;
     }
     __syncthreads();
-    // road boundaries: ranks of the EP words of [w0, w1]
+    // road boundaries: ranks of the EP words of [w0, w1].  Each thread takes
+    // a run of up to 64 consecutive words per round (one block scan).
     unsigned running = 0;
-    for (unsigned long long t0 = w0; t0 <= w1; t0 += BLOCK) {
-        unsigned long long i = t0 + threadIdx.x;
-        bool ep = i <= w1 && ((__ldg(d.words + i) >> 30) & 1u);
+    for (unsigned long long rw = w0; rw <= w1; rw += (unsigned long long)BLOCK * 64) {
+        const unsigned long long len = min(w1 + 1 - rw, (unsigned long long)BLOCK * 64);
+        const unsigned per = (unsigned)((len + BLOCK - 1) / BLOCK);
+        const unsigned long long a = rw + (unsigned long long)threadIdx.x * per;
+        unsigned long long bits = 0;
+        for (unsigned j = 0; j < per; ++j) {
+            const unsigned long long i = a + j;
+            if (i < rw + len && ((__ldg(d.words + i) >> 30) & 1u))
+                bits |= 1ull << j;
+        }
         unsigned long long tot;
-        unsigned long long ex = block_excl_scan(ep ? 1ull : 0ull, &tot);
-        unsigned k = running + (unsigned)ex;
-        if (ep && k < MAX_ROADS_EV)
-            s.end[k] = (uint32_t)i;
+        unsigned k = running + (unsigned)block_excl_scan((unsigned long long)__popcll(bits), &tot);
+        for (; bits; bits &= bits - 1, ++k)
+            if (k < MAX_ROADS_EV)
+                s.end[k] = (uint32_t)(a + (unsigned)(__ffsll((long long)bits) - 1));
         running += (unsigned)tot;
     }
     bool last_ep = (__ldg(d.words + w1) >> 30) & 1u;
@@ -444,12 +464,29 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
         s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
     unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
 
-    // decode: warp per road
+    // decode: warp per road; the first words of the warp's next road are
+    // loaded while it decodes the current one
     unsigned long long err = ~0ull;
-    for (unsigned k = warp_id(); k < nr; k += WARPS) {
-        unsigned long long start = k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1;
-        unsigned long long end = k < running ? (unsigned long long)s.end[k] : w1;
-        decode_road(d, s, k, start, end, err);
+    {
+        unsigned k = warp_id();
+        unsigned long long start = 0, end = 0;
+        uint32_t w_next = 0;
+        if (k < nr) {
+            start = k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1;
+            end = k < running ? (unsigned long long)s.end[k] : w1;
+            w_next = first_word(d, start, end);
+        }
+        for (; k < nr; k += WARPS) {
+            const unsigned long long cs = start, ce = end;
+            const uint32_t w_cur = w_next;
+            const unsigned kn = k + WARPS;
+            if (kn < nr) {
+                start = (unsigned long long)s.end[kn - 1] + 1;
+                end = kn < running ? (unsigned long long)s.end[kn] : w1;
+                w_next = first_word(d, start, end);
+            }
+            decode_road(d, s, k, cs, ce, w_cur, err);
+        }
     }
     err = warp_min_u64(err);
     if (lane_id() == 0 && err != ~0ull)
@@ -484,7 +521,6 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
         }
     }
     __syncthreads();
-    unsigned long long n_comb = 0;
     for (unsigned k = warp_id(); k < nr; k += WARPS) {
         uint32_t pk = s.pk[k];
         unsigned long long xm = 0;
@@ -530,7 +566,17 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem)
             }
         }
     }
-    if (lane_id() == 0 && n_comb)
+}
+
+// P2 over the event queue; one combination-count atomic per CTA
+__device__ void p2_phase(const Dev &d, unsigned char *smem)
+{
+    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
+    unsigned long long n_comb = 0;
+    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
+        p2_event(d, e, smem, n_comb);
+    n_comb = block_sum(n_comb);
+    if (threadIdx.x == 0 && n_comb)
         atomicAdd(&d.ctrl->n_comb, n_comb);
 }
 
@@ -1205,8 +1251,6 @@ __device__ void clear_hash(const Dev &d, unsigned i)
 // the persistent fused kernel
 // ---------------------------------------------------------------------------
 
-// queue indices
-enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
 
 __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
 {
@@ -1229,9 +1273,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     if (!grid_sync(d))
         return;
 
-    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
-    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
-        p2_event(d, e, smem);
+    p2_phase(d, smem);
     if (!grid_sync(d))
         return;
     if (ldcg(&d.ctrl->err_inv) != 0ull)
@@ -1283,9 +1325,7 @@ __global__ void __launch_bounds__(BLOCK) k_p2(Dev d)
     extern __shared__ __align__(16) unsigned char smem[];
     if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
         return;
-    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
-    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
-        p2_event(d, e, smem);
+    p2_phase(d, smem);
 }
 
 __device__ __forceinline__ bool stop_after_unpack(const Dev &d)
