@@ -284,6 +284,9 @@ def gpu_arm(args):
         "latency_us": {"p50": 1e3 * float(np.percentile(times, 50)),
                        "p99": 1e3 * float(np.percentile(times, 99))},
         "tracks_per_step": stats["n_tracks"], "status": stats["status"],
+        "phase_us": dict(zip(["word_scan", "event_scatter", "unpack", "fit_cut_local_warrior",
+                              "cross_road_warrior", "output"],
+                             [round(x / 1e3, 1) for x in stats["phase_ns"]])),
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved / peak_tops, "traffic": None,

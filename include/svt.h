@@ -106,6 +106,12 @@ typedef struct {
     int32_t status;           /* SVT_OK or the batch's error code */
     uint32_t pad;
     uint64_t error_word;      /* word position of the first fault (if any) */
+    uint64_t phase_ns[6];     /* SVT_PERSISTENT: device time of each stage, from the
+                                 first CTA's view of the grid barriers: word scan,
+                                 event scatter, unpack, fit + cut + road-local
+                                 warrior, cross-road warrior, output (to the last
+                                 CTA's exit); 0 when a stage did not complete, and
+                                 for SVT_PLAIN */
 } svt_stats;
 
 /* Create a context on `device` (cudaSetDevice is called).  Allocates all

@@ -45,10 +45,12 @@ class Stats(C.Structure):
     _fields_ = [("n_events", C.c_uint64), ("n_roads", C.c_uint64),
                 ("n_combinations", C.c_uint64), ("n_passing", C.c_uint64),
                 ("n_tracks", C.c_uint64), ("status", C.c_int32), ("pad", C.c_uint32),
-                ("error_word", C.c_uint64)]
+                ("error_word", C.c_uint64), ("phase_ns", C.c_uint64 * 6)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "phase_ns")}
+        d["phase_ns"] = list(self.phase_ns)
+        return d
 
 
 # every entry point of include/svt.h with its argument types

@@ -405,6 +405,10 @@ int svt_get_stats(svt_ctx *c, svt_stats *out, void *stream)
     out->n_tracks = h.n_out;
     out->status = status_of(h);
     out->error_word = h.err_inv ? (~h.err_inv) >> 8 : 0ull;
+    for (int k = 0; k < 6; ++k) {
+        const unsigned long long t0 = h.t_phase[k], t1 = h.t_phase[k + 1];
+        out->phase_ns[k] = (t0 && t1 && t1 >= t0) ? t1 - t0 : 0ull;
+    }
     return SVT_OK;
 }
 

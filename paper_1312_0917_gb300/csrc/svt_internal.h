@@ -48,6 +48,8 @@ struct Ctrl {
     unsigned int pad0;
     unsigned long long n_comb, n_pass, n_out;
     unsigned long long pad1[2];
+    unsigned long long t_phase[8];   // persistent kernel: globaltimer at its start, after each
+                                     // barrier (block 0) and at the last CTA's exit (max)
 };
 
 // Unpacked road, 16 bytes.  pk: n[l] in bits 4l..4l+3 (l < 5), excluded layer

@@ -257,6 +257,13 @@ __device__ bool grid_sync(const Dev &d)
     return s_ok != 0;
 }
 
+// phase timestamp k of the persistent kernel (block 0, thread 0)
+__device__ __forceinline__ void stamp(const Dev &d, unsigned k)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        d.ctrl->t_phase[k] = globaltimer_ns();
+}
+
 // work-queue indices (Ctrl::q)
 enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
 
@@ -1258,6 +1265,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     if (d.skip_arrival && blockIdx.x == 0)
         return;   // test hook: this CTA never arrives at the first barrier
     const unsigned nb = gridDim.x;
+    stamp(d, 0);
 
     for (unsigned c = grab(d, Q_P0); c < d.n_chunks_w; c = grab(d, Q_P0))
         p0_item(d, c);
@@ -1265,6 +1273,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         p0_finish(d);
     if (!grid_sync(d))
         return;
+    stamp(d, 1);
     if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
         return;
 
@@ -1272,16 +1281,19 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         p1_item(d, c);
     if (!grid_sync(d))
         return;
+    stamp(d, 2);
 
     p2_phase(d, smem);
     if (!grid_sync(d))
         return;
+    stamp(d, 3);
     if (ldcg(&d.ctrl->err_inv) != 0ull)
         return;   // a data fault: no tracks
 
     p3_phase<false>(d, smem, Q_BIG, Q_SMALL);
     if (!grid_sync(d))
         return;
+    stamp(d, 4);
 
     const unsigned n_roads = ldcg(&d.ctrl->n_roads);
     const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
@@ -1291,6 +1303,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         p4_finish(d, n_chunks);
     if (!grid_sync(d))
         return;
+    stamp(d, 5);
     if (!(ldcg(&d.ctrl->flags) & FLAG_CAPACITY))
         for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
             p5_item<false>(d, c, n_roads);
@@ -1298,6 +1311,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += nb * BLOCK)
         clear_hash(d, i);
+    if (threadIdx.x == 0)
+        atomicMax(&d.ctrl->t_phase[6], globaltimer_ns());
 }
 
 // ---------------------------------------------------------------------------

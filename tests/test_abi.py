@@ -49,7 +49,7 @@ def test_struct_layouts():
     assert B.CONST_DTYPE.itemsize == 96
     assert B.TRACK_DTYPE.itemsize == 40 and B.TRACK_DTYPE.fields["chi2"][1] == 24
     assert B.ROAD_DTYPE.itemsize == 100 and B.ROAD_DTYPE.fields["coord"][1] == 20
-    assert C.sizeof(B.Limits) == 40 and C.sizeof(B.Stats) == 56
+    assert C.sizeof(B.Limits) == 40 and C.sizeof(B.Stats) == 104
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):
