@@ -633,6 +633,7 @@ struct BlockGroup {
 struct RoadSmem {
     int4 *A;                  // [32] partial chi-square sums of fitted slot j, hit d
     uint16_t *co;             // [40] coordinates of the road (layer * 8 + hit)
+    const svt_const_set *cs;  // the road's constant set (a copy in shared memory)
     uint8_t *canon;           // [40] lowest hit index with the same coordinate, per layer
     unsigned long long *Q;    // pair tables
     unsigned long long *K;    // key of each distinct fit (excluded-layer hit 0)
@@ -649,7 +650,6 @@ struct RoadInfo {
     unsigned long long M[3];         // magic divisors of m[0..2]
     unsigned N4, off[7];             // distinct fits; pair-table offsets
     int curv, phi;
-    const svt_const_set *cs;
 };
 
 // pair p -> slots (a, b), complement (c, e)
@@ -694,7 +694,6 @@ __device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRe
         r.off[p + 1] = r.off[p] + r.m[c_pair[p][0]] * r.m[c_pair[p][1]];
     r.curv = rec.curv;
     r.phi = rec.phi;
-    r.cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
 }
 
 __device__ __forceinline__ void digits4(const RoadInfo &r, unsigned f, unsigned &f0, unsigned &f1,
@@ -800,44 +799,43 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     const unsigned tid = grp.rank();
     const unsigned ne = r.n[r.excl];
 
-    // partial sums and canonical hit indices
+    // canonical hit indices: the lowest index with the same coordinate
+    bool dup = false;
     for (unsigned idx = tid; idx < 40; idx += G::SIZE) {
-        unsigned l = idx >> 3, dd = idx & 7u;
+        const unsigned l = idx >> 3, dd = idx & 7u;
         unsigned c = dd;
         if (dd < r.n[l]) {
-            unsigned v = sm.co[idx];
-            for (unsigned x = 0; x < dd; ++x)
-                if (c == dd && sm.co[l * 8 + x] == v)
-                    c = x;
+            const unsigned v = sm.co[idx];
+            unsigned eq = 0;
+#pragma unroll
+            for (unsigned x = 0; x < MAX_HITS; ++x)
+                eq |= (x < dd && sm.co[l * 8 + x] == v) ? 1u << x : 0u;
+            c = eq ? (unsigned)(__ffs(eq) - 1) : dd;
         }
         sm.canon[idx] = (uint8_t)c;
+        dup = dup || c != dd;
     }
+    // partial chi-square sums of every fitted hit
     if (!PLAIN) {
+        const svt_const_set *cs = sm.cs;
         for (unsigned idx = tid; idx < 32; idx += G::SIZE) {
             unsigned j = idx >> 3, dd = idx & 7u;
             int4 a = make_int4(0, 0, 0, 0);
             if (dd < r.m[j]) {
                 int h = sm.co[r.L[j] * 8 + dd];
-                const svt_const_set *cs = r.cs;
-                a.x = (int)__ldg(&cs->C[0][j]) * h;
-                a.y = (int)__ldg(&cs->C[1][j]) * h;
-                a.z = (int)__ldg(&cs->C[2][j]) * h;
+                a.x = (int)cs->C[0][j] * h;
+                a.y = (int)cs->C[1][j] * h;
+                a.z = (int)cs->C[2][j] * h;
                 if (j == 0) {   // curvature, phi and 4096 * offset ride on slot 0
-                    a.x += (int)__ldg(&cs->C[0][4]) * r.curv + (int)__ldg(&cs->C[0][5]) * r.phi +
-                           4096 * __ldg(&cs->k[0]);
-                    a.y += (int)__ldg(&cs->C[1][4]) * r.curv + (int)__ldg(&cs->C[1][5]) * r.phi +
-                           4096 * __ldg(&cs->k[1]);
-                    a.z += (int)__ldg(&cs->C[2][4]) * r.curv + (int)__ldg(&cs->C[2][5]) * r.phi +
-                           4096 * __ldg(&cs->k[2]);
+                    a.x += (int)cs->C[0][4] * r.curv + (int)cs->C[0][5] * r.phi + 4096 * cs->k[0];
+                    a.y += (int)cs->C[1][4] * r.curv + (int)cs->C[1][5] * r.phi + 4096 * cs->k[1];
+                    a.z += (int)cs->C[2][4] * r.curv + (int)cs->C[2][5] * r.phi + 4096 * cs->k[2];
                 }
             }
             sm.A[idx] = a;
         }
     }
     grp.sync();
-    bool dup = false;
-    for (unsigned idx = tid; idx < 40; idx += G::SIZE)
-        dup = dup || sm.canon[idx] != (idx & 7u);
     dup = grp.any(dup);
 
     // keys of all distinct fits
@@ -1039,6 +1037,7 @@ struct P3Big {
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_BIG];
     unsigned long long K[N4_MAX];
+    svt_const_set cs;
     uint16_t co[40];
     uint8_t canon[40];
     unsigned cnt[WARPS + 1];
@@ -1048,14 +1047,23 @@ struct P3Warp {
     unsigned long long S[SURV_SLOTS];
     unsigned long long Q[QTAB_SMALL];
     unsigned long long K[N4_SMALL_MAX];
+    svt_const_set cs;
     uint16_t co[40];
     uint8_t canon[40];
 };
 
+// The 24 words of the constant set of a road record (svt_const_set is 96 B).
+__device__ __forceinline__ const uint32_t *const_words(const Dev &d, unsigned set)
+{
+    return reinterpret_cast<const uint32_t *>(d.consts + min(set, (unsigned)(N_SETS - 1)));
+}
+constexpr unsigned CONST_WORDS = sizeof(svt_const_set) / 4;
+static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane");
+
 // Roads with more than small_n4 distinct fits (listed in P2) are fitted by a
 // whole CTA; then every warp takes runs of WARP_ROADS consecutive roads and
-// fits the others itself, loading the next road's record and coordinates
-// while it fits the current one.
+// fits the others itself.  While it fits road g it has the record of road
+// g + 2 and the coordinates and constants of road g + 1 in flight.
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
@@ -1065,12 +1073,15 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         P3Big &s = *reinterpret_cast<P3Big *>(smem);
         BlockGroup grp{s.cnt};
-        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S};
+        RoadSmem sm{s.A, s.co, &s.cs, s.canon, s.Q, s.K, s.S};
+        uint32_t *cst = reinterpret_cast<uint32_t *>(&s.cs);
         for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig)) {
             const unsigned g = min(ldcg(d.big_list + i), d.max_roads - 1);
             if (threadIdx.x < 40)
                 s.co[threadIdx.x] = ldcg(d.coords + (size_t)g * 40 + threadIdx.x);
             const RoadRec rec = ldcg(d.roads + g);
+            if (threadIdx.x < CONST_WORDS)
+                cst[threadIdx.x] = __ldg(const_words(d, rec.set) + threadIdx.x);
             __syncthreads();
             fit_road<BlockGroup, PLAIN>(d, grp, sm, g, rec, npass);
         }
@@ -1079,7 +1090,8 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         P3Warp &s = reinterpret_cast<P3Warp *>(smem)[warp_id()];
         WarpGroup grp;
-        RoadSmem sm{s.A, s.co, s.canon, s.Q, s.K, s.S};
+        RoadSmem sm{s.A, s.co, &s.cs, s.canon, s.Q, s.K, s.S};
+        uint32_t *cst = reinterpret_cast<uint32_t *>(&s.cs);
         const unsigned lane = lane_id();
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
         while (true) {
@@ -1093,16 +1105,26 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
             RoadRec next = ldcg(d.roads + g0);
             uint16_t nco0 = ldcg(d.coords + (size_t)g0 * 40 + lane);
             uint16_t nco1 = lane < 8 ? ldcg(d.coords + (size_t)g0 * 40 + 32 + lane) : (uint16_t)0;
+            uint32_t ncst = lane < CONST_WORDS ? __ldg(const_words(d, next.set) + lane) : 0u;
+            RoadRec next2 = next;
+            if (g0 + 1 < g1)
+                next2 = ldcg(d.roads + g0 + 1);
             for (unsigned g = g0; g < g1; ++g) {
                 const RoadRec rec = next;
                 s.co[lane] = nco0;
                 if (lane < 8)
                     s.co[32 + lane] = nco1;
+                if (lane < CONST_WORDS)
+                    cst[lane] = ncst;
                 if (g + 1 < g1) {
-                    next = ldcg(d.roads + g + 1);
+                    next = next2;
                     nco0 = ldcg(d.coords + (size_t)(g + 1) * 40 + lane);
                     if (lane < 8)
                         nco1 = ldcg(d.coords + (size_t)(g + 1) * 40 + 32 + lane);
+                    if (lane < CONST_WORDS)
+                        ncst = __ldg(const_words(d, next.set) + lane);
+                    if (g + 2 < g1)
+                        next2 = ldcg(d.roads + g + 2);
                 }
                 unsigned long long N;
                 unsigned N4;
