@@ -1060,10 +1060,352 @@ __device__ __forceinline__ const uint32_t *const_words(const Dev &d, unsigned se
 constexpr unsigned CONST_WORDS = sizeof(svt_const_set) / 4;
 static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane");
 
+// ---------------------------------------------------------------------------
+// P3, flat path: a warp fits a run of small roads together, one lane per
+// table entry across the roads of the run (fit, pair tables, survivors), so
+// the per-road work is spread over the lanes instead of repeated per road.
+// It takes roads with no cross-road candidate flag and no repeated
+// coordinate in a layer; other small roads go through fit_road.
+// ---------------------------------------------------------------------------
+
+constexpr unsigned FLAT_K = 128, FLAT_Q = 128, FLAT_A = 64;
+
+// One road of a run, in the warp's shared memory.
+struct FlatRoad {
+    unsigned g, N4, E, kb, qb, ab, ne, key_hi, set;
+    int curv, phi;
+    unsigned m[4], L[4], st[4], SL[4], aoff[4];
+    unsigned off[6];
+    unsigned long long M[3];
+    unsigned long long cb;        // plain mode: first combination of the road
+};
+
+struct P3Flat {
+    int4 A[FLAT_A];                       // partial chi-square sums, [ab + aoff[j] + hit]
+    unsigned long long K[FLAT_K];         // keys of distinct fits, [kb + f]
+    unsigned long long Q[FLAT_Q];         // pair tables, [qb + off[p] + x * m_b + y]
+    FlatRoad rd[WARP_ROADS];
+    uint16_t co[WARP_ROADS][40];
+    unsigned cnt[WARP_ROADS];             // survivors found so far
+};
+
+// the six pairs of fitted slots (a, b) and their complements (c, e)
+__device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_b(unsigned p) { return (0x332321u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_c(unsigned p) { return (0x000112u >> (4 * p)) & 15u; }
+__device__ __forceinline__ unsigned pair_e(unsigned p) { return (0x123233u >> (4 * p)) & 15u; }
+
+// The roads of a sub-run, in order, are the set bits of `sub` (lanes of the
+// run).  A table over the sub-run packs the first entry of its k-th road in
+// byte k of (lo, hi) (0xFF past the last road) and the road's lane in nibble
+// k of `lanes`.
+struct FlatIndex {
+    unsigned lo, hi, lanes;
+    // lane of the road that owns entry t
+    __device__ unsigned owner(unsigned t) const
+    {
+        unsigned k = 0;
+#pragma unroll
+        for (unsigned q = 1; q < 4; ++q)
+            k += t >= ((lo >> (8 * q)) & 0xFFu);
+#pragma unroll
+        for (unsigned q = 0; q < 4; ++q)
+            k += t >= ((hi >> (8 * q)) & 0xFFu);
+        return (lanes >> (4 * k)) & 15u;
+    }
+};
+
+// Build the index from each road lane's first entry (every lane calls it).
+__device__ __forceinline__ FlatIndex flat_index(unsigned first, unsigned sub)
+{
+    FlatIndex x{0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    unsigned rest = sub;
+    for (unsigned k = 0; k < WARP_ROADS && rest; ++k) {
+        const unsigned ln = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const unsigned v = __shfl_sync(FULL_MASK, first, ln) & 0xFFu;
+        if (k < 4)
+            x.lo = (x.lo & ~(0xFFu << (8 * k))) | (v << (8 * k));
+        else
+            x.hi = (x.hi & ~(0xFFu << (8 * (k - 4)))) | (v << (8 * (k - 4)));
+        x.lanes |= ln << (4 * k);
+    }
+    return x;
+}
+
+// Fit roads g0 .. g0 + R - 1 (R <= WARP_ROADS) with one warp.  `region` is
+// the warp's shared memory, seen as P3Flat for the flat sub-runs and then as
+// P3Warp for the roads that fit_road takes.  Roads whose distinct fits exceed
+// small_n4 are skipped (a CTA fits them).
+template <bool PLAIN>
+__device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsigned R,
+                        unsigned long long &npass)
+{
+    P3Flat &F = *reinterpret_cast<P3Flat *>(region);
+    const unsigned lane = lane_id();
+
+    // the run's records and coordinates
+    RoadRec rec = {};
+    unsigned long long N = 0;
+    unsigned N4 = 0;
+    if (lane < R) {
+        rec = ldcg(d.roads + g0 + lane);
+        road_sizes(rec.pk, N, N4);
+    }
+    for (unsigned idx = lane; idx < R * 40; idx += 32)
+        F.co[idx / 40][idx % 40] = ldcg(d.coords + (size_t)g0 * 40 + idx);
+    __syncwarp();
+
+    // lane i < R: the shape of road i and whether the flat path takes it
+    const bool small = lane < R && N > 0 && N4 <= (unsigned)d.small_n4;
+    FlatRoad fr;
+    unsigned E = 0, asum = 0;
+    bool flat = false;
+    if (small) {
+        const uint32_t pk = rec.pk;
+        const unsigned excl = min((pk >> 20) & 7u, 4u);
+        unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            n[l] = min((pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
+            S5[l] = S;
+            S *= n[l];
+        }
+        unsigned j = 0, st = 1;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            if (l == excl)
+                continue;
+            fr.L[j] = l;
+            fr.m[j] = n[l];
+            fr.st[j] = st;
+            fr.SL[j] = S5[l];
+            fr.aoff[j] = asum;
+            asum += n[l];
+            st *= n[l];
+            ++j;
+        }
+        for (unsigned p = 0; p < 6; ++p) {
+            fr.off[p] = E;
+            E += fr.m[pair_a(p)] * fr.m[pair_b(p)];
+        }
+        for (unsigned s = 0; s < 3; ++s)
+            fr.M[s] = c_magic[fr.m[s]];
+        fr.g = g0 + lane;
+        fr.N4 = N4;
+        fr.E = E;
+        fr.ne = n[excl];
+        fr.key_hi = rec.pk >> 24;
+        fr.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+        fr.curv = rec.curv;
+        fr.phi = rec.phi;
+        fr.cb = PLAIN ? ldcg(d.comb_off + g0 + lane) : 0ull;
+        // a coordinate repeated within a layer needs the canonical-index path
+        bool dup = false;
+        for (unsigned l = 0; l < N_LAYERS; ++l)
+            for (unsigned x = 1; x < n[l]; ++x)
+                for (unsigned y = 0; y < x; ++y)
+                    dup = dup || F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y];
+        const bool cand = (pk >> 23) & 1u;
+        flat = !cand && !dup && N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
+    }
+
+    // flat sub-runs: a prefix of the remaining flat roads that fits the tables
+    unsigned todo = __ballot_sync(FULL_MASK, flat);
+    while (todo) {
+        const bool mine = (todo >> lane) & 1u;
+        unsigned ik = mine ? N4 : 0u, iq = mine ? E : 0u, ia = mine ? asum : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {   // inclusive prefix sums over the lanes
+            const unsigned uk = __shfl_up_sync(FULL_MASK, ik, o);
+            const unsigned uq = __shfl_up_sync(FULL_MASK, iq, o);
+            const unsigned ua = __shfl_up_sync(FULL_MASK, ia, o);
+            if ((int)lane >= o) {
+                ik += uk;
+                iq += uq;
+                ia += ua;
+            }
+        }
+        const bool take = mine && ik <= FLAT_K && iq <= FLAT_Q && ia <= FLAT_A;
+        const unsigned sub = __ballot_sync(FULL_MASK, take);   // the first roads left
+        const unsigned s1 = 31 - __clz(sub);
+        const unsigned nk = __shfl_sync(FULL_MASK, ik, s1), nq = __shfl_sync(FULL_MASK, iq, s1),
+                       na = __shfl_sync(FULL_MASK, ia, s1);
+        if (take) {
+            fr.kb = ik - N4;
+            fr.qb = iq - E;
+            fr.ab = ia - asum;
+            F.rd[lane] = fr;
+            F.cnt[lane] = 0;
+        }
+        const FlatIndex xk = flat_index(ik - N4, sub), xq = flat_index(iq - E, sub),
+                        xa = flat_index(ia - asum, sub);
+        __syncwarp();
+
+        // partial chi-square sums of every fitted hit of every road
+        if (!PLAIN) {
+            for (unsigned t = lane; t < na; t += 32) {
+                const unsigned ri = xa.owner(t);
+                const FlatRoad &r = F.rd[ri];
+                const unsigned local = t - r.ab;
+                const unsigned j = (local >= r.aoff[1]) + (local >= r.aoff[2]) + (local >= r.aoff[3]);
+                const unsigned dd = local - r.aoff[j];
+                const int h = F.co[ri][r.L[j] * 8 + dd];
+                const svt_const_set *cs = d.consts + r.set;
+                int4 a;
+                a.x = (int)__ldg(&cs->C[0][j]) * h;
+                a.y = (int)__ldg(&cs->C[1][j]) * h;
+                a.z = (int)__ldg(&cs->C[2][j]) * h;
+                a.w = 0;
+                if (j == 0) {   // curvature, phi and 4096 * offset ride on slot 0
+                    a.x += (int)__ldg(&cs->C[0][4]) * r.curv + (int)__ldg(&cs->C[0][5]) * r.phi +
+                           4096 * __ldg(&cs->k[0]);
+                    a.y += (int)__ldg(&cs->C[1][4]) * r.curv + (int)__ldg(&cs->C[1][5]) * r.phi +
+                           4096 * __ldg(&cs->k[1]);
+                    a.z += (int)__ldg(&cs->C[2][4]) * r.curv + (int)__ldg(&cs->C[2][5]) * r.phi +
+                           4096 * __ldg(&cs->k[2]);
+                }
+                F.A[t] = a;
+            }
+            __syncwarp();
+        }
+
+        // keys of the distinct fits
+        const long long cut = d.cut;
+        for (unsigned t = lane; t < nk; t += 32) {
+            const FlatRoad &r = F.rd[xk.owner(t)];
+            const unsigned f = t - r.kb;
+            const unsigned q0 = divm(f, r.M[0]), f0 = f - q0 * r.m[0];
+            const unsigned q1 = divm(q0, r.M[1]), f1 = q0 - q1 * r.m[1];
+            const unsigned f3 = divm(q1, r.M[2]), f2 = q1 - f3 * r.m[2];
+            const unsigned comb = f0 * r.SL[0] + f1 * r.SL[1] + f2 * r.SL[2] + f3 * r.SL[3];
+            unsigned long long key;
+            if (PLAIN) {
+                key = ldcg(d.fit_key + r.cb + comb);
+            } else {
+                const int4 a0 = F.A[r.ab + r.aoff[0] + f0], a1 = F.A[r.ab + r.aoff[1] + f1];
+                const int4 a2 = F.A[r.ab + r.aoff[2] + f2], a3 = F.A[r.ab + r.aoff[3] + f3];
+                const int sx = a0.x + a1.x + a2.x + a3.x;
+                const int sy = a0.y + a1.y + a2.y + a3.y;
+                const int sz = a0.z + a1.z + a2.z + a3.z;
+                const long long chi2 = sq(sx >> 12) + sq(sy >> 12) + sq(sz >> 12);
+                const bool pass = chi2 <= cut;
+                npass += pass ? r.ne : 0u;
+                key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
+            }
+            F.K[t] = key;
+        }
+        __syncwarp();
+
+        // pair tables: minimum key over the fits with given hits on two slots
+        for (unsigned t = lane; t < nq; t += 32) {
+            const FlatRoad &r = F.rd[xq.owner(t)];
+            const unsigned local = t - r.qb;
+            const unsigned p = (local >= r.off[1]) + (local >= r.off[2]) + (local >= r.off[3]) +
+                               (local >= r.off[4]) + (local >= r.off[5]);
+            const unsigned a = pair_a(p), b = pair_b(p), c = pair_c(p), e = pair_e(p);
+            const unsigned lp = local - r.off[p], mb = r.m[b];
+            const unsigned x = lp / mb, y = lp - x * mb;
+            const unsigned fb = r.kb + x * r.st[a] + y * r.st[b];
+            const unsigned mc = r.m[c], me = r.m[e], sc = r.st[c], se = r.st[e];
+            unsigned long long mn = NO_KEY;
+            for (unsigned z = 0; z < mc; ++z)
+                for (unsigned w = 0; w < me; ++w) {
+                    const unsigned long long k = F.K[fb + z * sc + w * se];
+                    mn = k < mn ? k : mn;
+                }
+            F.Q[t] = mn;
+        }
+        __syncwarp();
+
+        // survivors: keys that are the minimum of all six of their pair tables
+        for (unsigned base = 0; base < nk; base += 32) {
+            const unsigned t = base + lane;
+            unsigned ri = 0;
+            bool surv = false;
+            unsigned long long key = NO_KEY;
+            if (t < nk) {
+                ri = xk.owner(t);
+                const FlatRoad &r = F.rd[ri];
+                key = F.K[t];
+                if (key != NO_KEY) {
+                    const unsigned f = t - r.kb;
+                    unsigned fd[4];
+                    const unsigned q0 = divm(f, r.M[0]);
+                    fd[0] = f - q0 * r.m[0];
+                    const unsigned q1 = divm(q0, r.M[1]);
+                    fd[1] = q0 - q1 * r.m[1];
+                    fd[3] = divm(q1, r.M[2]);
+                    fd[2] = q1 - fd[3] * r.m[2];
+                    surv = true;
+#pragma unroll
+                    for (unsigned p = 0; p < 6; ++p) {
+                        const unsigned a = pair_a(p), b = pair_b(p);
+                        surv = surv && F.Q[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == key;
+                    }
+                }
+            }
+            const unsigned sv = __ballot_sync(FULL_MASK, surv);
+            // lanes of road ri in this pass: its entries [kb, kb + N4) within [base, base + 32)
+            if (surv) {
+                const FlatRoad &r = F.rd[ri];
+                const unsigned lo = max(r.kb, base) - base;
+                const unsigned pos = F.cnt[ri] + __popc(sv & lanemask_lt() & ~((1u << lo) - 1u));
+                if (pos < SURV_SLOTS)
+                    d.surv_pool[(size_t)r.g * SURV_SLOTS + pos] = key;
+                else
+                    raise_flag(d, FLAG_INTERNAL);
+            }
+            __syncwarp();
+            if ((sub >> lane) & 1u) {   // road of this lane: add this pass's survivors
+                const unsigned lo = min(max(fr.kb, base), base + 32) - base;
+                const unsigned hi = min(max(fr.kb + N4, base), base + 32) - base;
+                if (lo < 32) {
+                    const unsigned below_hi = hi >= 32 ? ~0u : (1u << hi) - 1u;
+                    F.cnt[lane] += __popc(sv & below_hi & ~((1u << lo) - 1u));
+                }
+            }
+            __syncwarp();
+        }
+        if ((sub >> lane) & 1u)
+            d.surv_cnt[g0 + lane] = (uint8_t)min(F.cnt[lane], (unsigned)SURV_SLOTS);
+        todo &= ~sub;
+        __syncwarp();
+    }
+
+    // the other small roads of the run, one at a time
+    unsigned rest = __ballot_sync(FULL_MASK, small && !flat);
+    if (!rest)
+        return;
+    P3Warp &W = *reinterpret_cast<P3Warp *>(region);
+    WarpGroup grp;
+    RoadSmem sm{W.A, W.co, &W.cs, W.canon, W.Q, W.K, W.S};
+    uint32_t *cst = reinterpret_cast<uint32_t *>(&W.cs);
+    while (rest) {
+        const unsigned i = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const unsigned g = g0 + i;
+        RoadRec ri;
+        ri.event = __shfl_sync(FULL_MASK, rec.event, i);
+        ri.pk = __shfl_sync(FULL_MASK, rec.pk, i);
+        ri.curv = (int16_t)__shfl_sync(FULL_MASK, (int)rec.curv, i);
+        ri.phi = (int16_t)__shfl_sync(FULL_MASK, (int)rec.phi, i);
+        ri.set = (uint16_t)__shfl_sync(FULL_MASK, (unsigned)rec.set, i);
+        ri.pad = 0;
+        W.co[lane] = ldcg(d.coords + (size_t)g * 40 + lane);
+        if (lane < 8)
+            W.co[32 + lane] = ldcg(d.coords + (size_t)g * 40 + 32 + lane);
+        if (lane < CONST_WORDS)
+            cst[lane] = __ldg(const_words(d, ri.set) + lane);
+        __syncwarp();
+        fit_road<WarpGroup, PLAIN>(d, grp, sm, g, ri, npass);
+    }
+}
+
+// shared memory of one warp in the warp part of P3 (P3Flat, then P3Warp)
+constexpr size_t P3_WARP_BYTES = ((sizeof(P3Flat) > sizeof(P3Warp) ? sizeof(P3Flat) : sizeof(P3Warp)) + 15) / 16 * 16;
+
 // Roads with more than small_n4 distinct fits (listed in P2) are fitted by a
 // whole CTA; then every warp takes runs of WARP_ROADS consecutive roads and
-// fits the others itself.  While it fits road g it has the record of road
-// g + 2 and the coordinates and constants of road g + 1 in flight.
+// fits the others itself (fit_run).
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
@@ -1088,52 +1430,17 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     }
     __syncthreads();
     {
-        P3Warp &s = reinterpret_cast<P3Warp *>(smem)[warp_id()];
-        WarpGroup grp;
-        RoadSmem sm{s.A, s.co, &s.cs, s.canon, s.Q, s.K, s.S};
-        uint32_t *cst = reinterpret_cast<uint32_t *>(&s.cs);
-        const unsigned lane = lane_id();
+        unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
         while (true) {
             unsigned c = 0;
-            if (lane == 0)
+            if (lane_id() == 0)
                 c = atomicAdd(&d.ctrl->q[qsmall], 1u);
             c = __shfl_sync(FULL_MASK, c, 0);
             if (c >= n_runs)
                 break;
-            const unsigned g0 = c * WARP_ROADS, g1 = min(g0 + WARP_ROADS, n_roads);
-            RoadRec next = ldcg(d.roads + g0);
-            uint16_t nco0 = ldcg(d.coords + (size_t)g0 * 40 + lane);
-            uint16_t nco1 = lane < 8 ? ldcg(d.coords + (size_t)g0 * 40 + 32 + lane) : (uint16_t)0;
-            uint32_t ncst = lane < CONST_WORDS ? __ldg(const_words(d, next.set) + lane) : 0u;
-            RoadRec next2 = next;
-            if (g0 + 1 < g1)
-                next2 = ldcg(d.roads + g0 + 1);
-            for (unsigned g = g0; g < g1; ++g) {
-                const RoadRec rec = next;
-                s.co[lane] = nco0;
-                if (lane < 8)
-                    s.co[32 + lane] = nco1;
-                if (lane < CONST_WORDS)
-                    cst[lane] = ncst;
-                if (g + 1 < g1) {
-                    next = next2;
-                    nco0 = ldcg(d.coords + (size_t)(g + 1) * 40 + lane);
-                    if (lane < 8)
-                        nco1 = ldcg(d.coords + (size_t)(g + 1) * 40 + 32 + lane);
-                    if (lane < CONST_WORDS)
-                        ncst = __ldg(const_words(d, next.set) + lane);
-                    if (g + 2 < g1)
-                        next2 = ldcg(d.roads + g + 2);
-                }
-                unsigned long long N;
-                unsigned N4;
-                road_sizes(rec.pk, N, N4);
-                if (N == 0 || N4 > (unsigned)d.small_n4)
-                    continue;   // no combinations, or fitted by a CTA above
-                __syncwarp();
-                fit_road<WarpGroup, PLAIN>(d, grp, sm, g, rec, npass);
-            }
+            const unsigned g0 = c * WARP_ROADS;
+            fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
         }
     }
     npass = block_sum(npass);
@@ -1543,7 +1850,7 @@ __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
 static size_t p2_smem() { return sizeof(P2Smem); }
 static size_t p3_smem()
 {
-    size_t a = sizeof(P3Big), b = WARPS * sizeof(P3Warp);
+    size_t a = sizeof(P3Big), b = WARPS * P3_WARP_BYTES;
     return a > b ? a : b;
 }
 
