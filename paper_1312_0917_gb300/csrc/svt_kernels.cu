@@ -1068,7 +1068,7 @@ static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane
 // coordinate in a layer; other small roads go through fit_road.
 // ---------------------------------------------------------------------------
 
-constexpr unsigned FLAT_K = 128, FLAT_Q = 128, FLAT_A = 64;
+constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
 
 // One road of a run, in the warp's shared memory.
 struct FlatRoad {
@@ -1089,28 +1089,23 @@ struct P3Flat {
     unsigned cnt[WARP_ROADS];             // survivors found so far
 };
 
-// the six pairs of fitted slots (a, b) and their complements (c, e)
+// the six pairs of fitted slots (a, b)
 __device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
 __device__ __forceinline__ unsigned pair_b(unsigned p) { return (0x332321u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_c(unsigned p) { return (0x000112u >> (4 * p)) & 15u; }
-__device__ __forceinline__ unsigned pair_e(unsigned p) { return (0x123233u >> (4 * p)) & 15u; }
 
 // The roads of a sub-run, in order, are the set bits of `sub` (lanes of the
 // run).  A table over the sub-run packs the first entry of its k-th road in
-// byte k of (lo, hi) (0xFF past the last road) and the road's lane in nibble
+// half-word k of w (0xFFFF past the last road) and the road's lane in nibble
 // k of `lanes`.
 struct FlatIndex {
-    unsigned lo, hi, lanes;
+    unsigned w[4], lanes;
     // lane of the road that owns entry t
     __device__ unsigned owner(unsigned t) const
     {
-        unsigned k = 0;
+        unsigned k = t >= (w[0] >> 16);
 #pragma unroll
         for (unsigned q = 1; q < 4; ++q)
-            k += t >= ((lo >> (8 * q)) & 0xFFu);
-#pragma unroll
-        for (unsigned q = 0; q < 4; ++q)
-            k += t >= ((hi >> (8 * q)) & 0xFFu);
+            k += (t >= (w[q] & 0xFFFFu)) + (t >= (w[q] >> 16));
         return (lanes >> (4 * k)) & 15u;
     }
 };
@@ -1118,17 +1113,18 @@ struct FlatIndex {
 // Build the index from each road lane's first entry (every lane calls it).
 __device__ __forceinline__ FlatIndex flat_index(unsigned first, unsigned sub)
 {
-    FlatIndex x{0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
+    FlatIndex x{{0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, 0u};
     unsigned rest = sub;
-    for (unsigned k = 0; k < WARP_ROADS && rest; ++k) {
-        const unsigned ln = __ffs(rest) - 1;
+#pragma unroll
+    for (unsigned k = 0; k < WARP_ROADS; ++k) {
+        const unsigned ln = rest ? __ffs(rest) - 1 : 0u;
+        const unsigned v = __shfl_sync(FULL_MASK, first, ln) & 0xFFFFu;
+        if (rest) {
+            const unsigned sh = 16 * (k & 1u);
+            x.w[k >> 1] = (x.w[k >> 1] & ~(0xFFFFu << sh)) | (v << sh);
+            x.lanes |= ln << (4 * k);
+        }
         rest &= rest - 1;
-        const unsigned v = __shfl_sync(FULL_MASK, first, ln) & 0xFFu;
-        if (k < 4)
-            x.lo = (x.lo & ~(0xFFu << (8 * k))) | (v << (8 * k));
-        else
-            x.hi = (x.hi & ~(0xFFu << (8 * (k - 4)))) | (v << (8 * (k - 4)));
-        x.lanes |= ln << (4 * k);
     }
     return x;
 }
@@ -1236,8 +1232,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             F.rd[lane] = fr;
             F.cnt[lane] = 0;
         }
-        const FlatIndex xk = flat_index(ik - N4, sub), xq = flat_index(iq - E, sub),
-                        xa = flat_index(ia - asum, sub);
+        const FlatIndex xk = flat_index(ik - N4, sub), xa = flat_index(ia - asum, sub);
         __syncwarp();
 
         // partial chi-square sums of every fitted hit of every road
@@ -1268,7 +1263,14 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             __syncwarp();
         }
 
-        // keys of the distinct fits
+        // pair tables start empty
+        for (unsigned t = lane; t < nq; t += 32)
+            F.Q[t] = NO_KEY;
+        __syncwarp();
+
+        // keys of the distinct fits; each passing key lowers its entry in
+        // the six pair tables (minimum key over the fits with the same hits
+        // on two fitted slots)
         const long long cut = d.cut;
         for (unsigned t = lane; t < nk; t += 32) {
             const FlatRoad &r = F.rd[xk.owner(t)];
@@ -1292,27 +1294,14 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
             }
             F.K[t] = key;
-        }
-        __syncwarp();
-
-        // pair tables: minimum key over the fits with given hits on two slots
-        for (unsigned t = lane; t < nq; t += 32) {
-            const FlatRoad &r = F.rd[xq.owner(t)];
-            const unsigned local = t - r.qb;
-            const unsigned p = (local >= r.off[1]) + (local >= r.off[2]) + (local >= r.off[3]) +
-                               (local >= r.off[4]) + (local >= r.off[5]);
-            const unsigned a = pair_a(p), b = pair_b(p), c = pair_c(p), e = pair_e(p);
-            const unsigned lp = local - r.off[p], mb = r.m[b];
-            const unsigned x = lp / mb, y = lp - x * mb;
-            const unsigned fb = r.kb + x * r.st[a] + y * r.st[b];
-            const unsigned mc = r.m[c], me = r.m[e], sc = r.st[c], se = r.st[e];
-            unsigned long long mn = NO_KEY;
-            for (unsigned z = 0; z < mc; ++z)
-                for (unsigned w = 0; w < me; ++w) {
-                    const unsigned long long k = F.K[fb + z * sc + w * se];
-                    mn = k < mn ? k : mn;
+            if (key != NO_KEY) {
+                const unsigned fd[4] = {f0, f1, f2, f3};
+#pragma unroll
+                for (unsigned p = 0; p < 6; ++p) {
+                    const unsigned a = pair_a(p), b = pair_b(p);
+                    atomicMin(&F.Q[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], key);
                 }
-            F.Q[t] = mn;
+            }
         }
         __syncwarp();
 
