@@ -196,6 +196,75 @@ int svt_last_launch_count(svt_ctx *ctx);
 
 const char *svt_strerror(int code);
 
+/* ---- serving: continuous batching of independent requests -------------- *
+ * Not a step of the paper's chain: it serves the chain to a stream of
+ * independent requests (batches of events), the low-latency trigger setting
+ * of the paper's data-flow tests (Sec. III, Fig. 1).  A server owns `n_slots`
+ * slots; each holds a context sized for one request, a CUDA stream and pinned
+ * host staging, with the constants resident.  svt_server_submit admits a
+ * request as soon as a slot is free and enqueues its host->device copy, its
+ * kernel and the read of its status at once, so requests admitted while
+ * others run overlap on the device.  A progress thread of the server fetches
+ * each result's tracks once their count is known; results are returned in
+ * completion order.  Each request's result is the same as running it alone
+ * through svt_unpack / svt_fit_events / svt_get_tracks. */
+typedef struct svt_server svt_server;
+
+typedef struct {
+    uint32_t n_slots;          /* requests on the device at once; 0 = as many as a quarter of
+                                  the free device memory holds, at most 8 */
+    uint32_t ctas_per_sm;      /* CTAs per SM of each request's persistent kernel (0 = 1) */
+    uint32_t max_ctas;         /* grid cap of each request's kernel (0 = SMs x ctas_per_sm) */
+    int32_t mode;              /* SVT_PERSISTENT or SVT_PLAIN (0 is SVT_PLAIN) */
+    uint64_t max_words;        /* words per request (0 = 1 << 21) */
+    uint32_t max_events;       /* events per request (0 = 4096) */
+    uint32_t max_roads;        /* roads per request (0 = 1 << 17) */
+    uint64_t max_tracks;       /* tracks per request (0 = 1 << 20) */
+    uint32_t hash_slots;       /* cross-road group table per slot, power of 2 (0 = 1 << 20) */
+    uint32_t pad;
+    uint64_t max_combinations; /* SVT_PLAIN combination buffers per slot (0 = 1 << 24) */
+} svt_server_config;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t status;            /* the request's SVT_* status */
+    uint32_t pad;
+    uint64_t n_tracks;         /* surviving tracks (0 unless status is SVT_OK) */
+    uint64_t n_events;
+    uint64_t n_combinations;
+    uint64_t latency_ns;       /* svt_server_submit entry -> tracks in host memory */
+} svt_server_result;
+
+/* Create a server on `device` with the constant sets (HOST memory, as for
+ * svt_load_constants) and chi-square cut resident in every slot.  config
+ * NULL = defaults with SVT_PLAIN; the chosen values are in
+ * svt_server_get_config.  Starts the server's progress thread. */
+int svt_server_create(svt_server **out, int device, const svt_server_config *config,
+                      const svt_const_set *sets, uint32_t n_sets, int64_t chi2_cut);
+
+/* Wait (at most 10 s) for the requests in flight, stop the progress thread and
+ * free every slot.  Results not taken are dropped. */
+void svt_server_destroy(svt_server *srv);
+
+int svt_server_get_config(svt_server *srv, svt_server_config *out);
+
+/* Admit one request: `words` (HOST memory, n_words, copied before return) is a
+ * packed word stream as for svt_unpack.  Blocks until a slot is free; returns
+ * the request's id in *request_id.  SVT_E_CAPACITY if n_words exceeds
+ * max_words (the request is not admitted).  Errors of the request itself
+ * (format, limits, capacity, CUDA) are its result's status.  Thread-safe. */
+int svt_server_submit(svt_server *srv, const uint32_t *words, size_t n_words, uint64_t *request_id);
+
+/* Next completed request, in completion order: waits up to timeout_us
+ * microseconds (< 0: no limit); SVT_E_TIMEOUT if none completed. */
+int svt_server_wait(svt_server *srv, int64_t timeout_us, svt_server_result *out);
+
+/* Copy the tracks of a completed request (in (event, road, comb) order) to
+ * HOST memory `out` (cap records) and release them.  *n_out = number of
+ * tracks; SVT_E_CAPACITY (nothing released) if cap is smaller;
+ * SVT_E_STATE if the id is unknown or already taken. */
+int svt_server_take(svt_server *srv, uint64_t request_id, svt_track *out, size_t cap, size_t *n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,19 @@ class Stats(C.Structure):
         return d
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("n_slots", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("max_ctas", C.c_uint32),
+                ("mode", C.c_int32), ("max_words", C.c_uint64), ("max_events", C.c_uint32),
+                ("max_roads", C.c_uint32), ("max_tracks", C.c_uint64), ("hash_slots", C.c_uint32),
+                ("pad", C.c_uint32), ("max_combinations", C.c_uint64)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("status", C.c_int32), ("pad", C.c_uint32),
+                ("n_tracks", C.c_uint64), ("n_events", C.c_uint64), ("n_combinations", C.c_uint64),
+                ("latency_ns", C.c_uint64)]
+
+
 # every entry point of include/svt.h with its argument types
 SIGNATURES = {
     "svt_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Limits)]),
@@ -70,6 +83,13 @@ SIGNATURES = {
     "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
     "svt_last_launch_count": (C.c_int, [C.c_void_p]),
     "svt_strerror": (C.c_char_p, [C.c_int]),
+    "svt_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(ServerConfig), C.c_void_p,
+                                    C.c_uint32, C.c_int64]),
+    "svt_server_destroy": (None, [C.c_void_p]),
+    "svt_server_get_config": (C.c_int, [C.c_void_p, C.POINTER(ServerConfig)]),
+    "svt_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_uint64)]),
+    "svt_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(ServerResult)]),
+    "svt_server_take": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
 }
 
 _lib = None
@@ -206,3 +226,53 @@ class Context:
 
     def last_launch_count(self) -> int:
         return lib().svt_last_launch_count(self._h)
+
+
+class Server:
+    """A serving runtime (svt_server): continuous batching of independent
+    requests over device slots.  Words and results are host numpy arrays."""
+
+    def __init__(self, consts: dict, cut: int, device: int = 0, mode: int = PERSISTENT, **config):
+        self._h = C.c_void_p()
+        cfg = ServerConfig(mode=mode, **config)
+        sets = pack_constants(consts)
+        check(lib().svt_server_create(C.byref(self._h), device, C.byref(cfg), sets.ctypes.data,
+                                      len(sets), int(cut)), "svt_server_create")
+
+    def config(self) -> dict:
+        cfg = ServerConfig()
+        check(lib().svt_server_get_config(self._h, C.byref(cfg)), "svt_server_get_config")
+        return {f: getattr(cfg, f) for f, _ in cfg._fields_ if f != "pad"}
+
+    def submit(self, words) -> int:
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        rid = C.c_uint64()
+        check(lib().svt_server_submit(self._h, w.ctypes.data, len(w), C.byref(rid)), "svt_server_submit")
+        return rid.value
+
+    def wait(self, timeout_us: int = -1):
+        """Next completed request as a dict, or None on timeout."""
+        r = ServerResult()
+        st = lib().svt_server_wait(self._h, int(timeout_us), C.byref(r))
+        if st == E_TIMEOUT:
+            return None
+        check(st, "svt_server_wait")
+        return {f: getattr(r, f) for f, _ in r._fields_ if f != "pad"}
+
+    def take(self, request_id: int, n_tracks: int) -> np.ndarray:
+        out = np.zeros(n_tracks, dtype=TRACK_DTYPE)
+        n = C.c_size_t()
+        check(lib().svt_server_take(self._h, request_id, out.ctypes.data, n_tracks, C.byref(n)),
+              "svt_server_take")
+        return out[:n.value]
+
+    def close(self):
+        if self._h:
+            lib().svt_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,5 @@
 // svt_api.cu -- the C ABI (include/svt.h): context, buffers, status, launches.
-#include "svt_internal.h"
+#include "svt_ctx.h"
 
 #include <cstdlib>
 #include <cstring>
@@ -12,32 +12,6 @@ static_assert(sizeof(svt_track) == 40, "svt_track layout");
 static_assert(sizeof(svt_road) == 100, "svt_road layout");
 static_assert(sizeof(RoadRec) == 16, "RoadRec layout");
 
-struct svt_ctx {
-    int device = 0;
-    svt_limits lim{};
-    Dev d{};
-    Ctrl *h_ctrl = nullptr;          // pinned mirror of the control block
-    bool consts_loaded = false;
-    bool bound = false;              // a batch is bound by svt_unpack
-    bool roads_valid = false;        // the road table holds the bound batch
-    bool ran = false;                // svt_fit_events ran on the bound batch
-    int blocks_per_sm = 0;
-    int last_launches = 0;
-    unsigned long long wait_ns = 2000000000ull;
-    int skip_arrival = 0;
-    bool hash_dirty = false;         // a batch stopped before clearing its group table
-    // CUDA graph of one svt_fit_events enqueue
-    bool use_graph = false;
-    cudaGraphExec_t gexec = nullptr;
-    int g_mode = -1;
-    const uint32_t *g_words = nullptr;
-    unsigned long long g_n = 0;
-    cudaStream_t g_stream = nullptr;
-    int g_launches = 0;
-    unsigned long long g_key = 0;
-    void *allocs[40] = {};
-    int n_allocs = 0;
-};
 
 namespace {
 
@@ -139,10 +113,19 @@ cudaError_t enqueue(svt_ctx *c, int mode, cudaStream_t s, int *launches)
             return e;
         return launch_fit_plain(d, s, launches);
     }
-    return launch_persistent(d, s, c->blocks_per_sm, launches);
+    return launch_persistent(d, s, c->blocks_per_sm, c->max_ctas, launches);
 }
 
 }  // namespace
+
+namespace svt {
+cudaError_t ctx_enqueue(svt_ctx *c, int mode, cudaStream_t s, int *launches)
+{
+    return enqueue(c, mode, s, launches);
+}
+int ctx_status(const svt_ctx *c) { return status_of(*c->h_ctrl); }
+int ctx_prepare(svt_ctx *c, int mode) { return mode == SVT_PLAIN ? ensure_plain_buffers(c) : SVT_OK; }
+}  // namespace svt
 
 extern "C" {
 

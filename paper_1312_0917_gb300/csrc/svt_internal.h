@@ -104,7 +104,7 @@ struct Dev {
 // launchers (svt_kernels.cu)
 cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches);
 cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches);
-cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int *n_launches);
+cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas, int *n_launches);
 cudaError_t launch_export_roads(const Dev &d, cudaStream_t s);
 int persistent_max_blocks_per_sm(int device);
 size_t persistent_smem_bytes();

@@ -1917,7 +1917,7 @@ cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches)
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int *n_launches)
+cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas, int *n_launches)
 {
     cudaError_t e = set_smem_attrs();
     if (e)
@@ -1932,7 +1932,10 @@ cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, i
     Dev dd = d;
     void *args[] = {&dd};
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(sms * bps));
+    int grid = sms * bps;
+    if (max_ctas > 0 && max_ctas < grid)
+        grid = max_ctas;
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(BLOCK);
     cfg.dynamicSmemBytes = persistent_smem_bytes();
     cfg.stream = s;

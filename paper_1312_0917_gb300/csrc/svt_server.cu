@@ -1,0 +1,394 @@
+// svt_server.cu -- serving runtime: continuous batching of independent event
+// batches (requests) over a fixed set of device slots.
+//
+// Each slot owns a context (device buffers sized for one request), a CUDA
+// stream and pinned host staging for the request's words and tracks.  A
+// request is admitted when a slot is free; its host->device copy, persistent
+// kernel and control-block read are enqueued on the slot's stream at once,
+// so requests admitted while others run overlap on the device (each kernel
+// takes a share of the SMs).  A progress thread watches the slots' events,
+// fetches each result's tracks once their count is known and releases the
+// slot.  Latency runs from svt_server_submit to the moment the tracks are in
+// host memory.
+#include "svt_ctx.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+using namespace svt;
+
+static_assert(sizeof(svt_server_config) == 56, "svt_server_config layout");
+static_assert(sizeof(svt_server_result) == 48, "svt_server_result layout");
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum SlotState { SLOT_FREE = 0, SLOT_RESERVED, SLOT_RUNNING, SLOT_FETCHING };
+
+struct Slot {
+    svt_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    uint32_t *h_words = nullptr;     // pinned staging of the request's words
+    uint32_t *d_words = nullptr;     // device copy of the words
+    svt_track *h_tracks = nullptr;   // pinned staging of the result
+    cudaEvent_t ev_ctrl = nullptr;   // control block in host memory
+    cudaEvent_t ev_done = nullptr;   // tracks in host memory
+    int state = SLOT_FREE;
+    uint64_t id = 0;
+    size_t n_tracks = 0;
+    int status = SVT_OK;
+    Clock::time_point t_submit;
+};
+
+struct Result {
+    svt_server_result info;
+    std::vector<svt_track> tracks;
+};
+
+}  // namespace
+
+struct svt_server {
+    int device = 0;
+    svt_server_config cfg{};
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_slot;   // a slot became free
+    std::condition_variable cv_done;   // a result is ready
+    std::deque<uint64_t> done_order;   // completed, not yet reported by svt_server_wait
+    std::list<Result> results;         // completed, not yet taken
+    std::thread progress;
+    std::atomic<bool> stop{false};
+    uint64_t next_id = 1;
+    unsigned in_flight = 0;
+};
+
+namespace {
+
+void finish(svt_server *s, Slot &sl, int status, size_t n_tracks)
+{
+    Result r;
+    r.info.request_id = sl.id;
+    r.info.status = status;
+    r.info.pad = 0;
+    r.info.n_tracks = status == SVT_OK ? n_tracks : 0;
+    const Ctrl &h = *sl.ctx->h_ctrl;
+    r.info.n_events = h.n_events;
+    r.info.n_combinations = h.n_comb;
+    r.info.latency_ns =
+        (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - sl.t_submit).count();
+    if (status == SVT_OK && n_tracks)
+        r.tracks.assign(sl.h_tracks, sl.h_tracks + n_tracks);
+    if (h.flags & FLAG_TIMEOUT)
+        sl.ctx->hash_dirty = true;   // the batch may have stopped before clearing its table
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->results.push_back(std::move(r));
+    s->done_order.push_back(sl.id);
+    sl.state = SLOT_FREE;
+    --s->in_flight;
+    s->cv_slot.notify_all();
+    s->cv_done.notify_all();
+}
+
+// One pass over the slots; returns true if any slot advanced.
+bool progress_once(svt_server *s)
+{
+    bool moved = false;
+    for (Slot &sl : s->slots) {
+        int state;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            state = sl.state;
+        }
+        if (state == SLOT_RUNNING) {
+            const cudaError_t q = cudaEventQuery(sl.ev_ctrl);
+            if (q == cudaErrorNotReady)
+                continue;
+            moved = true;
+            if (q != cudaSuccess) {
+                finish(s, sl, SVT_E_CUDA, 0);
+                continue;
+            }
+            int st = ctx_status(sl.ctx);
+            const size_t n = (size_t)sl.ctx->h_ctrl->n_out;
+            if (st == SVT_OK && n > s->cfg.max_tracks)
+                st = SVT_E_CAPACITY;
+            if (st != SVT_OK || n == 0) {
+                finish(s, sl, st, 0);
+                continue;
+            }
+            sl.n_tracks = n;
+            if (cudaMemcpyAsync(sl.h_tracks, sl.ctx->d.tracks, n * sizeof(svt_track), cudaMemcpyDeviceToHost,
+                                sl.stream) != cudaSuccess ||
+                cudaEventRecord(sl.ev_done, sl.stream) != cudaSuccess) {
+                finish(s, sl, SVT_E_CUDA, 0);
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(s->mu);
+            sl.state = SLOT_FETCHING;
+        } else if (state == SLOT_FETCHING) {
+            const cudaError_t q = cudaEventQuery(sl.ev_done);
+            if (q == cudaErrorNotReady)
+                continue;
+            moved = true;
+            finish(s, sl, q == cudaSuccess ? SVT_OK : SVT_E_CUDA, sl.n_tracks);
+        }
+    }
+    return moved;
+}
+
+void progress_loop(svt_server *s)
+{
+    cudaSetDevice(s->device);
+    while (!s->stop.load(std::memory_order_acquire)) {
+        if (!progress_once(s)) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->in_flight == 0)
+                s->cv_slot.wait_for(lk, std::chrono::milliseconds(1));
+            else {
+                lk.unlock();
+                std::this_thread::yield();
+            }
+        }
+    }
+}
+
+void destroy_slots(svt_server *s)
+{
+    for (Slot &sl : s->slots) {
+        if (sl.stream)
+            cudaStreamSynchronize(sl.stream);
+        if (sl.ev_ctrl)
+            cudaEventDestroy(sl.ev_ctrl);
+        if (sl.ev_done)
+            cudaEventDestroy(sl.ev_done);
+        if (sl.h_words)
+            cudaFreeHost(sl.h_words);
+        if (sl.h_tracks)
+            cudaFreeHost(sl.h_tracks);
+        if (sl.d_words)
+            cudaFree(sl.d_words);
+        if (sl.stream)
+            cudaStreamDestroy(sl.stream);
+        if (sl.ctx)
+            svt_destroy(sl.ctx);
+        sl = Slot{};
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int svt_server_create(svt_server **out, int device, const svt_server_config *config,
+                      const svt_const_set *sets, uint32_t n_sets, int64_t chi2_cut)
+{
+    if (!out)
+        return SVT_E_INVAL;
+    *out = nullptr;
+    svt_server_config cfg = config ? *config : svt_server_config{};
+    if (!cfg.ctas_per_sm) cfg.ctas_per_sm = 1;
+    if (!cfg.max_words) cfg.max_words = 1ull << 21;
+    if (!cfg.max_events) cfg.max_events = 4096;
+    if (!cfg.max_roads) cfg.max_roads = 1u << 17;
+    if (!cfg.max_tracks) cfg.max_tracks = 1ull << 20;
+    if (!cfg.hash_slots) cfg.hash_slots = 1u << 20;
+    if ((cfg.mode != SVT_PERSISTENT && cfg.mode != SVT_PLAIN) || cfg.n_slots > 64 ||
+        cfg.max_words >= (1ull << 32) || cfg.max_tracks >= (1ull << 32) ||
+        (cfg.hash_slots & (cfg.hash_slots - 1)))
+        return SVT_E_INVAL;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return SVT_E_CUDA;
+    svt_server *s = new (std::nothrow) svt_server();
+    if (!s)
+        return SVT_E_INVAL;
+    s->device = device;
+
+    svt_limits lim{};
+    lim.max_words = cfg.max_words;
+    lim.max_events = cfg.max_events;
+    lim.max_roads = cfg.max_roads;
+    lim.max_tracks = cfg.max_tracks;
+    lim.hash_slots = cfg.hash_slots;
+    lim.max_combinations = cfg.mode == SVT_PLAIN ? (cfg.max_combinations ? cfg.max_combinations : 1ull << 24) : 1;
+    cfg.max_combinations = lim.max_combinations;
+
+    // admission by device memory: without an explicit slot count, take as
+    // many slots as a quarter of the free memory holds (at least one)
+    unsigned n_slots = cfg.n_slots;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete s;
+        return SVT_E_CUDA;
+    }
+    int st = SVT_OK;
+    s->slots.resize(n_slots ? n_slots : 1);
+    for (size_t i = 0; i < s->slots.size() && st == SVT_OK; ++i) {
+        Slot &sl = s->slots[i];
+        size_t before = 0, after = 0, tot = 0;
+        cudaMemGetInfo(&before, &tot);
+        if ((st = svt_create(&sl.ctx, device, &lim)) != SVT_OK)
+            break;
+        if ((st = svt_load_constants(sl.ctx, sets, n_sets, chi2_cut, nullptr)) != SVT_OK)
+            break;
+        if ((st = ctx_prepare(sl.ctx, cfg.mode)) != SVT_OK)
+            break;
+        sl.ctx->blocks_per_sm = (int)cfg.ctas_per_sm;
+        sl.ctx->max_ctas = (int)cfg.max_ctas;
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&sl.h_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
+            cudaMallocHost(&sl.h_tracks, sizeof(svt_track) * cfg.max_tracks) != cudaSuccess ||
+            cudaMalloc(&sl.d_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev_ctrl, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming) != cudaSuccess) {
+            st = SVT_E_CUDA;
+            break;
+        }
+        cudaMemGetInfo(&after, &tot);
+        if (!n_slots && i == 0) {   // size the slot count from the first slot's footprint
+            const size_t per = before > after ? before - after : 1;
+            const size_t want = std::max<size_t>(1, std::min<size_t>(8, free_b / 4 / per));
+            s->slots.resize(want);
+        }
+    }
+    if (st != SVT_OK) {
+        destroy_slots(s);
+        delete s;
+        return st;
+    }
+    cfg.n_slots = (uint32_t)s->slots.size();
+    s->cfg = cfg;
+    s->progress = std::thread(progress_loop, s);
+    *out = s;
+    return SVT_OK;
+}
+
+void svt_server_destroy(svt_server *s)
+{
+    if (!s)
+        return;
+    cudaSetDevice(s->device);
+    {
+        // wait for the requests in flight
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_slot.wait_for(lk, std::chrono::seconds(10), [s] { return s->in_flight == 0; });
+    }
+    s->stop.store(true, std::memory_order_release);
+    s->cv_slot.notify_all();
+    if (s->progress.joinable())
+        s->progress.join();
+    destroy_slots(s);
+    delete s;
+}
+
+int svt_server_get_config(svt_server *s, svt_server_config *out)
+{
+    if (!s || !out)
+        return SVT_E_INVAL;
+    *out = s->cfg;
+    return SVT_OK;
+}
+
+int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t *request_id)
+{
+    if (!s || !request_id || (n_words && !words))
+        return SVT_E_INVAL;
+    *request_id = 0;
+    if (n_words > s->cfg.max_words)
+        return SVT_E_CAPACITY;
+    const Clock::time_point t0 = Clock::now();
+    Slot *sl = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_slot.wait(lk, [s, &sl] {
+            for (Slot &x : s->slots)
+                if (x.state == SLOT_FREE) {
+                    sl = &x;
+                    return true;
+                }
+            return false;
+        });
+        sl->state = SLOT_RESERVED;
+        sl->id = s->next_id++;
+        sl->t_submit = t0;
+        ++s->in_flight;
+    }
+    s->cv_slot.notify_all();   // wakes an idle progress thread
+    *request_id = sl->id;
+    if (n_words)
+        std::memcpy(sl->h_words, words, n_words * sizeof(uint32_t));
+    int launches = 0;
+    bool ok = cudaSetDevice(s->device) == cudaSuccess &&
+              (!n_words || cudaMemcpyAsync(sl->d_words, sl->h_words, n_words * sizeof(uint32_t),
+                                           cudaMemcpyHostToDevice, sl->stream) == cudaSuccess) &&
+              svt_unpack(sl->ctx, sl->d_words, n_words, sl->stream) == SVT_OK &&
+              ctx_enqueue(sl->ctx, s->cfg.mode, sl->stream, &launches) == cudaSuccess &&
+              cudaMemcpyAsync(sl->ctx->h_ctrl, sl->ctx->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                              sl->stream) == cudaSuccess &&
+              cudaEventRecord(sl->ev_ctrl, sl->stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        std::memset(sl->ctx->h_ctrl, 0, sizeof(Ctrl));
+        finish(s, *sl, SVT_E_CUDA, 0);
+        return SVT_OK;   // the failure is the request's status
+    }
+    sl->ctx->ran = true;
+    sl->ctx->last_launches = launches;
+    std::lock_guard<std::mutex> lk(s->mu);
+    sl->state = SLOT_RUNNING;
+    return SVT_OK;
+}
+
+int svt_server_wait(svt_server *s, int64_t timeout_us, svt_server_result *out)
+{
+    if (!s || !out)
+        return SVT_E_INVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [s] { return !s->done_order.empty(); };
+    if (timeout_us < 0)
+        s->cv_done.wait(lk, ready);
+    else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+        return SVT_E_TIMEOUT;
+    const uint64_t id = s->done_order.front();
+    s->done_order.pop_front();
+    for (const Result &r : s->results)
+        if (r.info.request_id == id) {
+            *out = r.info;
+            return SVT_OK;
+        }
+    return SVT_E_STATE;
+}
+
+int svt_server_take(svt_server *s, uint64_t request_id, svt_track *out, size_t cap, size_t *n_out)
+{
+    if (!s || !n_out)
+        return SVT_E_INVAL;
+    *n_out = 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->results.begin(); it != s->results.end(); ++it) {
+        if (it->info.request_id != request_id)
+            continue;
+        const size_t n = it->tracks.size();
+        *n_out = n;
+        if (n > cap)
+            return SVT_E_CAPACITY;
+        if (n && !out)
+            return SVT_E_INVAL;
+        if (n)
+            std::memcpy(out, it->tracks.data(), n * sizeof(svt_track));
+        s->results.erase(it);
+        return SVT_OK;
+    }
+    return SVT_E_STATE;
+}
+
+}  // extern "C"

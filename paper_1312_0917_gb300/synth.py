@@ -34,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "Config", "CONFIGS", "Batch", "make_constants", "make_batch",
-    "encode_roads", "N_SETS", "N_LAYERS", "MAX_HITS", "MAX_ROADS",
+    "encode_roads", "request_sizes", "N_SETS", "N_LAYERS", "MAX_HITS", "MAX_ROADS",
 ]
 
 N_LAYERS = 5          # silicon layers per road
@@ -287,6 +287,21 @@ def make_batch(cfg: Config | str, seed: int = 0, n_events: int | None = None) ->
     roads["coords"] = np.where(valid, coords, 0)
     n_fits = int(np.prod(nh, axis=1).sum())
     return Batch(cfg, seed, words, event_offsets, roads, n_fits)
+
+
+_S_REQ = 30
+
+
+def request_sizes(seed: int, n_requests: int, max_events: int = 512) -> np.ndarray:
+    """Event counts of serving requests, spread evenly over octaves: octave k
+    uniform in 0..log2(max_events) - 1, then a count uniform in [2^k, 2^(k+1))
+    (a log-uniform law on [1, max_events) in integer arithmetic)."""
+    n_oct = max(1, int(max_events).bit_length() - 1)
+    i = np.arange(n_requests)
+    k = uniform_int(seed, _S_REQ, 2 * i, 0, n_oct - 1)
+    lo = np.left_shift(1, k)
+    off = (draws(seed, _S_REQ, 2 * i + 1) >> np.uint64(32)).astype(np.int64)
+    return (lo + (off * lo) // (1 << 32)).astype(np.int64)
 
 
 def encode_roads(events) -> np.ndarray:

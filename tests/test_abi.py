@@ -42,6 +42,8 @@ def test_strerror_and_null_checks(lib):
     n = C.c_size_t()
     assert lib.svt_get_tracks(None, None, 0, C.byref(n), None) == B.E_INVAL
     assert lib.svt_last_launch_count(None) == 0
+    assert lib.svt_server_create(None, 0, None, None, 0, 0) == B.E_INVAL
+    assert lib.svt_server_submit(None, None, 0, None) == B.E_INVAL
 
 
 def test_struct_layouts():
@@ -50,6 +52,7 @@ def test_struct_layouts():
     assert B.TRACK_DTYPE.itemsize == 40 and B.TRACK_DTYPE.fields["chi2"][1] == 24
     assert B.ROAD_DTYPE.itemsize == 100 and B.ROAD_DTYPE.fields["coord"][1] == 20
     assert C.sizeof(B.Limits) == 40 and C.sizeof(B.Stats) == 104
+    assert C.sizeof(B.ServerConfig) == 56 and C.sizeof(B.ServerResult) == 48
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):

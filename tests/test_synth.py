@@ -53,3 +53,14 @@ def test_words_well_formed():
     assert (ep[ee == 1] == 1).all() and ee[-1] == 1
     # event offsets are the positions after each EE word
     assert np.array_equal(np.nonzero(ee)[0] + 1, b.event_offsets[1:])
+
+
+def test_request_sizes_cover_the_octaves():
+    """Serving request sizes: in [1, 512), deterministic, every octave used
+    about equally (log-uniform law)."""
+    r = synth.request_sizes(0, 9000)
+    assert r.min() >= 1 and r.max() < 512
+    assert np.array_equal(r, synth.request_sizes(0, 9000))
+    octave = np.floor(np.log2(r)).astype(int)
+    counts = np.bincount(octave, minlength=9)
+    assert len(counts) == 9 and counts.min() > 850 and counts.max() < 1150
