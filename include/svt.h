@@ -180,6 +180,25 @@ int svt_get_stats(svt_ctx *ctx, svt_stats *out, void *stream);
  * effect from the next svt_fit_events. */
 int svt_set_launch(svt_ctx *ctx, int blocks_per_sm, int small_n4);
 
+/* One configuration measured by svt_autotune. */
+typedef struct {
+    int32_t blocks_per_sm;
+    int32_t small_n4;
+    float ms;                  /* median device time of one SVT_PERSISTENT batch */
+} svt_tune_point;
+
+/* Autotuner of the persistent kernel: for every resident-CTA count per SM
+ * (1 .. occupancy maximum) and every split between warp and CTA roads
+ * (small_n4 = 64, 128, 256), run the bound batch once to warm up and `reps`
+ * times timed with CUDA events on `stream`, then keep the configuration with
+ * the smallest median time (as svt_set_launch would).  The tracks do not
+ * depend on these settings.  Writes up to `cap` measured points to `points`
+ * (HOST memory) and their number to *n_points.  Requires constants and a
+ * bound batch; synchronises `stream`; SVT_E_CAPACITY if cap > 0 is too small
+ * (the best configuration is still applied). */
+int svt_autotune(svt_ctx *ctx, int reps, svt_tune_point *points, uint32_t cap, uint32_t *n_points,
+                 void *stream);
+
 /* Capture the enqueue of svt_fit_events(ctx, mode) for the bound batch into a
  * CUDA graph and use it for later svt_fit_events calls with the same batch
  * binding (enable = 1); enable = 0 returns to direct launches. */

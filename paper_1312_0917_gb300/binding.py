@@ -53,6 +53,10 @@ class Stats(C.Structure):
         return d
 
 
+class TunePoint(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int32), ("small_n4", C.c_int32), ("ms", C.c_float)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("n_slots", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("max_ctas", C.c_uint32),
                 ("mode", C.c_int32), ("max_words", C.c_uint64), ("max_events", C.c_uint32),
@@ -83,6 +87,8 @@ SIGNATURES = {
     "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
     "svt_last_launch_count": (C.c_int, [C.c_void_p]),
     "svt_strerror": (C.c_char_p, [C.c_int]),
+    "svt_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32),
+                                C.c_void_p]),
     "svt_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(ServerConfig), C.c_void_p,
                                     C.c_uint32, C.c_int64]),
     "svt_server_destroy": (None, [C.c_void_p]),
@@ -217,6 +223,14 @@ class Context:
 
     def set_launch(self, blocks_per_sm: int = 0, small_n4: int = 0):
         check(lib().svt_set_launch(self._h, blocks_per_sm, small_n4), "svt_set_launch")
+
+    def autotune(self, reps: int = 5, stream=None) -> list:
+        """Measure every launch configuration on the bound batch and keep the
+        fastest; returns [(blocks_per_sm, small_n4, ms), ...]."""
+        pts = (TunePoint * 64)()
+        n = C.c_uint32()
+        check(lib().svt_autotune(self._h, reps, pts, 64, C.byref(n), stream_ptr(stream)), "svt_autotune")
+        return [(p.blocks_per_sm, p.small_n4, p.ms) for p in pts[:n.value]]
 
     def use_graph(self, enable: bool = True):
         check(lib().svt_use_graph(self._h, int(enable)), "svt_use_graph")

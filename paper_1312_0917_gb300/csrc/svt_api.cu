@@ -1,7 +1,9 @@
 // svt_api.cu -- the C ABI (include/svt.h): context, buffers, status, launches.
 #include "svt_ctx.h"
 
+#include <algorithm>
 #include <cstdlib>
+#include <vector>
 #include <cstring>
 #include <new>
 
@@ -403,6 +405,70 @@ int svt_set_launch(svt_ctx *c, int blocks_per_sm, int small_n4)
     c->d.small_n4 = small_n4 ? small_n4 : N4_SMALL_MAX;
     drop_graph(c);
     return SVT_OK;
+}
+
+int svt_autotune(svt_ctx *c, int reps, svt_tune_point *points, uint32_t cap, uint32_t *n_points,
+                 void *stream)
+{
+    if (!c || reps < 1 || (cap && !points))
+        return SVT_E_INVAL;
+    if (n_points)
+        *n_points = 0;
+    if (!c->consts_loaded || !c->bound)
+        return SVT_E_STATE;
+    if (cudaSetDevice(c->device))
+        return SVT_E_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int maxb = persistent_max_blocks_per_sm(c->device);
+    if (maxb <= 0)
+        return SVT_E_CUDA;
+    static const int kSmall[] = {64, 128, N4_SMALL_MAX};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1))
+        return SVT_E_CUDA;
+    const int old_bps = c->blocks_per_sm, old_small = c->d.small_n4;
+    int best_bps = old_bps, best_small = old_small, st = SVT_OK;
+    float best = 0.f;
+    uint32_t n = 0;
+    std::vector<float> t(reps);
+    for (int bps = 1; bps <= maxb && st == SVT_OK; ++bps)
+        for (int small : kSmall) {
+            c->blocks_per_sm = bps;
+            c->d.small_n4 = small;
+            int nl = 0;
+            if (enqueue(c, SVT_PERSISTENT, s, &nl) || read_ctrl(c, s)) {   // warm-up
+                st = SVT_E_CUDA;
+                break;
+            }
+            if ((st = status_of(*c->h_ctrl)) != SVT_OK)
+                break;
+            for (int r = 0; r < reps && st == SVT_OK; ++r) {
+                if (cudaEventRecord(e0, s) || enqueue(c, SVT_PERSISTENT, s, &nl) || cudaEventRecord(e1, s) ||
+                    cudaEventSynchronize(e1) || cudaEventElapsedTime(&t[r], e0, e1))
+                    st = SVT_E_CUDA;
+            }
+            if (st != SVT_OK)
+                break;
+            std::sort(t.begin(), t.end());
+            const float med = t[reps / 2];
+            if (n < cap)
+                points[n] = svt_tune_point{bps, small, med};
+            ++n;
+            if (best == 0.f || med < best) {
+                best = med;
+                best_bps = bps;
+                best_small = small;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    c->blocks_per_sm = st == SVT_OK ? best_bps : old_bps;
+    c->d.small_n4 = st == SVT_OK ? best_small : old_small;
+    drop_graph(c);
+    if (n_points)
+        *n_points = n;
+    return st != SVT_OK ? st : n > cap && cap ? SVT_E_CAPACITY : SVT_OK;
 }
 
 int svt_use_graph(svt_ctx *c, int enable)

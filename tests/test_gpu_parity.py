@@ -288,3 +288,18 @@ def test_constant_bounds_rejected():
         c.load_constants(z, 1)
     assert e.value.code == B.E_INVAL
     c.close()
+
+
+def test_autotune_keeps_the_fastest_and_the_tracks(ctx, orc, consts, cuts):
+    b = synth.make_batch("uneven", seed=3, n_events=300)
+    ctx.load_constants(consts, cuts["uneven"])
+    d = torch_words(b.words)
+    assert ctx.unpack(d, len(b.words)) == B.OK
+    pts = ctx.autotune(reps=3)
+    assert len(pts) >= 3 and len(pts) % 3 == 0
+    assert {p[1] for p in pts} == {64, 128, 256}
+    assert all(p[2] > 0 for p in pts)
+    st, got, _ = run_gpu(ctx, b.words, B.PERSISTENT, d_words=d)
+    assert st == B.OK
+    assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["uneven"]))
+    ctx.set_launch(0, 0)
