@@ -215,6 +215,29 @@ int svt_last_launch_count(svt_ctx *ctx);
 
 const char *svt_strerror(int code);
 
+/* ---- the chain without allocation ----------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when a batch arrives (a process whose free
+ * device memory is owned by another allocator or fixed at start-up, a
+ * trigger path where an allocation's latency or failure is not acceptable).
+ *
+ * svt_run_static runs SVT_PERSISTENT on one batch over a scratch arena that
+ * is a fixed-size __device__ array of the library (under 8 MB per device),
+ * not a context: it allocates nothing.  Limits: 131072 words, 1024 events,
+ * 8192 roads (SVT_E_CAPACITY beyond; n_words is checked before any work).
+ * d_words: the batch on the device (4-byte aligned); sets: the 360 constant
+ * sets in HOST memory (same admission rule as svt_load_constants); d_tracks:
+ * caller-owned DEVICE buffer of `cap` records (8-byte aligned) that receives
+ * the tracks in (event, road, comb) order; *n_out (HOST) = number of tracks
+ * (with SVT_E_CAPACITY, the number that did not fit `cap`).  Synchronises
+ * `stream`.  The first call on a device does its setup (looks up the arena,
+ * clears its group table, sets the kernel's shared-memory limit), so it must
+ * come before any stream capture; there is one arena per device, so calls
+ * that overlap in time (threads or streams with work in flight) race on it. */
+int svt_run_static(const uint32_t *d_words, size_t n_words, const svt_const_set *sets,
+                   uint32_t n_sets, int64_t chi2_cut, svt_track *d_tracks, size_t cap,
+                   size_t *n_out, void *stream);
+
 /* ---- serving: continuous batching of independent requests -------------- *
  * Not a step of the paper's chain: it serves the chain to a stream of
  * independent requests (batches of events), the low-latency trigger setting

@@ -89,6 +89,8 @@ SIGNATURES = {
     "svt_strerror": (C.c_char_p, [C.c_int]),
     "svt_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32),
                                 C.c_void_p]),
+    "svt_run_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint32, C.c_int64, C.c_void_p,
+                                  C.c_size_t, C.POINTER(C.c_size_t), C.c_void_p]),
     "svt_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(ServerConfig), C.c_void_p,
                                     C.c_uint32, C.c_int64]),
     "svt_server_destroy": (None, [C.c_void_p]),

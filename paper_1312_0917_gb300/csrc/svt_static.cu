@@ -1,0 +1,188 @@
+// svt_static.cu -- svt_run_static: the whole chain on one batch with no
+// allocation at call time.
+//
+// Some callers cannot allocate device memory when a batch arrives: a process
+// whose free device memory is already owned by another allocator (a caching
+// allocator that holds the pool, or a budget fixed at start-up), and trigger
+// paths where an allocation's latency or failure is not acceptable.  For them
+// this entry point runs the persistent kernel over a scratch arena that is a
+// file-scope __device__ array of fixed size (ARENA_BYTES), placed by the
+// module loader, and writes the tracks into the caller's buffer.
+//
+// The first call on a device looks up the arena's address with
+// cudaGetSymbolAddress and clears its group table; later calls reuse both.
+// There is one arena per device: calls that overlap in time (two host threads,
+// or two streams with work in flight) race on it.
+#include "svt_ctx.h"
+
+#include <cstdlib>
+#include <mutex>
+
+using namespace svt;
+
+namespace {
+
+// limits of one batch in the arena
+constexpr unsigned long long S_WORDS = 1ull << 17;
+constexpr unsigned S_EVENTS = 1u << 10;
+constexpr unsigned S_ROADS = 1u << 13;
+constexpr unsigned S_HASH = 1u << 15;
+constexpr unsigned S_CHUNKS_W = (unsigned)((S_WORDS + CHUNK_WORDS - 1) / CHUNK_WORDS);
+constexpr unsigned S_CHUNKS_R = (S_ROADS + ROAD_CHUNK - 1) / ROAD_CHUNK;
+
+constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// byte offsets of the arena's regions
+constexpr size_t OFF_CTRL = 0;
+constexpr size_t OFF_CONSTS = OFF_CTRL + up256(sizeof(Ctrl));
+constexpr size_t OFF_CHUNK = OFF_CONSTS + up256(sizeof(svt_const_set) * N_SETS);   // 4 x [S_CHUNKS_W] u32
+constexpr size_t OFF_EV = OFF_CHUNK + up256(4 * sizeof(uint32_t) * S_CHUNKS_W);     // 2 x [S_EVENTS] u32
+constexpr size_t OFF_ROADS = OFF_EV + up256(2 * sizeof(uint32_t) * S_EVENTS);
+constexpr size_t OFF_COORDS = OFF_ROADS + up256(sizeof(RoadRec) * S_ROADS);
+constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS);
+constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
+constexpr size_t OFF_SURV = OFF_BIG + up256(sizeof(uint32_t) * S_ROADS);
+constexpr size_t OFF_SCNT = OFF_SURV + up256(sizeof(unsigned long long) * SURV_SLOTS * S_ROADS);
+constexpr size_t OFF_RCH = OFF_SCNT + up256(S_ROADS);                                 // 2 x [S_CHUNKS_R] u32
+constexpr size_t OFF_CCH = OFF_RCH + up256(2 * sizeof(uint32_t) * S_CHUNKS_R);       // 2 x [S_CHUNKS_R] u64
+constexpr size_t OFF_HASH = OFF_CCH + up256(2 * sizeof(unsigned long long) * S_CHUNKS_R);
+constexpr size_t OFF_HUSED = OFF_HASH + up256(sizeof(HashSlot) * S_HASH);
+constexpr size_t ARENA_BYTES = OFF_HUSED + up256(sizeof(uint32_t) * S_HASH);
+static_assert(ARENA_BYTES < (8u << 20), "the static arena stays modest (under 8 MB)");
+
+}  // namespace
+
+// The arena.  The first call on a device clears its group table; the kernel
+// leaves the table empty after every batch that completes.
+static __device__ __align__(256) unsigned char g_arena[ARENA_BYTES];
+
+namespace {
+
+struct DeviceArena {
+    unsigned char *base = nullptr;
+    bool hash_dirty = true;   // clear the group table before the next batch
+};
+
+std::mutex g_mu;
+DeviceArena g_dev[64];
+
+// the same admission rule as svt_load_constants
+bool constants_admissible(const svt_const_set *sets)
+{
+    for (int s = 0; s < N_SETS; ++s) {
+        long long chi_bound = 0;
+        for (int k = 0; k < 3; ++k) {
+            long long bf = 4096ll * std::llabs((long long)sets[s].q[k]);
+            long long bc = 4096ll * std::llabs((long long)sets[s].k[k]);
+            for (int j = 0; j < 6; ++j) {
+                const long long mx = j < 4 ? 4095 : 32768;
+                bf += std::llabs((long long)sets[s].F[k][j]) * mx;
+                bc += std::llabs((long long)sets[s].C[k][j]) * mx;
+            }
+            if (bf >= (1ll << 31) || bc >= (1ll << 31))
+                return false;
+            const long long a = bc / 4096 + 1;
+            chi_bound += a * a;
+        }
+        if (chi_bound >= (1ll << 38))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt_const_set *sets,
+                              uint32_t n_sets, int64_t chi2_cut, svt_track *d_tracks, size_t cap,
+                              size_t *n_out, void *stream)
+{
+    if (n_out)
+        *n_out = 0;
+    if (!n_out || !sets || n_sets != (uint32_t)N_SETS || chi2_cut < 0 || (n_words && !d_words) ||
+        ((uintptr_t)d_words & 3u) || (cap && !d_tracks) || ((uintptr_t)d_tracks & 7u))
+        return SVT_E_INVAL;
+    if (n_words > S_WORDS)
+        return SVT_E_CAPACITY;
+    if (!constants_admissible(sets))
+        return SVT_E_INVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return SVT_E_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    DeviceArena *da = &g_dev[dev];
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!da->base) {   // first call on this device
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p)
+                return SVT_E_CUDA;
+            da->base = static_cast<unsigned char *>(p);
+        }
+    }
+    unsigned char *b = da->base;
+    Dev d{};
+    d.ctrl = reinterpret_cast<Ctrl *>(b + OFF_CTRL);
+    d.consts = reinterpret_cast<const svt_const_set *>(b + OFF_CONSTS);
+    d.words = d_words;
+    d.n_words = n_words;
+    d.n_chunks_w = (unsigned)((n_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
+    d.max_events = S_EVENTS;
+    d.max_roads = S_ROADS;
+    d.max_chunks_r = S_CHUNKS_R;
+    d.max_tracks = cap;
+    d.max_combs = 0;
+    uint32_t *chunk = reinterpret_cast<uint32_t *>(b + OFF_CHUNK);
+    d.chunk_ee = chunk;
+    d.chunk_ep = chunk + S_CHUNKS_W;
+    d.chunk_ee_off = chunk + 2 * S_CHUNKS_W;
+    d.chunk_ep_off = chunk + 3 * S_CHUNKS_W;
+    uint32_t *ev = reinterpret_cast<uint32_t *>(b + OFF_EV);
+    d.ev_word_end = ev;
+    d.ev_road_end = ev + S_EVENTS;
+    d.roads = reinterpret_cast<RoadRec *>(b + OFF_ROADS);
+    d.coords = reinterpret_cast<uint16_t *>(b + OFF_COORDS);
+    d.xmask = reinterpret_cast<unsigned long long *>(b + OFF_XMASK);
+    d.big_list = reinterpret_cast<uint32_t *>(b + OFF_BIG);
+    d.surv_pool = reinterpret_cast<unsigned long long *>(b + OFF_SURV);
+    d.surv_cnt = reinterpret_cast<uint8_t *>(b + OFF_SCNT);
+    uint32_t *rch = reinterpret_cast<uint32_t *>(b + OFF_RCH);
+    d.rchunk_sum = rch;
+    d.rchunk_off = rch + S_CHUNKS_R;
+    unsigned long long *cch = reinterpret_cast<unsigned long long *>(b + OFF_CCH);
+    d.cchunk_sum = cch;
+    d.cchunk_off = cch + S_CHUNKS_R;
+    d.hash = reinterpret_cast<HashSlot *>(b + OFF_HASH);
+    d.hash_used = reinterpret_cast<uint32_t *>(b + OFF_HUSED);
+    d.hash_mask = S_HASH - 1;
+    d.tracks = d_tracks;
+    d.cut = chi2_cut;
+    d.small_n4 = N4_SMALL_MAX;
+    d.wait_ns = 2000000000ull;
+
+    // what must start at zero: the control block every batch, the group
+    // table on the first batch and after one that did not finish
+    int launches = 0;
+    if (cudaMemcpyAsync(b + OFF_CONSTS, sets, sizeof(svt_const_set) * N_SETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s) ||
+        (da->hash_dirty && cudaMemsetAsync(d.hash, 0, sizeof(HashSlot) * S_HASH, s)) ||
+        launch_persistent(d, s, 0, 0, &launches))
+        return SVT_E_CUDA;
+    Ctrl h;
+    if (cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))
+        return SVT_E_CUDA;
+    da->hash_dirty = (h.flags & FLAG_TIMEOUT) != 0;
+    int st = SVT_OK;
+    if (h.flags & FLAG_TIMEOUT)
+        st = SVT_E_TIMEOUT;
+    else if (h.flags & FLAG_CAPACITY)
+        st = SVT_E_CAPACITY;
+    else if (h.err_inv) {
+        const unsigned rank = (unsigned)(~h.err_inv & 0xFFull);
+        st = rank == RANK_BAD ? SVT_E_BADWORD : rank == RANK_LIMIT ? SVT_E_LIMIT : SVT_E_TRUNCATED;
+    } else if (h.flags & FLAG_INTERNAL)
+        st = SVT_E_CUDA;
+    if (st == SVT_OK || st == SVT_E_CAPACITY)
+        *n_out = (size_t)h.n_out;
+    return st;
+}
