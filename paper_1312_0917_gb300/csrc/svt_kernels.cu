@@ -1073,6 +1073,7 @@ constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
 // One road of a run, in the warp's shared memory.
 struct FlatRoad {
     unsigned g, N4, E, kb, qb, ab, ne, key_hi, set;
+    unsigned event, excl, nl, Se, cand;   // nl: hits per layer, 4 bits each; Se: comb stride of excl
     int curv, phi;
     unsigned m[4], L[4], st[4], SL[4], aoff[4];
     unsigned off[6];
@@ -1127,6 +1128,76 @@ __device__ __forceinline__ FlatIndex flat_index(unsigned first, unsigned sub)
         rest &= rest - 1;
     }
     return x;
+}
+
+// Publish, for road ri of a flat sub-run (no repeated coordinate in a layer,
+// so every hit index is canonical), the minimum key of every group (layer
+// triple, three coordinates) whose three hits are flagged as shared with
+// another road of the event.  The whole warp takes the groups.
+__device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
+{
+    const FlatRoad &r = F.rd[ri];
+    const unsigned long long xm = ldcg(d.xmask + r.g);
+    unsigned fl[N_LAYERS], cnt[10], total = 0;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        const unsigned n = (r.nl >> (4 * l)) & 15u;
+        fl[l] = (unsigned)(xm >> (8 * l)) & ((1u << n) - 1u);
+    }
+    for (unsigned t = 0; t < 10; ++t) {
+        cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) * __popc(fl[c_triple[t][2]]);
+        total += cnt[t];
+    }
+    for (unsigned gi = lane_id(); gi < total; gi += 32) {
+        unsigned t = 0, rem = gi;
+        while (t < 9 && rem >= cnt[t]) {
+            rem -= cnt[t];
+            ++t;
+        }
+        const unsigned lt[3] = {c_triple[t][0], c_triple[t][1], c_triple[t][2]};
+        const unsigned p0 = __popc(fl[lt[0]]), p1 = __popc(fl[lt[1]]);
+        const unsigned dsel[3] = {nth_bit(fl[lt[0]], rem % p0), nth_bit(fl[lt[1]], (rem / p0) % p1),
+                                  nth_bit(fl[lt[2]], rem / (p0 * p1))};
+        unsigned long long mn = NO_KEY;
+        if (lt[0] != r.excl && lt[1] != r.excl && lt[2] != r.excl) {
+            // the free fitted slot runs over its hits, the three others are fixed
+            unsigned fb = 0, free_slot = 0 + 1 + 2 + 3;
+            for (unsigned q = 0; q < 3; ++q) {
+                const unsigned sq_ = lt[q] - (lt[q] > r.excl);
+                free_slot -= sq_;
+                fb += dsel[q] * r.st[sq_];
+            }
+            for (unsigned z = 0; z < r.m[free_slot]; ++z) {
+                const unsigned long long k = F.K[r.kb + fb + z * r.st[free_slot]];
+                mn = k < mn ? k : mn;
+            }
+        } else {
+            // the excluded layer in the triple: its lowest hit index of the
+            // coordinate (the index itself, canonical) and the pair table
+            unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
+            for (unsigned q = 0; q < 3; ++q) {
+                if (lt[q] == r.excl) {
+                    de = dsel[q];
+                } else if (fa == 4) {
+                    fa = lt[q] - (lt[q] > r.excl);
+                    da = dsel[q];
+                } else {
+                    fb = lt[q] - (lt[q] > r.excl);
+                    db = dsel[q];
+                }
+            }
+            unsigned p = 0;
+            while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
+                ++p;
+            mn = F.Q[r.qb + r.off[p] + da * r.m[fb] + db];
+            if (mn != NO_KEY)
+                mn += (unsigned long long)de * r.Se;
+        }
+        if (mn != NO_KEY)
+            hash_min(d, group_key(r.event, t, F.co[ri][lt[0] * 8 + dsel[0]], F.co[ri][lt[1] * 8 + dsel[1]],
+                                  F.co[ri][lt[2] * 8 + dsel[2]]),
+                     mn);
+    }
+    __syncwarp();
 }
 
 // Fit roads g0 .. g0 + R - 1 (R <= WARP_ROADS) with one warp.  `region` is
@@ -1186,6 +1257,11 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         for (unsigned s = 0; s < 3; ++s)
             fr.M[s] = c_magic[fr.m[s]];
         fr.g = g0 + lane;
+        fr.event = rec.event;
+        fr.excl = excl;
+        fr.nl = pk & 0xFFFFFu;
+        fr.Se = S5[excl];
+        fr.cand = (pk >> 23) & 1u;
         fr.N4 = N4;
         fr.E = E;
         fr.ne = n[excl];
@@ -1200,8 +1276,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             for (unsigned x = 1; x < n[l]; ++x)
                 for (unsigned y = 0; y < x; ++y)
                     dup = dup || F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y];
-        const bool cand = (pk >> 23) & 1u;
-        flat = !cand && !dup && N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
+        flat = !dup && N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
     }
 
     // flat sub-runs: a prefix of the remaining flat roads that fits the tables
@@ -1356,6 +1431,10 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         }
         if ((sub >> lane) & 1u)
             d.surv_cnt[g0 + lane] = (uint8_t)min(F.cnt[lane], (unsigned)SURV_SLOTS);
+        // cross-road candidates of the sub-run publish their group minima
+        for (unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && fr.cand); cands;
+             cands &= cands - 1)
+            flat_publish(d, F, __ffs(cands) - 1);
         todo &= ~sub;
         __syncwarp();
     }
@@ -1421,15 +1500,17 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
-        while (true) {
+        while (true) {   // two runs per queue step
             unsigned c = 0;
             if (lane_id() == 0)
-                c = atomicAdd(&d.ctrl->q[qsmall], 1u);
+                c = atomicAdd(&d.ctrl->q[qsmall], 2u);
             c = __shfl_sync(FULL_MASK, c, 0);
             if (c >= n_runs)
                 break;
-            const unsigned g0 = c * WARP_ROADS;
-            fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
+            for (unsigned r = c; r < min(c + 2u, n_runs); ++r) {
+                const unsigned g0 = r * WARP_ROADS;
+                fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
+            }
         }
     }
     npass = block_sum(npass);
