@@ -1500,17 +1500,15 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
-        while (true) {   // two runs per queue step
+        while (true) {
             unsigned c = 0;
             if (lane_id() == 0)
-                c = atomicAdd(&d.ctrl->q[qsmall], 2u);
+                c = atomicAdd(&d.ctrl->q[qsmall], 1u);
             c = __shfl_sync(FULL_MASK, c, 0);
             if (c >= n_runs)
                 break;
-            for (unsigned r = c; r < min(c + 2u, n_runs); ++r) {
-                const unsigned g0 = r * WARP_ROADS;
-                fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
-            }
+            const unsigned g0 = c * WARP_ROADS;
+            fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
         }
     }
     npass = block_sum(npass);
