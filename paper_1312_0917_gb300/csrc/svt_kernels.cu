@@ -364,67 +364,42 @@ struct P2Smem {
     uint32_t n_ep, n_seg;
 };
 
-// Decode road k of the event (words [start, end]) with one warp; `w_first`
-// is word start + lane (0 past the end), loaded by the caller.
+// Decode road k of the event (words [start, end]) with one thread.  The
+// event's words are in L1 from the boundary scan.  Hit d of layer l is the
+// d-th hit word of that layer in the road.
 __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long long start,
-                            unsigned long long end, uint32_t w_first, unsigned long long &err)
+                            unsigned long long end, unsigned long long &err)
 {
-    const unsigned lane = lane_id();
-    unsigned cnt[N_LAYERS] = {0, 0, 0, 0, 0};
+    unsigned n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;
     uint32_t hdr = 0, cw = 0, pw = 0;
-    for (unsigned c = lane; c < 40; c += 32)
-        s.coord[k][c] = 0;
-    __syncwarp();
-    for (unsigned long long q0 = 0; start + q0 <= end; q0 += 32) {
-        unsigned long long q = q0 + lane, pos = start + q;
-        bool valid = pos <= end;
-        uint32_t w = q0 == 0 ? w_first : valid ? __ldg(d.words + pos) : 0u;
-        unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
-        bool bad = valid && ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) ||
-                             (q >= 3 && type > 4) || (ep && q < 2));
-        if (bad)
+    for (unsigned long long pos = start; pos <= end; ++pos) {
+        const unsigned long long q = pos - start;
+        const uint32_t w = __ldg(d.words + pos);
+        const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
+        if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
+            (ep && q < 2))
             err = min(err, (pos << 8) | RANK_BAD);
-        bool hit = valid && q >= 3 && type <= 4;
-        unsigned rank = 0;
-#pragma unroll
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
-            unsigned m = __ballot_sync(FULL_MASK, hit && type == l);
-            if (hit && type == l)
-                rank = cnt[l] + __popc(m & lanemask_lt());
-            cnt[l] += __popc(m);
-        }
-        if (hit) {
+        if (q == 0) {
+            hdr = w;
+        } else if (q == 1) {
+            cw = w;
+        } else if (q == 2) {
+            pw = w;
+        } else if (type <= 4) {
+            const unsigned rank = type == 0 ? n0++ : type == 1 ? n1++ : type == 2 ? n2++ : type == 3 ? n3++ : n4++;
             if (rank >= MAX_HITS)
                 err = min(err, (pos << 8) | RANK_LIMIT);
             else
                 s.coord[k][type * 8 + rank] = (uint16_t)(w & 0xFFFu);
         }
-        if (q0 == 0) {
-            hdr = __shfl_sync(FULL_MASK, w, 0);
-            cw = __shfl_sync(FULL_MASK, w, 1);
-            pw = __shfl_sync(FULL_MASK, w, 2);
-        }
     }
-    if (lane == 0) {
-        unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
-        unsigned excl = min((hdr >> 7) & 7u, 4u);
-        uint32_t pk = 0;
-#pragma unroll
-        for (unsigned l = 0; l < N_LAYERS; ++l)
-            pk |= min(cnt[l], (unsigned)MAX_HITS) << (4 * l);
-        pk |= excl << 20;
-        pk |= (k & 255u) << 24;
-        s.pk[k] = pk;
-        s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
-        s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
-    }
-}
-
-// Word `start + lane` of a road (0 past its last word).
-__device__ __forceinline__ uint32_t first_word(const Dev &d, unsigned long long start, unsigned long long end)
-{
-    const unsigned long long pos = start + lane_id();
-    return pos <= end ? __ldg(d.words + pos) : 0u;
+    const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
+    const unsigned excl = min((hdr >> 7) & 7u, 4u);
+    const unsigned mh = MAX_HITS;
+    s.pk[k] = min(n0, mh) | (min(n1, mh) << 4) | (min(n2, mh) << 8) | (min(n3, mh) << 12) |
+              (min(n4, mh) << 16) | (excl << 20) | ((k & 255u) << 24);
+    s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
+    s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
 }
 
 // Unpack event e (CTA-wide); adds the event's combinations to n_comb.
@@ -471,30 +446,14 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
     unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
 
-    // decode: warp per road; the first words of the warp's next road are
-    // loaded while it decodes the current one
+    // decode: one thread per road; unused hit slots stay 0
+    for (unsigned i = threadIdx.x; i < nr * 40; i += BLOCK)
+        (&s.coord[0][0])[i] = 0;
+    __syncthreads();
     unsigned long long err = ~0ull;
-    {
-        unsigned k = warp_id();
-        unsigned long long start = 0, end = 0;
-        uint32_t w_next = 0;
-        if (k < nr) {
-            start = k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1;
-            end = k < running ? (unsigned long long)s.end[k] : w1;
-            w_next = first_word(d, start, end);
-        }
-        for (; k < nr; k += WARPS) {
-            const unsigned long long cs = start, ce = end;
-            const uint32_t w_cur = w_next;
-            const unsigned kn = k + WARPS;
-            if (kn < nr) {
-                start = (unsigned long long)s.end[kn - 1] + 1;
-                end = kn < running ? (unsigned long long)s.end[kn] : w1;
-                w_next = first_word(d, start, end);
-            }
-            decode_road(d, s, k, cs, ce, w_cur, err);
-        }
-    }
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK)
+        decode_road(d, s, k, k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1,
+                    k < running ? (unsigned long long)s.end[k] : w1, err);
     err = warp_min_u64(err);
     if (lane_id() == 0 && err != ~0ull)
         atomicMin(&s.err, err);
@@ -510,17 +469,19 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         (&s.multi[0][0])[i] = 0;
     }
     __syncthreads();
-    for (unsigned k = warp_id(); k < nr; k += WARPS) {
-        uint32_t pk = s.pk[k];
-        for (unsigned j = lane_id(); j < 40; j += 32) {
-            unsigned l = j >> 3, dd = j & 7u;
-            if (dd < ((pk >> (4 * l)) & 15u)) {
-                unsigned v = s.coord[k][j];
+    // one thread per road: each distinct coordinate of a layer marks the
+    // event's bitmap; a second road with it sets the multi bit
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
+        const uint32_t pk = s.pk[k];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned n = (pk >> (4 * l)) & 15u;
+            for (unsigned dd = 0; dd < n; ++dd) {
+                const unsigned v = s.coord[k][l * 8 + dd];
                 bool first = true;
                 for (unsigned x = 0; x < dd; ++x)
                     first = first && s.coord[k][l * 8 + x] != v;
                 if (first) {
-                    unsigned bit = 1u << (v & 31u);
+                    const unsigned bit = 1u << (v & 31u);
                     if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
                         atomicOr(&s.multi[l][v >> 5], bit);
                 }
@@ -528,29 +489,25 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         }
     }
     __syncthreads();
-    for (unsigned k = warp_id(); k < nr; k += WARPS) {
-        uint32_t pk = s.pk[k];
+    // the road records (one thread per road), then the coordinates (coalesced)
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
+        const uint32_t pk = s.pk[k];
         unsigned long long xm = 0;
-        for (unsigned pass = 0; pass < 2; ++pass) {      // all lanes vote in both passes
-            unsigned j = pass * 32 + lane_id(), l = j >> 3, dd = j & 7u;
-            bool f = false;
-            if (j < 40 && dd < ((pk >> (4 * l)) & 15u)) {
-                unsigned v = s.coord[k][j];
-                f = (s.multi[l][v >> 5] >> (v & 31u)) & 1u;
-            }
-            unsigned m = __ballot_sync(FULL_MASK, f);
-            xm |= (unsigned long long)m << (pass * 32);
-        }
         unsigned layers = 0;
-#pragma unroll
-        for (unsigned l = 0; l < N_LAYERS; ++l)
-            layers += ((xm >> (8 * l)) & 0xFFull) != 0;
-        bool cand = layers >= 3;
-        unsigned g = r0 + k;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned n = (pk >> (4 * l)) & 15u;
+            unsigned m = 0;
+            for (unsigned dd = 0; dd < n; ++dd) {
+                const unsigned v = s.coord[k][l * 8 + dd];
+                m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
+            }
+            xm |= (unsigned long long)m << (8 * l);
+            layers += m != 0;
+        }
+        const bool cand = layers >= 3;
+        const unsigned g = r0 + k;
         if (k < s.n_ep && g < d.max_roads) {   // EP-terminated segments are the roads
-            for (unsigned j = lane_id(); j < 40; j += 32)
-                d.coords[(size_t)g * 40 + j] = s.coord[k][j];
-            if (lane_id() == 0) {
+            {
                 RoadRec r;
                 r.event = e;
                 r.pk = pk | (cand ? (1u << 23) : 0u);
@@ -572,6 +529,11 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
                 n_comb += N;
             }
         }
+    }
+    for (unsigned i = threadIdx.x; i < nr * 40; i += BLOCK) {
+        const unsigned k = i / 40, g = r0 + k;
+        if (k < s.n_ep && g < d.max_roads)
+            d.coords[(size_t)r0 * 40 + i] = (&s.coord[0][0])[i];
     }
 }
 
