@@ -277,11 +277,20 @@ __device__ void p0_item(const Dev &d, unsigned c)
     unsigned long long end = min(base + CHUNK_WORDS, d.n_words);
     unsigned ee = 0, ep = 0;
     unsigned long long bad = ~0ull;
-    for (unsigned long long i = base + threadIdx.x; i < end; i += BLOCK) {
-        uint32_t w = __ldg(d.words + i);
-        ee += w >> 31;
-        ep += (w >> 30) & 1u;
-        if (!word_ok(w) && bad == ~0ull)
+    // all loads of a thread are issued before the first is used
+    static_assert(CHUNK_WORDS % BLOCK == 0, "a word chunk is a whole number of words per thread");
+    uint32_t w[CHUNK_WORDS / BLOCK];
+#pragma unroll
+    for (unsigned k = 0; k < CHUNK_WORDS / BLOCK; ++k) {
+        const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+        w[k] = i < end ? __ldg(d.words + i) : 0u;
+    }
+#pragma unroll
+    for (unsigned k = 0; k < CHUNK_WORDS / BLOCK; ++k) {
+        const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+        ee += w[k] >> 31;
+        ep += (w[k] >> 30) & 1u;
+        if (i < end && !word_ok(w[k]) && bad == ~0ull)
             bad = i;
     }
     if (bad != ~0ull)
@@ -425,10 +434,16 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         const unsigned per = (unsigned)((len + BLOCK - 1) / BLOCK);
         const unsigned long long a = rw + (unsigned long long)threadIdx.x * per;
         unsigned long long bits = 0;
-        for (unsigned j = 0; j < per; ++j) {
-            const unsigned long long i = a + j;
-            if (i < rw + len && ((__ldg(d.words + i) >> 30) & 1u))
-                bits |= 1ull << j;
+        for (unsigned j0 = 0; j0 < per; j0 += 8) {   // eight loads in flight
+            uint32_t w[8];
+#pragma unroll
+            for (unsigned u = 0; u < 8; ++u) {
+                const unsigned long long i = a + j0 + u;
+                w[u] = (j0 + u < per && i < rw + len) ? __ldg(d.words + i) : 0u;
+            }
+#pragma unroll
+            for (unsigned u = 0; u < 8; ++u)
+                bits |= (unsigned long long)((w[u] >> 30) & 1u) << (j0 + u);
         }
         unsigned long long tot;
         unsigned k = running + (unsigned)block_excl_scan((unsigned long long)__popcll(bits), &tot);
@@ -1485,22 +1500,21 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
 __device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
 {
     RoadRec rec = ldcg(d.roads + g);
-    unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
+    unsigned n[N_LAYERS];
+    for (unsigned l = 0; l < N_LAYERS; ++l)
         n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-        S5[l] = S;
-        S *= n[l];
-    }
     unsigned long long xm = ldcg(d.xmask + g);
     const uint16_t *co = d.coords + (size_t)g * 40;
     unsigned kept = 0;
     unsigned long long *keys = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = 0; i < cnt; ++i) {
         unsigned long long key = ldcg(keys + i);
-        unsigned comb = (unsigned)(key & 0x7FFFu);
+        unsigned t = (unsigned)(key & 0x7FFFu);
         unsigned dl[N_LAYERS], v[N_LAYERS];
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
-            dl[l] = (comb / S5[l]) % n[l];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
+            const unsigned q = divm(t, c_magic[n[l]]);
+            dl[l] = t - q * n[l];
+            t = q;
             v[l] = ldcg(co + l * 8 + dl[l]);
         }
         bool dropped = false;
@@ -1553,12 +1567,9 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
     if (!cnt)
         return;
     RoadRec rec = ldcg(d.roads + g);
-    unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
+    unsigned n[N_LAYERS];
+    for (unsigned l = 0; l < N_LAYERS; ++l)
         n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-        S5[l] = S;
-        S *= n[l];
-    }
     const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
     const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
     const uint16_t *co = d.coords + (size_t)g * 40;
@@ -1574,9 +1585,11 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
         t.chi2 = (long long)(key >> 23);
         int x[6];
         unsigned long long hits = 0;
-        unsigned j = 0;
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
-            unsigned dl = (comb / S5[l]) % n[l];
+        unsigned j = 0, rest = comb;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
+            const unsigned q = divm(rest, c_magic[n[l]]);
+            const unsigned dl = rest - q * n[l];
+            rest = q;
             unsigned v = ldcg(co + l * 8 + dl);
             hits |= (unsigned long long)v << (12 * l);
             if (l != excl)
