@@ -109,17 +109,14 @@ __device__ __forceinline__ void road_sizes(uint32_t pk, unsigned long long &N, u
     }
 }
 
-// exact floor(x / m) for x < 2^32 / m, m >= 1, with M = ceil(2^32 / m)
-__device__ __forceinline__ unsigned divm(unsigned x, unsigned long long M)
-{
-    return (unsigned)(((unsigned long long)x * M) >> 32);
-}
-__host__ __device__ constexpr unsigned long long magic(unsigned m)
-{
-    return ((1ull << 32) + m - 1) / m;
-}
+// floor(x / m) for 1 <= m <= 8 and x < 2^16 with M = ceil(2^31 / m):
+// (2x)(2^31 + e) / (m 2^32) = x / m + 2 x e / (m 2^32) with e < m, and
+// 2 x e < 2^32, so the high word of 2x * M is the quotient (32-bit
+// multiply-high, no 64-bit product).
+__device__ __forceinline__ unsigned divm(unsigned x, unsigned M) { return __umulhi(x << 1, M); }
+__host__ __device__ constexpr unsigned magic(unsigned m) { return (unsigned)(((1ull << 31) + m - 1) / m); }
 // magic(m) for the hit counts m = 1..8 (entry 0 repeats m = 1)
-__device__ __constant__ unsigned long long c_magic[MAX_HITS + 1] = {
+__device__ __constant__ unsigned c_magic[MAX_HITS + 1] = {
     magic(1), magic(1), magic(2), magic(3), magic(4), magic(5), magic(6), magic(7), magic(8)};
 
 template <class T>
@@ -624,7 +621,7 @@ struct RoadInfo {
     unsigned m[4], L[4], st[4];      // fitted slots: size, layer, 4-D stride
     unsigned slot_of[N_LAYERS];      // fitted slot of a layer (4 = excluded)
     unsigned S5[N_LAYERS];           // combination stride of each layer
-    unsigned long long M[3];         // magic divisors of m[0..2]
+    unsigned M[3];                   // magic divisors of m[0..2]
     unsigned N4, off[7];             // distinct fits; pair-table offsets
     int curv, phi;
 };
@@ -1054,7 +1051,7 @@ struct FlatRoad {
     int curv, phi;
     unsigned m[4], L[4], st[4], SL[4], aoff[4];
     unsigned off[6];
-    unsigned long long M[3];
+    unsigned M[3];                // magic divisors of m[0..2]
     unsigned long long cb;        // plain mode: first combination of the road
 };
 
