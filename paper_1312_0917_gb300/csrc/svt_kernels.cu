@@ -1058,7 +1058,9 @@ struct FlatRoad {
 struct P3Flat {
     int4 A[FLAT_A];                       // partial chi-square sums, [ab + aoff[j] + hit]
     unsigned long long K[FLAT_K];         // keys of distinct fits, [kb + f]
-    unsigned long long Q[FLAT_Q];         // pair tables, [qb + off[p] + x * m_b + y]
+    unsigned Qh[FLAT_Q], Ql[FLAT_Q];      // pair tables, [qb + off[p] + x * m_b + y]: high and
+                                          // low word of the minimum key (all ones = none)
+    uint16_t dig[FLAT_K];                 // the fit's four slot hits (3 bits each), its road's lane
     FlatRoad rd[WARP_ROADS];
     uint16_t co[WARP_ROADS][40];
     unsigned cnt[WARP_ROADS];             // survivors found so far
@@ -1162,7 +1164,8 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
             unsigned p = 0;
             while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
                 ++p;
-            mn = F.Q[r.qb + r.off[p] + da * r.m[fb] + db];
+            const unsigned idx = r.qb + r.off[p] + da * r.m[fb] + db;
+            mn = ((unsigned long long)F.Qh[idx] << 32) | F.Ql[idx];
             if (mn != NO_KEY)
                 mn += (unsigned long long)de * r.Se;
         }
@@ -1313,16 +1316,20 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         }
 
         // pair tables start empty
-        for (unsigned t = lane; t < nq; t += 32)
-            F.Q[t] = NO_KEY;
+        for (unsigned t = lane; t < nq; t += 32) {
+            F.Qh[t] = 0xFFFFFFFFu;
+            F.Ql[t] = 0xFFFFFFFFu;
+        }
         __syncwarp();
 
-        // keys of the distinct fits; each passing key lowers its entry in
-        // the six pair tables (minimum key over the fits with the same hits
-        // on two fitted slots)
+        // keys of the distinct fits.  The pair tables hold the minimum key of
+        // the fits with the same hits on two fitted slots; a 64-bit minimum
+        // is taken in two 32-bit atomic passes: the high words here, then
+        // the low words of the keys whose high word is the minimum.
         const long long cut = d.cut;
         for (unsigned t = lane; t < nk; t += 32) {
-            const FlatRoad &r = F.rd[xk.owner(t)];
+            const unsigned ri = xk.owner(t);
+            const FlatRoad &r = F.rd[ri];
             const unsigned f = t - r.kb;
             const unsigned q0 = divm(f, r.M[0]), f0 = f - q0 * r.m[0];
             const unsigned q1 = divm(q0, r.M[1]), f1 = q0 - q1 * r.m[1];
@@ -1343,13 +1350,32 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
             }
             F.K[t] = key;
+            F.dig[t] = (uint16_t)(f0 | (f1 << 3) | (f2 << 6) | (f3 << 9) | (ri << 12));
             if (key != NO_KEY) {
                 const unsigned fd[4] = {f0, f1, f2, f3};
+                const unsigned hi = (unsigned)(key >> 32);
 #pragma unroll
                 for (unsigned p = 0; p < 6; ++p) {
                     const unsigned a = pair_a(p), b = pair_b(p);
-                    atomicMin(&F.Q[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], key);
+                    atomicMin(&F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], hi);
                 }
+            }
+        }
+        __syncwarp();
+        for (unsigned t = lane; t < nk; t += 32) {
+            const unsigned long long key = F.K[t];
+            if (key == NO_KEY)
+                continue;
+            const unsigned dg = F.dig[t];
+            const FlatRoad &r = F.rd[dg >> 12];
+            const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
+            const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+#pragma unroll
+            for (unsigned p = 0; p < 6; ++p) {
+                const unsigned a = pair_a(p), b = pair_b(p);
+                const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                if (F.Qh[idx] == hi)
+                    atomicMin(&F.Ql[idx], lo);
             }
         }
         __syncwarp();
@@ -1361,23 +1387,19 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             bool surv = false;
             unsigned long long key = NO_KEY;
             if (t < nk) {
-                ri = xk.owner(t);
+                const unsigned dg = F.dig[t];
+                ri = dg >> 12;
                 const FlatRoad &r = F.rd[ri];
                 key = F.K[t];
                 if (key != NO_KEY) {
-                    const unsigned f = t - r.kb;
-                    unsigned fd[4];
-                    const unsigned q0 = divm(f, r.M[0]);
-                    fd[0] = f - q0 * r.m[0];
-                    const unsigned q1 = divm(q0, r.M[1]);
-                    fd[1] = q0 - q1 * r.m[1];
-                    fd[3] = divm(q1, r.M[2]);
-                    fd[2] = q1 - fd[3] * r.m[2];
+                    const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
+                    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
                     surv = true;
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
-                        surv = surv && F.Q[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == key;
+                        const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                        surv = surv && F.Qh[idx] == hi && F.Ql[idx] == lo;
                     }
                 }
             }
