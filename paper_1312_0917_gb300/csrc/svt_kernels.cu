@@ -378,25 +378,35 @@ __device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long l
 {
     unsigned n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;
     uint32_t hdr = 0, cw = 0, pw = 0;
-    for (unsigned long long pos = start; pos <= end; ++pos) {
-        const unsigned long long q = pos - start;
-        const uint32_t w = __ldg(d.words + pos);
-        const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
-        if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
-            (ep && q < 2))
-            err = min(err, (pos << 8) | RANK_BAD);
-        if (q == 0) {
-            hdr = w;
-        } else if (q == 1) {
-            cw = w;
-        } else if (q == 2) {
-            pw = w;
-        } else if (type <= 4) {
-            const unsigned rank = type == 0 ? n0++ : type == 1 ? n1++ : type == 2 ? n2++ : type == 3 ? n3++ : n4++;
-            if (rank >= MAX_HITS)
-                err = min(err, (pos << 8) | RANK_LIMIT);
-            else
-                s.coord[k][type * 8 + rank] = (uint16_t)(w & 0xFFFu);
+    for (unsigned long long base = start; base <= end; base += 8) {
+        uint32_t wb[8];
+#pragma unroll
+        for (unsigned u = 0; u < 8; ++u)   // eight loads in flight
+            wb[u] = base + u <= end ? __ldg(d.words + base + u) : 0u;
+#pragma unroll
+        for (unsigned u = 0; u < 8; ++u) {
+            const unsigned long long pos = base + u;
+            if (pos > end)
+                break;
+            const unsigned long long q = pos - start;
+            const uint32_t w = wb[u];
+            const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
+            if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
+                (ep && q < 2))
+                err = min(err, (pos << 8) | RANK_BAD);
+            if (q == 0) {
+                hdr = w;
+            } else if (q == 1) {
+                cw = w;
+            } else if (q == 2) {
+                pw = w;
+            } else if (type <= 4) {
+                const unsigned rank = type == 0 ? n0++ : type == 1 ? n1++ : type == 2 ? n2++ : type == 3 ? n3++ : n4++;
+                if (rank >= MAX_HITS)
+                    err = min(err, (pos << 8) | RANK_LIMIT);
+                else
+                    s.coord[k][type * 8 + rank] = (uint16_t)(w & 0xFFFu);
+            }
         }
     }
     const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
