@@ -370,52 +370,110 @@ struct P2Smem {
     uint32_t n_ep, n_seg;
 };
 
-// Decode road k of the event (words [start, end]) with one thread.  The
-// event's words are in L1 from the boundary scan.  Hit d of layer l is the
-// d-th hit word of that layer in the road.
-__device__ void decode_road(const Dev &d, P2Smem &s, unsigned k, unsigned long long start,
-                            unsigned long long end, unsigned long long &err)
+constexpr unsigned ROAD_THREADS = 4;                      // threads per road in P2
+constexpr unsigned ROADS_PER_PASS = BLOCK / ROAD_THREADS;
+
+// OR over the four threads of a road (lanes 4i .. 4i+3 of a warp)
+__device__ __forceinline__ unsigned group_or(unsigned x)
 {
-    unsigned n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;
+    x |= __shfl_xor_sync(FULL_MASK, x, 1, ROAD_THREADS);
+    x |= __shfl_xor_sync(FULL_MASK, x, 2, ROAD_THREADS);
+    return x;
+}
+
+// Decode road k of the event (words [start, end]) with the four threads of
+// its group; `sub` (0..3) takes a quarter of the words.  Every lane of the
+// warp calls it (`active` false for lanes without a road).  Hit d of layer l
+// is the d-th hit word of that layer in the road: each thread counts its
+// quarter's hits per layer, an exclusive scan over the group gives the ranks.
+__device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, unsigned sub,
+                            unsigned long long start, unsigned long long end, unsigned long long &err)
+{
+    const unsigned long long len = active && end >= start ? end - start + 1 : 0;
+    const unsigned long long per = (len + ROAD_THREADS - 1) / ROAD_THREADS;
+    const unsigned long long qa = min(sub * per, len), qb = min(qa + per, len);
+    unsigned c[N_LAYERS] = {0, 0, 0, 0, 0};
     uint32_t hdr = 0, cw = 0, pw = 0;
-    for (unsigned long long base = start; base <= end; base += 8) {
+    // pass 1: grammar, the road's first three words, hits per layer
+    for (unsigned long long base = qa; base < qb; base += 8) {
         uint32_t wb[8];
 #pragma unroll
         for (unsigned u = 0; u < 8; ++u)   // eight loads in flight
-            wb[u] = base + u <= end ? __ldg(d.words + base + u) : 0u;
+            wb[u] = base + u < qb ? __ldg(d.words + start + base + u) : 0u;
 #pragma unroll
         for (unsigned u = 0; u < 8; ++u) {
-            const unsigned long long pos = base + u;
-            if (pos > end)
+            const unsigned long long q = base + u;
+            if (q >= qb)
                 break;
-            const unsigned long long q = pos - start;
             const uint32_t w = wb[u];
             const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
             if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
                 (ep && q < 2))
-                err = min(err, (pos << 8) | RANK_BAD);
-            if (q == 0) {
+                err = min(err, ((start + q) << 8) | RANK_BAD);
+            if (q == 0)
                 hdr = w;
-            } else if (q == 1) {
+            else if (q == 1)
                 cw = w;
-            } else if (q == 2) {
+            else if (q == 2)
                 pw = w;
-            } else if (type <= 4) {
-                const unsigned rank = type == 0 ? n0++ : type == 1 ? n1++ : type == 2 ? n2++ : type == 3 ? n3++ : n4++;
-                if (rank >= MAX_HITS)
-                    err = min(err, (pos << 8) | RANK_LIMIT);
-                else
-                    s.coord[k][type * 8 + rank] = (uint16_t)(w & 0xFFFu);
-            }
+            else if (type <= 4)
+#pragma unroll
+                for (unsigned l = 0; l < N_LAYERS; ++l)
+                    c[l] += type == l;
         }
     }
-    const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
-    const unsigned excl = min((hdr >> 7) & 7u, 4u);
-    const unsigned mh = MAX_HITS;
-    s.pk[k] = min(n0, mh) | (min(n1, mh) << 4) | (min(n2, mh) << 8) | (min(n3, mh) << 12) |
-              (min(n4, mh) << 16) | (excl << 20) | ((k & 255u) << 24);
-    s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
-    s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
+    // ranks: exclusive scan of the per-layer counts over the group
+    unsigned rank[N_LAYERS], total[N_LAYERS];
+#pragma unroll
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        unsigned inc = c[l];
+#pragma unroll
+        for (unsigned o = 1; o < ROAD_THREADS; o <<= 1) {
+            const unsigned v = __shfl_up_sync(FULL_MASK, inc, o, ROAD_THREADS);
+            if (sub >= o)
+                inc += v;
+        }
+        rank[l] = inc - c[l];
+        total[l] = __shfl_sync(FULL_MASK, inc, ROAD_THREADS - 1, ROAD_THREADS);
+    }
+    hdr = group_or(hdr);
+    cw = group_or(cw);
+    pw = group_or(pw);
+    // pass 2: place the hits (the words are in L1)
+    for (unsigned long long base = max(qa, 3ull); base < qb; base += 8) {
+        uint32_t wb[8];
+#pragma unroll
+        for (unsigned u = 0; u < 8; ++u)
+            wb[u] = base + u < qb ? __ldg(d.words + start + base + u) : 0u;
+#pragma unroll
+        for (unsigned u = 0; u < 8; ++u) {
+            const unsigned long long q = base + u;
+            if (q >= qb)
+                break;
+            const uint32_t w = wb[u];
+            const unsigned type = (w >> 27) & 7u;
+            if (type > 4)
+                continue;
+            unsigned r = 0;
+#pragma unroll
+            for (unsigned l = 0; l < N_LAYERS; ++l)
+                if (type == l)
+                    r = rank[l]++;
+            if (r >= MAX_HITS)
+                err = min(err, ((start + q) << 8) | RANK_LIMIT);
+            else
+                s.coord[k][type * 8 + r] = (uint16_t)(w & 0xFFFu);
+        }
+    }
+    if (active && sub == 0) {
+        const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
+        const unsigned excl = min((hdr >> 7) & 7u, 4u);
+        const unsigned mh = MAX_HITS;
+        s.pk[k] = min(total[0], mh) | (min(total[1], mh) << 4) | (min(total[2], mh) << 8) |
+                  (min(total[3], mh) << 12) | (min(total[4], mh) << 16) | (excl << 20) | ((k & 255u) << 24);
+        s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
+        s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
+    }
 }
 
 // Unpack event e (CTA-wide); adds the event's combinations to n_comb.
@@ -468,14 +526,18 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
     unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
 
-    // decode: one thread per road; unused hit slots stay 0
+    // decode: four threads per road; unused hit slots stay 0
     for (unsigned i = threadIdx.x; i < nr * 40; i += BLOCK)
         (&s.coord[0][0])[i] = 0;
     __syncthreads();
     unsigned long long err = ~0ull;
-    for (unsigned k = threadIdx.x; k < nr; k += BLOCK)
-        decode_road(d, s, k, k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1,
-                    k < running ? (unsigned long long)s.end[k] : w1, err);
+    const unsigned sub = threadIdx.x % ROAD_THREADS;
+    for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
+        const unsigned k = kb + threadIdx.x / ROAD_THREADS;
+        const bool active = k < nr;
+        decode_road(d, s, active, k, sub, !active || k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1,
+                    !active ? w0 : k < running ? (unsigned long long)s.end[k] : w1, err);
+    }
     err = warp_min_u64(err);
     if (lane_id() == 0 && err != ~0ull)
         atomicMin(&s.err, err);
@@ -491,11 +553,13 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         (&s.multi[0][0])[i] = 0;
     }
     __syncthreads();
-    // one thread per road: each distinct coordinate of a layer marks the
-    // event's bitmap; a second road with it sets the multi bit
-    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
+    // four threads per road (layers sub and sub + 4): each distinct
+    // coordinate of a layer marks the event's bitmap; a second road with it
+    // sets the multi bit
+    for (unsigned i = threadIdx.x; i < nr * ROAD_THREADS; i += BLOCK) {
+        const unsigned k = i / ROAD_THREADS;
         const uint32_t pk = s.pk[k];
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
+        for (unsigned l = i % ROAD_THREADS; l < N_LAYERS; l += ROAD_THREADS) {
             const unsigned n = (pk >> (4 * l)) & 15u;
             for (unsigned dd = 0; dd < n; ++dd) {
                 const unsigned v = s.coord[k][l * 8 + dd];
@@ -511,24 +575,32 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         }
     }
     __syncthreads();
-    // the road records (one thread per road), then the coordinates (coalesced)
-    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
-        const uint32_t pk = s.pk[k];
-        unsigned long long xm = 0;
-        unsigned layers = 0;
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
+    // the road records (four threads per road: layers sub and sub + 4, the
+    // first thread writes), then the coordinates (coalesced)
+    for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
+        const unsigned k = kb + threadIdx.x / ROAD_THREADS;
+        const uint32_t pk = k < nr ? s.pk[k] : 0u;
+        unsigned lo = 0, hi = 0;   // flagged hits of layers 0..3 and of layer 4
+        for (unsigned l = sub; l < N_LAYERS && k < nr; l += ROAD_THREADS) {
             const unsigned n = (pk >> (4 * l)) & 15u;
             unsigned m = 0;
             for (unsigned dd = 0; dd < n; ++dd) {
                 const unsigned v = s.coord[k][l * 8 + dd];
                 m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
             }
-            xm |= (unsigned long long)m << (8 * l);
-            layers += m != 0;
+            if (l < 4)
+                lo |= m << (8 * l);
+            else
+                hi = m;
         }
+        lo = group_or(lo);
+        hi = group_or(hi);
+        const unsigned long long xm = ((unsigned long long)hi << 32) | lo;
+        const unsigned layers = ((lo & 0xFFu) != 0) + ((lo & 0xFF00u) != 0) + ((lo & 0xFF0000u) != 0) +
+                                ((lo >> 24) != 0) + (hi != 0);
         const bool cand = layers >= 3;
         const unsigned g = r0 + k;
-        if (k < s.n_ep && g < d.max_roads) {   // EP-terminated segments are the roads
+        if (k < nr && sub == 0 && k < s.n_ep && g < d.max_roads) {   // EP-terminated segments are the roads
             {
                 RoadRec r;
                 r.event = e;
