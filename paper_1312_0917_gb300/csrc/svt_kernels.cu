@@ -1659,25 +1659,44 @@ __device__ void p4_finish(const Dev &d, unsigned n_chunks)
     }
 }
 
+// Output of one chunk of ROAD_CHUNK roads: a block scan of the survivor
+// counts gives each road's first output slot; then each thread takes
+// survivors (not roads), so roads with many survivors are spread out.
 template <bool PLAIN>
-__device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
+__device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_first)
 {
-    unsigned g = c * ROAD_CHUNK + threadIdx.x;
-    unsigned cnt = g < n_roads ? ldcg(d.surv_cnt + g) : 0u;
-    unsigned long long pos = ldcg(d.rchunk_off + c) + block_excl_scan(cnt, nullptr);
-    if (!cnt)
-        return;
-    RoadRec rec = ldcg(d.roads + g);
-    unsigned n[N_LAYERS];
-    for (unsigned l = 0; l < N_LAYERS; ++l)
-        n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-    const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
-    const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
-    const uint16_t *co = d.coords + (size_t)g * 40;
-    const unsigned long long *keys = d.surv_pool + (size_t)g * SURV_SLOTS;
-    for (unsigned i = 0; i < cnt; ++i, ++pos) {
-        unsigned long long key = ldcg(keys + i);
-        unsigned comb = (unsigned)(key & 0x7FFFu);
+    // s_first: ROAD_CHUNK + 1 shared words, the first survivor of each road
+    static_assert(ROAD_CHUNK == BLOCK, "one thread per road of a chunk");
+    const unsigned g_me = c * ROAD_CHUNK + threadIdx.x;
+    const unsigned cnt_me = g_me < n_roads ? ldcg(d.surv_cnt + g_me) : 0u;
+    unsigned long long total;
+    const unsigned ex = (unsigned)block_excl_scan(cnt_me, &total);
+    s_first[threadIdx.x] = ex;
+    if (threadIdx.x == 0)
+        s_first[ROAD_CHUNK] = (unsigned)total;
+    const unsigned long long base = ldcg(d.rchunk_off + c);
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < (unsigned)total; i += BLOCK) {
+        // road of survivor i: the last r with s_first[r] <= i (and a survivor)
+        unsigned lo = 0, hi = ROAD_CHUNK;
+        while (hi - lo > 1) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (s_first[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const unsigned g = c * ROAD_CHUNK + lo, idx = i - s_first[lo];
+        const unsigned long long pos = base + i;
+        const RoadRec rec = ldcg(d.roads + g);
+        unsigned n[N_LAYERS];
+        for (unsigned l = 0; l < N_LAYERS; ++l)
+            n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+        const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
+        const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+        const uint16_t *co = d.coords + (size_t)g * 40;
+        const unsigned long long key = ldcg(d.surv_pool + (size_t)g * SURV_SLOTS + idx);
+        const unsigned comb = (unsigned)(key & 0x7FFFu);
         svt_track t;
         t.event = rec.event;
         t.road = (uint16_t)(rec.pk >> 24);
@@ -1691,7 +1710,7 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
             const unsigned q = divm(rest, c_magic[n[l]]);
             const unsigned dl = rest - q * n[l];
             rest = q;
-            unsigned v = ldcg(co + l * 8 + dl);
+            const unsigned v = ldcg(co + l * 8 + dl);
             hits |= (unsigned long long)v << (12 * l);
             if (l != excl)
                 x[j++] = (int)v;
@@ -1700,7 +1719,7 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
         x[5] = rec.phi;
         t.hits = hits;
         if (PLAIN) {
-            unsigned long long ci = ldcg(d.comb_off + g) + comb;
+            const unsigned long long ci = ldcg(d.comb_off + g) + comb;
             t.p[0] = ldcg(d.fit_p + 3 * ci);
             t.p[1] = ldcg(d.fit_p + 3 * ci + 1);
             t.p[2] = ldcg(d.fit_p + 3 * ci + 2);
@@ -1715,6 +1734,7 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads)
         if (pos < d.max_tracks)
             d.tracks[pos] = t;
     }
+    __syncthreads();   // s_first is reused by the next chunk
 }
 
 __device__ void clear_hash(const Dev &d, unsigned i)
@@ -1779,7 +1799,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     stamp(d, 5);
     if (!(ldcg(&d.ctrl->flags) & FLAG_CAPACITY))
         for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
-            p5_item<false>(d, c, n_roads);
+            p5_item<false>(d, c, n_roads, reinterpret_cast<unsigned *>(smem));
     // every lookup is done (barrier above): leave the group table empty
     const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += nb * BLOCK)
@@ -1953,11 +1973,12 @@ __global__ void __launch_bounds__(BLOCK) k_p4(Dev d)
 
 __global__ void __launch_bounds__(BLOCK) k_p5(Dev d)
 {
+    __shared__ unsigned s_first[ROAD_CHUNK + 1];
     const unsigned n_roads = ldcg(&d.ctrl->n_roads);
     const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
     if (!stop_after_unpack(d))
         for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
-            p5_item<true>(d, c, n_roads);
+            p5_item<true>(d, c, n_roads, s_first);
     // the previous kernels' lookups are done: leave the group table empty
     const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += gridDim.x * BLOCK)
