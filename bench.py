@@ -170,8 +170,9 @@ def run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, steps, warmup, stream)
 
 def cpu_baseline(batch, consts, cut, target_s=20.0):
     """The oracle as it stands, single thread, on the first events of the
-    batch (grown until one run takes about target_s / 2 seconds, or the
-    whole batch)."""
+    batch (grown until one run takes about target_s / 2 seconds; when the
+    whole batch takes less, it is run again until target_s / 2 seconds have
+    passed)."""
     import oracle
     oracle.build()
     n_ev = 25
@@ -183,10 +184,16 @@ def cpu_baseline(batch, consts, cut, target_s=20.0):
         if dt > target_s / 2 or n_ev >= batch.n_events:
             break
         n_ev = min(batch.n_events, int(n_ev * max(2.0, 1.1 * target_s / 2 / max(dt, 1e-3))))
+    runs = 1
+    while dt < target_s / 2:
+        t0 = time.perf_counter()
+        oracle.run(words, consts, cut)
+        dt += time.perf_counter() - t0
+        runs += 1
     fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
-    return {"value": fits / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d events of the batch (%d combinations), one run, %.1f s"
-                      % (n_ev, fits, dt)}
+    return {"value": fits * runs / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d events of the batch (%d combinations), %d run(s), %.1f s"
+                      % (n_ev, fits, runs, dt)}
 
 
 def run_serving(B, synth, consts, cut, rates, seconds, n_slots=4, seed=0):
@@ -258,8 +265,8 @@ def run_serving(B, synth, consts, cut, rates, seconds, n_slots=4, seed=0):
 # sources (kernels and their header) it was taken on: the bench line reports
 # it only while they are unchanged.
 NCU_TRAFFIC = {"workload": "scaled",
-               "kernels_sha256": "2befe80619e1789a4d7fa70d526fbf315eedcc0391a52e88b264a9c7051d5610",
-               "bytes": 77790208}
+               "kernels_sha256": "6fc26f9f3f7a32158dd667eaee2b1a8e6e0da5aa44c1779dd7b0c775c2d48658",
+               "bytes": 69309184}
 
 
 def measured_traffic(workload: str):
