@@ -1444,66 +1444,78 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             }
         }
         __syncwarp();
-        for (unsigned t = lane; t < nk; t += 32) {
-            const unsigned long long key = F.K[t];
-            if (key == NO_KEY)
-                continue;
-            const unsigned dg = F.dig[t];
-            const FlatRoad &r = F.rd[dg >> 12];
-            const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
-            const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
-#pragma unroll
-            for (unsigned p = 0; p < 6; ++p) {
-                const unsigned a = pair_a(p), b = pair_b(p);
-                const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
-                if (F.Qh[idx] == hi)
-                    atomicMin(&F.Ql[idx], lo);
-            }
-        }
-        __syncwarp();
-
-        // survivors: keys that are the minimum of all six of their pair tables
+        // low words: keys whose high word is a table's minimum.  A key whose
+        // high word is the minimum of all six tables is a candidate; the
+        // candidates are listed, in entry order, over the partial sums
+        // (no longer needed).
+        uint16_t *cl = reinterpret_cast<uint16_t *>(F.A);
+        static_assert(sizeof(F.A) >= FLAT_K * sizeof(uint16_t), "candidate list fits over A");
+        unsigned ncand = 0;
         for (unsigned base = 0; base < nk; base += 32) {
             const unsigned t = base + lane;
-            unsigned ri = 0;
-            bool surv = false;
-            unsigned long long key = NO_KEY;
+            bool cand = false;
             if (t < nk) {
-                const unsigned dg = F.dig[t];
-                ri = dg >> 12;
-                const FlatRoad &r = F.rd[ri];
-                key = F.K[t];
+                const unsigned long long key = F.K[t];
                 if (key != NO_KEY) {
+                    const unsigned dg = F.dig[t];
+                    const FlatRoad &r = F.rd[dg >> 12];
                     const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
                     const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
-                    surv = true;
+                    cand = true;
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
                         const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
-                        surv = surv && F.Qh[idx] == hi && F.Ql[idx] == lo;
+                        if (F.Qh[idx] == hi)
+                            atomicMin(&F.Ql[idx], lo);
+                        else
+                            cand = false;
                     }
                 }
             }
+            const unsigned cb = __ballot_sync(FULL_MASK, cand);
+            if (cand)
+                cl[ncand + __popc(cb & lanemask_lt())] = (uint16_t)t;
+            ncand += __popc(cb);
+        }
+        __syncwarp();
+
+        // survivors: candidates that hold the minimum of all six tables.  A
+        // road's survivors take its slots in entry order.
+        for (unsigned base = 0; base < ncand; base += 32) {
+            const unsigned i = base + lane;
+            unsigned ri = WARP_ROADS + lane;   // distinct per lane unless a survivor
+            bool surv = false;
+            unsigned long long key = NO_KEY;
+            if (i < ncand) {
+                const unsigned t = cl[i];
+                const unsigned dg = F.dig[t];
+                const FlatRoad &r = F.rd[dg >> 12];
+                const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
+                key = F.K[t];
+                const unsigned lo = (unsigned)key;
+                surv = true;
+#pragma unroll
+                for (unsigned p = 0; p < 6; ++p) {
+                    const unsigned a = pair_a(p), b = pair_b(p);
+                    surv = surv && F.Ql[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
+                }
+                if (surv)
+                    ri = dg >> 12;
+            }
             const unsigned sv = __ballot_sync(FULL_MASK, surv);
-            // lanes of road ri in this pass: its entries [kb, kb + N4) within [base, base + 32)
+            const unsigned same = __match_any_sync(FULL_MASK, ri) & sv;
+            unsigned pos = 0;
+            if (surv)
+                pos = F.cnt[ri] + __popc(same & lanemask_lt());
+            __syncwarp();
             if (surv) {
-                const FlatRoad &r = F.rd[ri];
-                const unsigned lo = max(r.kb, base) - base;
-                const unsigned pos = F.cnt[ri] + __popc(sv & lanemask_lt() & ~((1u << lo) - 1u));
                 if (pos < SURV_SLOTS)
-                    d.surv_pool[(size_t)r.g * SURV_SLOTS + pos] = key;
+                    d.surv_pool[(size_t)F.rd[ri].g * SURV_SLOTS + pos] = key;
                 else
                     raise_flag(d, FLAG_INTERNAL);
-            }
-            __syncwarp();
-            if ((sub >> lane) & 1u) {   // road of this lane: add this pass's survivors
-                const unsigned lo = min(max(fr.kb, base), base + 32) - base;
-                const unsigned hi = min(max(fr.kb + N4, base), base + 32) - base;
-                if (lo < 32) {
-                    const unsigned below_hi = hi >= 32 ? ~0u : (1u << hi) - 1u;
-                    F.cnt[lane] += __popc(sv & below_hi & ~((1u << lo) - 1u));
-                }
+                if ((same >> lane) == 1u)   // the last survivor of its road in this batch
+                    F.cnt[ri] = pos + 1;
             }
             __syncwarp();
         }
