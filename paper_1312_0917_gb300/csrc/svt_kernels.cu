@@ -1397,86 +1397,137 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             __syncwarp();
         }
 
-        // pair tables start empty
-        for (unsigned t = lane; t < nq; t += 32) {
+        // pair tables start empty (the low words once they are needed)
+        for (unsigned t = lane; t < nq; t += 32)
             F.Qh[t] = 0xFFFFFFFFu;
-            F.Ql[t] = 0xFFFFFFFFu;
-        }
         __syncwarp();
 
         // keys of the distinct fits.  The pair tables hold the minimum key of
         // the fits with the same hits on two fitted slots; a 64-bit minimum
-        // is taken in two 32-bit atomic passes: the high words here, then
-        // the low words of the keys whose high word is the minimum.
+        // is taken in two 32-bit steps: the high words here, then, only if
+        // a table has two keys with its minimum high word (a tie), the low
+        // words of the keys whose high word is the minimum.  A key that
+        // finds a lower high word already in one of its tables cannot be a
+        // table's minimum there; the others ("maybe" keys) are listed in
+        // entry order over the low words, unused until a tie.  The second
+        // of two keys with the minimum high word of a table always finds
+        // it there, so every tie at a minimum is seen.
         const long long cut = d.cut;
-        for (unsigned t = lane; t < nk; t += 32) {
-            const unsigned ri = xk.owner(t);
-            const FlatRoad &r = F.rd[ri];
-            const unsigned f = t - r.kb;
-            const unsigned q0 = divm(f, r.M[0]), f0 = f - q0 * r.m[0];
-            const unsigned q1 = divm(q0, r.M[1]), f1 = q0 - q1 * r.m[1];
-            const unsigned f3 = divm(q1, r.M[2]), f2 = q1 - f3 * r.m[2];
-            const unsigned comb = f0 * r.SL[0] + f1 * r.SL[1] + f2 * r.SL[2] + f3 * r.SL[3];
-            unsigned long long key;
-            if (PLAIN) {
-                key = ldcg(d.fit_key + r.cb + comb);
-            } else {
-                const int4 a0 = F.A[r.ab + r.aoff[0] + f0], a1 = F.A[r.ab + r.aoff[1] + f1];
-                const int4 a2 = F.A[r.ab + r.aoff[2] + f2], a3 = F.A[r.ab + r.aoff[3] + f3];
-                const int sx = a0.x + a1.x + a2.x + a3.x;
-                const int sy = a0.y + a1.y + a2.y + a3.y;
-                const int sz = a0.z + a1.z + a2.z + a3.z;
-                const long long chi2 = sq(sx >> 12) + sq(sy >> 12) + sq(sz >> 12);
-                const bool pass = chi2 <= cut;
-                npass += pass ? r.ne : 0u;
-                key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
-            }
-            F.K[t] = key;
-            F.dig[t] = (uint16_t)(f0 | (f1 << 3) | (f2 << 6) | (f3 << 9) | (ri << 12));
-            if (key != NO_KEY) {
-                const unsigned fd[4] = {f0, f1, f2, f3};
-                const unsigned hi = (unsigned)(key >> 32);
+        uint16_t *ml = reinterpret_cast<uint16_t *>(F.Ql);
+        static_assert(sizeof(F.Ql) >= FLAT_K * sizeof(uint16_t), "maybe list fits over Ql");
+        unsigned nmaybe = 0;
+        bool tie = false;
+        for (unsigned base = 0; base < nk; base += 32) {
+            const unsigned t = base + lane;
+            bool maybe = false;
+            if (t < nk) {
+                const unsigned ri = xk.owner(t);
+                const FlatRoad &r = F.rd[ri];
+                const unsigned f = t - r.kb;
+                const unsigned q0 = divm(f, r.M[0]), f0 = f - q0 * r.m[0];
+                const unsigned q1 = divm(q0, r.M[1]), f1 = q0 - q1 * r.m[1];
+                const unsigned f3 = divm(q1, r.M[2]), f2 = q1 - f3 * r.m[2];
+                const unsigned comb = f0 * r.SL[0] + f1 * r.SL[1] + f2 * r.SL[2] + f3 * r.SL[3];
+                unsigned long long key;
+                if (PLAIN) {
+                    key = ldcg(d.fit_key + r.cb + comb);
+                } else {
+                    const int4 a0 = F.A[r.ab + r.aoff[0] + f0], a1 = F.A[r.ab + r.aoff[1] + f1];
+                    const int4 a2 = F.A[r.ab + r.aoff[2] + f2], a3 = F.A[r.ab + r.aoff[3] + f3];
+                    const int sx = a0.x + a1.x + a2.x + a3.x;
+                    const int sy = a0.y + a1.y + a2.y + a3.y;
+                    const int sz = a0.z + a1.z + a2.z + a3.z;
+                    const long long chi2 = sq(sx >> 12) + sq(sy >> 12) + sq(sz >> 12);
+                    const bool pass = chi2 <= cut;
+                    npass += pass ? r.ne : 0u;
+                    key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
+                }
+                F.K[t] = key;
+                F.dig[t] = (uint16_t)(f0 | (f1 << 3) | (f2 << 6) | (f3 << 9) | (ri << 12));
+                if (key != NO_KEY) {
+                    const unsigned fd[4] = {f0, f1, f2, f3};
+                    const unsigned hi = (unsigned)(key >> 32);
+                    maybe = true;
 #pragma unroll
-                for (unsigned p = 0; p < 6; ++p) {
-                    const unsigned a = pair_a(p), b = pair_b(p);
-                    atomicMin(&F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], hi);
+                    for (unsigned p = 0; p < 6; ++p) {
+                        const unsigned a = pair_a(p), b = pair_b(p);
+                        const unsigned old = atomicMin(&F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], hi);
+                        maybe = maybe && old >= hi;
+                        tie = tie || old == hi;
+                    }
                 }
             }
+            const unsigned mb = __ballot_sync(FULL_MASK, maybe);
+            if (maybe)
+                ml[nmaybe + __popc(mb & lanemask_lt())] = (uint16_t)t;
+            nmaybe += __popc(mb);
         }
+        const bool ties = __any_sync(FULL_MASK, tie);
         __syncwarp();
-        // low words: keys whose high word is a table's minimum.  A key whose
-        // high word is the minimum of all six tables is a candidate; the
-        // candidates are listed, in entry order, over the partial sums
-        // (no longer needed).
+
+        // candidates: keys whose high word is the minimum of all six
+        // tables, listed in entry order over the partial sums (no longer
+        // needed).  Without a tie a candidate is a survivor.
         uint16_t *cl = reinterpret_cast<uint16_t *>(F.A);
         static_assert(sizeof(F.A) >= FLAT_K * sizeof(uint16_t), "candidate list fits over A");
         unsigned ncand = 0;
-        for (unsigned base = 0; base < nk; base += 32) {
-            const unsigned t = base + lane;
-            bool cand = false;
-            if (t < nk) {
-                const unsigned long long key = F.K[t];
-                if (key != NO_KEY) {
+        if (!ties) {
+            for (unsigned base = 0; base < nmaybe; base += 32) {
+                const unsigned i = base + lane;
+                bool cand = false;
+                unsigned t = 0;
+                if (i < nmaybe) {
+                    t = ml[i];
+                    const unsigned hi = (unsigned)(F.K[t] >> 32);
                     const unsigned dg = F.dig[t];
                     const FlatRoad &r = F.rd[dg >> 12];
                     const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
-                    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
                     cand = true;
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
-                        const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
-                        if (F.Qh[idx] == hi)
-                            atomicMin(&F.Ql[idx], lo);
-                        else
-                            cand = false;
+                        cand = cand && F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == hi;
                     }
                 }
+                const unsigned cb = __ballot_sync(FULL_MASK, cand);
+                if (cand)
+                    cl[ncand + __popc(cb & lanemask_lt())] = (uint16_t)t;
+                ncand += __popc(cb);
             }
-            const unsigned cb = __ballot_sync(FULL_MASK, cand);
-            if (cand)
-                cl[ncand + __popc(cb & lanemask_lt())] = (uint16_t)t;
-            ncand += __popc(cb);
+        } else {
+            // a tie: the low words start empty (the list over them is
+            // dropped) and every key with a table's minimum high word
+            // takes part in that table's low-word minimum
+            for (unsigned t = lane; t < nq; t += 32)
+                F.Ql[t] = 0xFFFFFFFFu;
+            __syncwarp();
+            for (unsigned base = 0; base < nk; base += 32) {
+                const unsigned t = base + lane;
+                bool cand = false;
+                if (t < nk) {
+                    const unsigned long long key = F.K[t];
+                    if (key != NO_KEY) {
+                        const unsigned dg = F.dig[t];
+                        const FlatRoad &r = F.rd[dg >> 12];
+                        const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
+                        const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+                        cand = true;
+#pragma unroll
+                        for (unsigned p = 0; p < 6; ++p) {
+                            const unsigned a = pair_a(p), b = pair_b(p);
+                            const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                            if (F.Qh[idx] == hi)
+                                atomicMin(&F.Ql[idx], lo);
+                            else
+                                cand = false;
+                        }
+                    }
+                }
+                const unsigned cb = __ballot_sync(FULL_MASK, cand);
+                if (cand)
+                    cl[ncand + __popc(cb & lanemask_lt())] = (uint16_t)t;
+                ncand += __popc(cb);
+            }
         }
         __syncwarp();
 
@@ -1495,10 +1546,12 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 key = F.K[t];
                 const unsigned lo = (unsigned)key;
                 surv = true;
+                if (ties) {
 #pragma unroll
-                for (unsigned p = 0; p < 6; ++p) {
-                    const unsigned a = pair_a(p), b = pair_b(p);
-                    surv = surv && F.Ql[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
+                    for (unsigned p = 0; p < 6; ++p) {
+                        const unsigned a = pair_a(p), b = pair_b(p);
+                        surv = surv && F.Ql[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
+                    }
                 }
                 if (surv)
                     ri = dg >> 12;
@@ -1521,10 +1574,35 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         }
         if ((sub >> lane) & 1u)
             d.surv_cnt[g0 + lane] = (uint8_t)min(F.cnt[lane], (unsigned)SURV_SLOTS);
-        // cross-road candidates of the sub-run publish their group minima
-        for (unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && fr.cand); cands;
-             cands &= cands - 1)
-            flat_publish(d, F, __ffs(cands) - 1);
+        // cross-road candidates of the sub-run publish their group minima,
+        // which read whole keys from the pair tables.  Without a tie the low
+        // words were not taken: each table's minimum high word belongs to
+        // one key, which writes its low word.
+        const unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && fr.cand);
+        if (cands && !ties) {
+            for (unsigned t = lane; t < nq; t += 32)
+                F.Ql[t] = 0xFFFFFFFFu;
+            __syncwarp();
+            for (unsigned t = lane; t < nk; t += 32) {
+                const unsigned long long key = F.K[t];
+                if (key == NO_KEY)
+                    continue;
+                const unsigned dg = F.dig[t];
+                const FlatRoad &r = F.rd[dg >> 12];
+                const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
+                const unsigned hi = (unsigned)(key >> 32);
+#pragma unroll
+                for (unsigned p = 0; p < 6; ++p) {
+                    const unsigned a = pair_a(p), b = pair_b(p);
+                    const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                    if (F.Qh[idx] == hi)
+                        F.Ql[idx] = (unsigned)key;
+                }
+            }
+            __syncwarp();
+        }
+        for (unsigned c = cands; c; c &= c - 1)
+            flat_publish(d, F, __ffs(c) - 1);
         todo &= ~sub;
         __syncwarp();
     }
