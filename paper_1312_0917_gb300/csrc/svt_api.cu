@@ -173,6 +173,8 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     c->lim = L;
     Dev &d = c->d;
     unsigned n_chunks_w = (unsigned)((L.max_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
+    // chunk slots: the plain kernels' word chunks, the persistent kernel's CTAs
+    const unsigned n_slots_w = n_chunks_w > (unsigned)MAX_GRID ? n_chunks_w : (unsigned)MAX_GRID;
     d.max_events = L.max_events;
     d.max_roads = L.max_roads;
     d.max_chunks_r = (L.max_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
@@ -182,8 +184,8 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     d.small_n4 = N4_SMALL_MAX;
     bool ok =
         !dalloc(c, &d.ctrl, 1) && !dalloc(c, const_cast<svt_const_set **>(&d.consts), N_SETS) &&
-        !dalloc(c, &d.chunk_ee, n_chunks_w) && !dalloc(c, &d.chunk_ep, n_chunks_w) &&
-        !dalloc(c, &d.chunk_ee_off, n_chunks_w) && !dalloc(c, &d.chunk_ep_off, n_chunks_w) &&
+        !dalloc(c, &d.chunk_ee, n_slots_w) && !dalloc(c, &d.chunk_ep, n_slots_w) &&
+        !dalloc(c, &d.chunk_ee_off, n_slots_w) && !dalloc(c, &d.chunk_ep_off, n_slots_w) &&
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&

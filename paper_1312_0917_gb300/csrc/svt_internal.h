@@ -11,6 +11,8 @@ namespace svt {
 constexpr int BLOCK = 256;                 // threads per CTA, every kernel
 constexpr int WARPS = BLOCK / 32;
 constexpr int CHUNK_WORDS = 4096;          // words per unpack work item (16 per thread)
+constexpr int MAX_GRID = 4096;             // CTAs of the persistent kernel at most (its word-scan
+                                           // totals use the first MAX_GRID chunk slots)
 constexpr int MAX_ROADS_EV = 256;          // format limit: roads per event
 constexpr int MAX_HITS = 8;                // format limit: hits per layer per road
 constexpr int N_LAYERS = 5;

@@ -355,6 +355,150 @@ __device__ void p1_item(const Dev &d, unsigned c)
 }
 
 // ---------------------------------------------------------------------------
+// P0 / P1 of the persistent kernel: CTA b owns one contiguous slice of the
+// words (equal slices, a multiple of 32 words).  P0 counts the slice's EE
+// and EP words; after the grid barrier every CTA sums the CTA totals below
+// its own (its offsets) and over all CTAs (the stream's counts), so no CTA
+// scans for the others, and P1 scatters the slice's event boundaries.
+// ---------------------------------------------------------------------------
+
+constexpr unsigned SCAN_PT = 32;                     // words per thread per tile
+constexpr unsigned SCAN_TILE = BLOCK * SCAN_PT;
+
+// a tile staged in shared memory, one pad word per 32 so that thread t can
+// read its 32 consecutive words without bank conflicts
+struct ScanSmem {
+    uint32_t w[SCAN_TILE + SCAN_TILE / 32];
+};
+__device__ __forceinline__ unsigned scan_pad(unsigned i) { return i + (i >> 5); }
+
+__device__ __forceinline__ void scan_slice(const Dev &d, unsigned long long &w0, unsigned long long &w1)
+{
+    const unsigned long long per = ((d.n_words + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+    w0 = min((unsigned long long)blockIdx.x * per, d.n_words);
+    w1 = min(w0 + per, d.n_words);
+}
+
+__device__ void scan_count(const Dev &d)
+{
+    unsigned long long w0, w1;
+    scan_slice(d, w0, w1);
+    unsigned ee = 0, ep = 0;
+    unsigned long long bad = ~0ull;
+    for (unsigned long long base = w0; base < w1; base += SCAN_TILE) {
+        uint32_t w[SCAN_PT];   // all loads issued before the first is used
+#pragma unroll
+        for (unsigned k = 0; k < SCAN_PT; ++k) {
+            const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+            w[k] = i < w1 ? __ldg(d.words + i) : 0u;
+        }
+#pragma unroll
+        for (unsigned k = 0; k < SCAN_PT; ++k) {
+            const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+            ee += w[k] >> 31;
+            ep += (w[k] >> 30) & 1u;
+            if (i < w1 && !word_ok(w[k]) && bad == ~0ull)
+                bad = i;
+        }
+    }
+    if (bad != ~0ull)
+        report(d, bad, RANK_BAD);
+    // EE count in the high half, EP count in the low half (each < 2^32)
+    const unsigned long long tot = block_sum(((unsigned long long)ee << 32) | ep);
+    if (threadIdx.x == 0) {
+        d.chunk_ee[blockIdx.x] = (uint32_t)(tot >> 32);
+        d.chunk_ep[blockIdx.x] = (uint32_t)tot;
+    }
+}
+
+// P1; false when the stream does not fit the context (every CTA sees the
+// same totals and stops)
+__device__ bool scan_scatter(const Dev &d, unsigned char *smem)
+{
+    ScanSmem &s = *reinterpret_cast<ScanSmem *>(smem);
+    unsigned long long w0, w1;
+    scan_slice(d, w0, w1);
+    // the first tile's loads go out before the sums over the CTA totals
+    uint32_t w[SCAN_PT];
+#pragma unroll
+    for (unsigned k = 0; k < SCAN_PT; ++k) {
+        const unsigned long long i = w0 + threadIdx.x + (unsigned long long)k * BLOCK;
+        w[k] = i < w1 ? __ldg(d.words + i) : 0u;
+    }
+    unsigned long long below = 0, all = 0;   // EE << 32 | EP
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += BLOCK) {
+        const unsigned long long v = ((unsigned long long)ldcg(d.chunk_ee + i) << 32) | ldcg(d.chunk_ep + i);
+        all += v;
+        below += i < blockIdx.x ? v : 0ull;
+    }
+    all = block_sum(all);
+    below = block_sum(below);
+    const unsigned n_ee = (unsigned)(all >> 32), n_ep = (unsigned)all;
+    const bool fits = n_ee <= d.max_events && n_ep <= d.max_roads;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *c = d.ctrl;
+        c->n_events = n_ee;
+        c->n_ep = n_ep;
+        unsigned tail = 0;
+        if (d.n_words > 0 && !(__ldg(d.words + d.n_words - 1) >> 31)) {
+            tail = 1;
+            report(d, d.n_words, RANK_TRUNC);
+        }
+        c->has_tail = tail;
+        if (!fits)
+            raise_flag(d, FLAG_CAPACITY);
+        if (n_ee == 0)
+            c->n_roads = 0;
+    }
+    if (!fits)
+        return false;
+    unsigned ev = (unsigned)(below >> 32), rd = (unsigned)below;
+    for (unsigned long long base = w0; base < w1; base += SCAN_TILE) {
+        if (base != w0) {
+#pragma unroll
+            for (unsigned k = 0; k < SCAN_PT; ++k) {
+                const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+                w[k] = i < w1 ? __ldg(d.words + i) : 0u;
+            }
+        }
+#pragma unroll
+        for (unsigned k = 0; k < SCAN_PT; ++k)
+            s.w[scan_pad(threadIdx.x + k * BLOCK)] = w[k];
+        __syncthreads();
+        // thread t: words 32t .. 32t + 31 of the tile (zero past the slice)
+        const unsigned t0 = threadIdx.x * SCAN_PT;
+        unsigned ee = 0, ep = 0;
+#pragma unroll
+        for (unsigned k = 0; k < SCAN_PT; ++k) {
+            const uint32_t x = s.w[scan_pad(t0 + k)];
+            ee += x >> 31;
+            ep += (x >> 30) & 1u;
+        }
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan(((unsigned long long)ee << 32) | ep, &tot);
+        unsigned my_ev = ev + (unsigned)(ex >> 32), my_rd = rd + (unsigned)ex;
+#pragma unroll
+        for (unsigned k = 0; k < SCAN_PT; ++k) {
+            const uint32_t x = s.w[scan_pad(t0 + k)];
+            my_rd += (x >> 30) & 1u;
+            if (x >> 31) {
+                if (my_ev < d.max_events) {
+                    d.ev_word_end[my_ev] = (uint32_t)(base + t0 + k);
+                    d.ev_road_end[my_ev] = my_rd;
+                }
+                if (my_ev + 1 == n_ee)
+                    d.ctrl->n_roads = my_rd;
+                ++my_ev;
+            }
+        }
+        ev += (unsigned)(tot >> 32);
+        rd += (unsigned)tot;
+        __syncthreads();   // the tile buffer is refilled next
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // P2: one event per CTA
 // ---------------------------------------------------------------------------
 
@@ -1850,18 +1994,12 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     const unsigned nb = gridDim.x;
     stamp(d, 0);
 
-    for (unsigned c = grab(d, Q_P0); c < d.n_chunks_w; c = grab(d, Q_P0))
-        p0_item(d, c);
-    if (last_block(&d.ctrl->done[0], nb))
-        p0_finish(d);
+    scan_count(d);
     if (!grid_sync(d))
         return;
     stamp(d, 1);
-    if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
+    if (!scan_scatter(d, smem))
         return;
-
-    for (unsigned c = grab(d, Q_P1); c < d.n_chunks_w; c = grab(d, Q_P1))
-        p1_item(d, c);
     if (!grid_sync(d))
         return;
     stamp(d, 2);
@@ -2111,8 +2249,9 @@ static size_t p3_smem()
 
 size_t persistent_smem_bytes()
 {
-    size_t a = p2_smem(), b = p3_smem();
-    return a > b ? a : b;
+    size_t a = p2_smem(), b = p3_smem(), c = sizeof(ScanSmem);
+    a = a > b ? a : b;
+    return a > c ? a : c;
 }
 
 static int plain_grid()
@@ -2201,6 +2340,8 @@ cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, i
     int grid = sms * bps;
     if (max_ctas > 0 && max_ctas < grid)
         grid = max_ctas;
+    if (grid > MAX_GRID)
+        grid = MAX_GRID;
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(BLOCK);
     cfg.dynamicSmemBytes = persistent_smem_bytes();

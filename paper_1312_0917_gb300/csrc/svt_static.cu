@@ -27,7 +27,8 @@ constexpr unsigned long long S_WORDS = 1ull << 17;
 constexpr unsigned S_EVENTS = 1u << 10;
 constexpr unsigned S_ROADS = 1u << 13;
 constexpr unsigned S_HASH = 1u << 15;
-constexpr unsigned S_CHUNKS_W = (unsigned)((S_WORDS + CHUNK_WORDS - 1) / CHUNK_WORDS);
+constexpr unsigned S_CHUNKS_W0 = (unsigned)((S_WORDS + CHUNK_WORDS - 1) / CHUNK_WORDS);
+constexpr unsigned S_CHUNKS_W = S_CHUNKS_W0 > (unsigned)MAX_GRID ? S_CHUNKS_W0 : (unsigned)MAX_GRID;
 constexpr unsigned S_CHUNKS_R = (S_ROADS + ROAD_CHUNK - 1) / ROAD_CHUNK;
 
 constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
