@@ -87,7 +87,7 @@ typedef struct {
 
 /* Capacity of a context (0 in a field = its default). */
 typedef struct {
-    uint64_t max_words;      /* words per batch            (default 1 << 24) */
+    uint64_t max_words;      /* words per batch            (default 1 << 24, below 1 << 31) */
     uint32_t max_events;     /* events per batch           (default 1 << 16) */
     uint32_t max_roads;      /* roads per batch            (default 1 << 20) */
     uint64_t max_tracks;     /* surviving tracks per batch (default 1 << 22) */
@@ -258,7 +258,7 @@ typedef struct {
     uint32_t ctas_per_sm;      /* CTAs per SM of each request's persistent kernel (0 = 1) */
     uint32_t max_ctas;         /* grid cap of each request's kernel (0 = SMs x ctas_per_sm) */
     int32_t mode;              /* SVT_PERSISTENT or SVT_PLAIN (0 is SVT_PLAIN) */
-    uint64_t max_words;        /* words per request (0 = 1 << 21) */
+    uint64_t max_words;        /* words per request (0 = 1 << 21, below 1 << 31) */
     uint32_t max_events;       /* events per request (0 = 4096) */
     uint32_t max_roads;        /* roads per request (0 = 1 << 17) */
     uint64_t max_tracks;       /* tracks per request (0 = 1 << 20) */

@@ -165,7 +165,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     if (!L.max_tracks) L.max_tracks = 1ull << 22;
     if (!L.hash_slots) L.hash_slots = 1u << 22;
     if (!L.max_combinations) L.max_combinations = 1ull << 26;
-    if ((L.hash_slots & (L.hash_slots - 1)) || L.max_words >= (1ull << 32) ||
+    if ((L.hash_slots & (L.hash_slots - 1)) || L.max_words >= (1ull << 31) ||
         L.max_tracks >= (1ull << 32)) {
         delete c;
         return SVT_E_INVAL;
@@ -189,6 +189,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
+        !dalloc(c, &d.cand_list, L.max_roads) &&
         !dalloc(c, &d.surv_pool, (size_t)L.max_roads * SURV_SLOTS) &&
         !dalloc(c, &d.surv_cnt, L.max_roads) &&
         !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&

@@ -61,6 +61,13 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // loads of data written earlier in the same launch by other CTAs: L2 only
 template <class T>
 __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
@@ -233,17 +240,21 @@ __device__ bool grid_sync(const Dev &d)
         unsigned target = (old / nb + 1u) * nb;
         unsigned long long t0 = globaltimer_ns();
         int ok = 1;
-        while ((int)(ld_acquire(&d.ctrl->bar) - target) < 0) {
-            if (ld_acquire(&d.ctrl->flags) & FLAG_TIMEOUT) {
-                ok = 0;
-                break;
+        // relaxed polls of the counter (the fence below orders what follows);
+        // the timeout flag and the clock are looked at every 16th poll
+        for (unsigned it = 1; (int)(ld_relaxed(&d.ctrl->bar) - target) < 0; ++it) {
+            if ((it & 15u) == 0) {
+                if (ld_relaxed(&d.ctrl->flags) & FLAG_TIMEOUT) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > d.wait_ns) {
+                    raise_flag(d, FLAG_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
             }
-            if (globaltimer_ns() - t0 > d.wait_ns) {
-                raise_flag(d, FLAG_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(100);
+            __nanosleep(32);
         }
         __threadfence();
         if (ld_acquire(&d.ctrl->flags) & FLAG_TIMEOUT)
@@ -379,30 +390,41 @@ __device__ __forceinline__ void scan_slice(const Dev &d, unsigned long long &w0,
     w1 = min(w0 + per, d.n_words);
 }
 
+// One tile of a slice into registers, word threadIdx.x + k * BLOCK of the
+// tile in w[k] (0 past the slice: neither EE nor EP).  The loads take a
+// clamped index, so that all of them issue before the first value is used.
+__device__ __forceinline__ void scan_load(const uint32_t *slice, unsigned n, unsigned off, uint32_t (&w)[SCAN_PT])
+{
+#pragma unroll
+    for (unsigned k = 0; k < SCAN_PT; ++k) {
+        const unsigned i = off + threadIdx.x + k * BLOCK;
+        const uint32_t x = __ldg(slice + min(i, n - 1u));
+        w[k] = i < n ? x : 0u;
+    }
+}
+
 __device__ void scan_count(const Dev &d)
 {
     unsigned long long w0, w1;
     scan_slice(d, w0, w1);
+    const unsigned n = (unsigned)(w1 - w0);   // a slice holds < 2^32 words
+    const uint32_t *slice = d.words + w0;
     unsigned ee = 0, ep = 0;
-    unsigned long long bad = ~0ull;
-    for (unsigned long long base = w0; base < w1; base += SCAN_TILE) {
-        uint32_t w[SCAN_PT];   // all loads issued before the first is used
+    unsigned bad = ~0u;
+    for (unsigned off = 0; off < n; off += SCAN_TILE) {
+        uint32_t w[SCAN_PT];
+        scan_load(slice, n, off, w);
 #pragma unroll
         for (unsigned k = 0; k < SCAN_PT; ++k) {
-            const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
-            w[k] = i < w1 ? __ldg(d.words + i) : 0u;
-        }
-#pragma unroll
-        for (unsigned k = 0; k < SCAN_PT; ++k) {
-            const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
+            const unsigned i = off + threadIdx.x + k * BLOCK;
             ee += w[k] >> 31;
             ep += (w[k] >> 30) & 1u;
-            if (i < w1 && !word_ok(w[k]) && bad == ~0ull)
+            if (i < n && !word_ok(w[k]) && bad == ~0u)
                 bad = i;
         }
     }
-    if (bad != ~0ull)
-        report(d, bad, RANK_BAD);
+    if (bad != ~0u)
+        report(d, w0 + bad, RANK_BAD);
     // EE count in the high half, EP count in the low half (each < 2^32)
     const unsigned long long tot = block_sum(((unsigned long long)ee << 32) | ep);
     if (threadIdx.x == 0) {
@@ -418,13 +440,12 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
     ScanSmem &s = *reinterpret_cast<ScanSmem *>(smem);
     unsigned long long w0, w1;
     scan_slice(d, w0, w1);
+    const unsigned n = (unsigned)(w1 - w0);
+    const uint32_t *slice = d.words + w0;
     // the first tile's loads go out before the sums over the CTA totals
     uint32_t w[SCAN_PT];
-#pragma unroll
-    for (unsigned k = 0; k < SCAN_PT; ++k) {
-        const unsigned long long i = w0 + threadIdx.x + (unsigned long long)k * BLOCK;
-        w[k] = i < w1 ? __ldg(d.words + i) : 0u;
-    }
+    if (n)
+        scan_load(slice, n, 0, w);
     unsigned long long below = 0, all = 0;   // EE << 32 | EP
     for (unsigned i = threadIdx.x; i < gridDim.x; i += BLOCK) {
         const unsigned long long v = ((unsigned long long)ldcg(d.chunk_ee + i) << 32) | ldcg(d.chunk_ep + i);
@@ -453,14 +474,9 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
     if (!fits)
         return false;
     unsigned ev = (unsigned)(below >> 32), rd = (unsigned)below;
-    for (unsigned long long base = w0; base < w1; base += SCAN_TILE) {
-        if (base != w0) {
-#pragma unroll
-            for (unsigned k = 0; k < SCAN_PT; ++k) {
-                const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
-                w[k] = i < w1 ? __ldg(d.words + i) : 0u;
-            }
-        }
+    for (unsigned off = 0; off < n; off += SCAN_TILE) {
+        if (off)
+            scan_load(slice, n, off, w);
 #pragma unroll
         for (unsigned k = 0; k < SCAN_PT; ++k)
             s.w[scan_pad(threadIdx.x + k * BLOCK)] = w[k];
@@ -483,7 +499,7 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
             my_rd += (x >> 30) & 1u;
             if (x >> 31) {
                 if (my_ev < d.max_events) {
-                    d.ev_word_end[my_ev] = (uint32_t)(base + t0 + k);
+                    d.ev_word_end[my_ev] = (uint32_t)(w0 + off + t0 + k);
                     d.ev_road_end[my_ev] = my_rd;
                 }
                 if (my_ev + 1 == n_ee)
@@ -764,6 +780,11 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
                     if (i < d.max_roads)
                         d.big_list[i] = g;
                 }
+                if (N > 0 && cand) {   // checked against the other roads' groups after the fit
+                    unsigned i = atomicAdd(&d.ctrl->n_cand, 1u);
+                    if (i < d.max_roads)
+                        d.cand_list[i] = g;
+                }
                 n_comb += N;
             }
         }
@@ -779,6 +800,10 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
 __device__ void p2_phase(const Dev &d, unsigned char *smem)
 {
     const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
+    // survivor totals of the road chunks start at zero (the fit adds to them)
+    const unsigned n_chunks = min((ldcg(&d.ctrl->n_roads) + ROAD_CHUNK - 1) / ROAD_CHUNK, d.max_chunks_r);
+    for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_chunks; i += gridDim.x * BLOCK)
+        d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
     for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
         p2_event(d, e, smem, n_comb);
@@ -1140,8 +1165,11 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     unsigned long long *slots = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = tid; i < n_surv; i += G::SIZE)
         slots[i] = sm.S[i];
-    if (tid == 0)
+    if (tid == 0) {
         d.surv_cnt[g] = (uint8_t)n_surv;
+        if (n_surv)
+            atomicAdd(&d.rchunk_sum[g / ROAD_CHUNK], n_surv);
+    }
 
     // cross-road candidates: publish the minimum of every group whose three
     // coordinates all appear in another road of the event
@@ -1716,8 +1744,22 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             }
             __syncwarp();
         }
-        if ((sub >> lane) & 1u)
-            d.surv_cnt[g0 + lane] = (uint8_t)min(F.cnt[lane], (unsigned)SURV_SLOTS);
+        {
+            // survivor counts of the sub-run's roads, and their sums per road
+            // chunk (a run spans at most two chunks)
+            const bool in_sub = (sub >> lane) & 1u;
+            const unsigned v = in_sub ? min(F.cnt[lane], (unsigned)SURV_SLOTS) : 0u;
+            if (in_sub)
+                d.surv_cnt[g0 + lane] = (uint8_t)v;
+            const unsigned ch0 = g0 / ROAD_CHUNK;
+            const bool second = (g0 + lane) / ROAD_CHUNK != ch0;
+            const unsigned s0 = __reduce_add_sync(FULL_MASK, second ? 0u : v);
+            const unsigned s1 = __reduce_add_sync(FULL_MASK, second ? v : 0u);
+            if (lane == 0 && s0)
+                atomicAdd(&d.rchunk_sum[ch0], s0);
+            if (lane == 0 && s1)
+                atomicAdd(&d.rchunk_sum[ch0 + 1], s1);
+        }
         // cross-road candidates of the sub-run publish their group minima,
         // which read whole keys from the pair tables.  Without a tie the low
         // words were not taken: each table's minimum high word belongs to
@@ -1893,9 +1935,75 @@ __device__ void p4_finish(const Dev &d, unsigned n_chunks)
     }
 }
 
-// Output of one chunk of ROAD_CHUNK roads: a block scan of the survivor
-// counts gives each road's first output slot; then each thread takes
-// survivors (not roads), so roads with many survivors are spread out.
+// Track of survivor idx of road g, written to output slot pos.
+template <bool PLAIN>
+__device__ void emit_track(const Dev &d, unsigned g, unsigned idx, unsigned long long pos)
+{
+    const RoadRec rec = ldcg(d.roads + g);
+    unsigned n[N_LAYERS];
+    for (unsigned l = 0; l < N_LAYERS; ++l)
+        n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+    const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
+    const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+    const uint16_t *co = d.coords + (size_t)g * 40;
+    const unsigned long long key = ldcg(d.surv_pool + (size_t)g * SURV_SLOTS + idx);
+    const unsigned comb = (unsigned)(key & 0x7FFFu);
+    svt_track t;
+    t.event = rec.event;
+    t.road = (uint16_t)(rec.pk >> 24);
+    t.comb = (uint16_t)comb;
+    t.pad = 0;
+    t.chi2 = (long long)(key >> 23);
+    int x[6];
+    unsigned long long hits = 0;
+    unsigned j = 0, rest = comb;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
+        const unsigned q = divm(rest, c_magic[n[l]]);
+        const unsigned dl = rest - q * n[l];
+        rest = q;
+        const unsigned v = ldcg(co + l * 8 + dl);
+        hits |= (unsigned long long)v << (12 * l);
+        if (l != excl)
+            x[j++] = (int)v;
+    }
+    x[4] = rec.curv;
+    x[5] = rec.phi;
+    t.hits = hits;
+    if (PLAIN) {
+        const unsigned long long ci = ldcg(d.comb_off + g) + comb;
+        t.p[0] = ldcg(d.fit_p + 3 * ci);
+        t.p[1] = ldcg(d.fit_p + 3 * ci + 1);
+        t.p[2] = ldcg(d.fit_p + 3 * ci + 2);
+    } else {
+        for (unsigned k = 0; k < 3; ++k) {
+            int acc = 0;
+            for (unsigned jj = 0; jj < 6; ++jj)
+                acc += (int)__ldg(&cs->F[k][jj]) * x[jj];
+            t.p[k] = (acc >> 12) + __ldg(&cs->q[k]);
+        }
+    }
+    if (pos < d.max_tracks)
+        d.tracks[pos] = t;
+}
+
+// road of survivor i of a chunk: the last r with s_first[r] <= i (a road
+// with survivors; s_first holds the chunk's exclusive scan of counts)
+__device__ __forceinline__ unsigned chunk_road(const unsigned *s_first, unsigned i)
+{
+    unsigned lo = 0, hi = ROAD_CHUNK;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (s_first[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Output of one chunk of ROAD_CHUNK roads (plain kernels): a block scan of
+// the survivor counts gives each road's first output slot; then each thread
+// takes survivors (not roads), so roads with many survivors are spread out.
 template <bool PLAIN>
 __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_first)
 {
@@ -1911,64 +2019,99 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_
     const unsigned long long base = ldcg(d.rchunk_off + c);
     __syncthreads();
     for (unsigned i = threadIdx.x; i < (unsigned)total; i += BLOCK) {
-        // road of survivor i: the last r with s_first[r] <= i (and a survivor)
-        unsigned lo = 0, hi = ROAD_CHUNK;
-        while (hi - lo > 1) {
-            const unsigned mid = (lo + hi) >> 1;
-            if (s_first[mid] <= i)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const unsigned g = c * ROAD_CHUNK + lo, idx = i - s_first[lo];
-        const unsigned long long pos = base + i;
-        const RoadRec rec = ldcg(d.roads + g);
-        unsigned n[N_LAYERS];
-        for (unsigned l = 0; l < N_LAYERS; ++l)
-            n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-        const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
-        const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
-        const uint16_t *co = d.coords + (size_t)g * 40;
-        const unsigned long long key = ldcg(d.surv_pool + (size_t)g * SURV_SLOTS + idx);
-        const unsigned comb = (unsigned)(key & 0x7FFFu);
-        svt_track t;
-        t.event = rec.event;
-        t.road = (uint16_t)(rec.pk >> 24);
-        t.comb = (uint16_t)comb;
-        t.pad = 0;
-        t.chi2 = (long long)(key >> 23);
-        int x[6];
-        unsigned long long hits = 0;
-        unsigned j = 0, rest = comb;
-        for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
-            const unsigned q = divm(rest, c_magic[n[l]]);
-            const unsigned dl = rest - q * n[l];
-            rest = q;
-            const unsigned v = ldcg(co + l * 8 + dl);
-            hits |= (unsigned long long)v << (12 * l);
-            if (l != excl)
-                x[j++] = (int)v;
-        }
-        x[4] = rec.curv;
-        x[5] = rec.phi;
-        t.hits = hits;
-        if (PLAIN) {
-            const unsigned long long ci = ldcg(d.comb_off + g) + comb;
-            t.p[0] = ldcg(d.fit_p + 3 * ci);
-            t.p[1] = ldcg(d.fit_p + 3 * ci + 1);
-            t.p[2] = ldcg(d.fit_p + 3 * ci + 2);
-        } else {
-            for (unsigned k = 0; k < 3; ++k) {
-                int acc = 0;
-                for (unsigned jj = 0; jj < 6; ++jj)
-                    acc += (int)__ldg(&cs->F[k][jj]) * x[jj];
-                t.p[k] = (acc >> 12) + __ldg(&cs->q[k]);
-            }
-        }
-        if (pos < d.max_tracks)
-            d.tracks[pos] = t;
+        const unsigned r = chunk_road(s_first, i);
+        emit_track<PLAIN>(d, c * ROAD_CHUNK + r, i - s_first[r], base + i);
     }
     __syncthreads();   // s_first is reused by the next chunk
+}
+
+// P4 of the persistent kernel: the cross-road hit-warrior over the listed
+// candidate roads only (the others keep their survivors).  A road that
+// loses survivors takes them off its chunk's total.
+__device__ void p4_cand_phase(const Dev &d)
+{
+    const unsigned n_cand = min(ldcg(&d.ctrl->n_cand), d.max_roads);
+    const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
+    // candidate i goes to CTA i % grid: the few candidates are spread out
+    for (unsigned i = threadIdx.x * gridDim.x + blockIdx.x; i < n_cand; i += gridDim.x * BLOCK) {
+        const unsigned g = ldcg(d.cand_list + i);
+        if (g >= n_roads)
+            continue;   // a road of the truncated tail: not fitted
+        const unsigned cnt = ldcg(d.surv_cnt + g);
+        if (!cnt)
+            continue;
+        const unsigned kept = cross_check(d, g, cnt);
+        if (kept != cnt) {
+            d.surv_cnt[g] = (uint8_t)kept;
+            atomicSub(&d.rchunk_sum[g / ROAD_CHUNK], cnt - kept);
+        }
+    }
+}
+
+// P5 of the persistent kernel: the tracks in road order, split evenly over
+// the CTAs.  Every CTA scans the chunk totals itself (no CTA scans for the
+// others), takes survivors [S b / grid, S (b + 1) / grid) of the S in all,
+// and scans the survivor counts of the chunks that hold them.
+__device__ void p5_phase(const Dev &d, unsigned char *smem)
+{
+    unsigned *s_first = reinterpret_cast<unsigned *>(smem);   // ROAD_CHUNK + 1 words
+    unsigned long long *s_at = reinterpret_cast<unsigned long long *>(smem + 2048);   // chunk, its first survivor
+    static_assert(sizeof(unsigned) * (ROAD_CHUNK + 1) <= 2048, "chunk scan below the start");
+    const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
+    const unsigned n_chunks = min((n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK, d.max_chunks_r);
+    // each thread sums a contiguous range of chunk totals
+    const unsigned per = (n_chunks + BLOCK - 1) / BLOCK;
+    const unsigned c0 = min(threadIdx.x * per, n_chunks), c1 = min(c0 + per, n_chunks);
+    unsigned long long mine = 0;
+    for (unsigned c = c0; c < c1; ++c)
+        mine += ldcg(d.rchunk_sum + c);
+    unsigned long long S;
+    const unsigned long long ex = block_excl_scan(mine, &S);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.ctrl->n_out = S;
+        if (S > d.max_tracks)
+            raise_flag(d, FLAG_CAPACITY);
+    }
+    if (S > d.max_tracks)
+        return;
+    const unsigned long long lo = S * blockIdx.x / gridDim.x, hi = S * (blockIdx.x + 1) / gridDim.x;
+    if (lo == hi)
+        return;
+    // the chunk holding survivor lo lies in one thread's range
+    if (ex <= lo && lo < ex + mine) {
+        unsigned c = c0;
+        unsigned long long pre = ex;
+        for (unsigned long long t = ldcg(d.rchunk_sum + c); pre + t <= lo; t = ldcg(d.rchunk_sum + c)) {
+            pre += t;
+            ++c;
+        }
+        s_at[0] = c;
+        s_at[1] = pre;
+    }
+    __syncthreads();
+    unsigned c = (unsigned)s_at[0];
+    unsigned long long pre = s_at[1];
+    while (pre < hi && c < n_chunks) {
+        const unsigned g_me = c * ROAD_CHUNK + threadIdx.x;
+        const unsigned cnt_me = g_me < n_roads ? ldcg(d.surv_cnt + g_me) : 0u;
+        unsigned long long tot;
+        const unsigned ex2 = (unsigned)block_excl_scan(cnt_me, &tot);
+        s_first[threadIdx.x] = ex2;
+        if (threadIdx.x == 0) {
+            s_first[ROAD_CHUNK] = (unsigned)tot;
+            if (tot != ldcg(d.rchunk_sum + c))
+                raise_flag(d, FLAG_INTERNAL);   // the counts and the chunk total disagree
+        }
+        __syncthreads();
+        const unsigned long long a = lo > pre ? lo : pre, b = hi < pre + tot ? hi : pre + tot;
+        for (unsigned long long i = a + threadIdx.x; i < b; i += BLOCK) {
+            const unsigned k = (unsigned)(i - pre), r = chunk_road(s_first, k);
+            emit_track<false>(d, c * ROAD_CHUNK + r, k - s_first[r], i);
+        }
+        pre += tot;
+        ++c;
+        __syncthreads();   // s_first is refilled next
+    }
 }
 
 __device__ void clear_hash(const Dev &d, unsigned i)
@@ -2016,18 +2159,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         return;
     stamp(d, 4);
 
-    const unsigned n_roads = ldcg(&d.ctrl->n_roads);
-    const unsigned n_chunks = (n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
-    for (unsigned c = grab(d, Q_P4); c < n_chunks; c = grab(d, Q_P4))
-        p4_item(d, c, n_roads);
-    if (last_block(&d.ctrl->done[1], nb))
-        p4_finish(d, n_chunks);
+    p4_cand_phase(d);
     if (!grid_sync(d))
         return;
     stamp(d, 5);
-    if (!(ldcg(&d.ctrl->flags) & FLAG_CAPACITY))
-        for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
-            p5_item<false>(d, c, n_roads, reinterpret_cast<unsigned *>(smem));
+    p5_phase(d, smem);
     // every lookup is done (barrier above): leave the group table empty
     const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += nb * BLOCK)

@@ -203,7 +203,7 @@ int svt_server_create(svt_server **out, int device, const svt_server_config *con
     if (!cfg.max_tracks) cfg.max_tracks = 1ull << 20;
     if (!cfg.hash_slots) cfg.hash_slots = 1u << 20;
     if ((cfg.mode != SVT_PERSISTENT && cfg.mode != SVT_PLAIN) || cfg.n_slots > 64 ||
-        cfg.max_words >= (1ull << 32) || cfg.max_tracks >= (1ull << 32) ||
+        cfg.max_words >= (1ull << 31) || cfg.max_tracks >= (1ull << 32) ||
         (cfg.hash_slots & (cfg.hash_slots - 1)))
         return SVT_E_INVAL;
     if (cudaSetDevice(device) != cudaSuccess)
