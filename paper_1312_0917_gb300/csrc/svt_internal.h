@@ -86,7 +86,8 @@ struct Dev {
     unsigned long long *xmask;                                    // [max_roads]
     uint32_t *big_list;                                           // [max_roads]
     uint32_t *cand_list;                                          // [max_roads]
-    unsigned long long *surv_pool;                                // [max_roads][SURV_SLOTS] road survivors
+    unsigned long long *surv_pool;                                // [SURV_SLOTS][max_roads] road survivors
+                                                                  // (slot-major: see surv_at)
     uint8_t *surv_cnt;                                            // [max_roads]
     uint32_t *rchunk_sum, *rchunk_off;                            // [max_chunks_r]
     unsigned long long *cchunk_sum, *cchunk_off;                  // [max_chunks_r]

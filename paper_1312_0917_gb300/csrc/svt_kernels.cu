@@ -88,6 +88,14 @@ __device__ __forceinline__ void report(const Dev &d, unsigned long long pos, uns
 
 __device__ __forceinline__ void raise_flag(const Dev &d, unsigned f) { atomicOr(&d.ctrl->flags, f); }
 
+// Survivor slot s of road g.  Slots are slot-major, so the first survivors
+// of consecutive roads are adjacent (the output stage reads them in road
+// order).
+__device__ __forceinline__ size_t surv_at(const Dev &d, unsigned g, unsigned s)
+{
+    return (size_t)s * d.max_roads + g;
+}
+
 __device__ __forceinline__ bool word_ok(uint32_t w)
 {
     uint32_t type = (w >> 27) & 7u, pl = w & 0x07FFFFFFu;
@@ -884,6 +892,12 @@ __device__ __constant__ unsigned char c_pair[6][4] = {
 __device__ __constant__ unsigned char c_triple[10][3] = {
     {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
     {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
+// the same triples as constants the compiler folds in unrolled loops: layer
+// k of triple t
+__device__ __forceinline__ unsigned triple_l(unsigned t, unsigned k)
+{
+    return (unsigned)(((k == 0 ? 0x2111000000ull : k == 1 ? 0x3322322111ull : 0x4443443432ull) >> (4 * t)) & 15u);
+}
 
 __device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRec &rec, RoadInfo &r)
 {
@@ -972,14 +986,17 @@ __device__ void hash_min(const Dev &d, unsigned long long gk, unsigned long long
     raise_flag(d, FLAG_CAPACITY);
 }
 
+// lookup after the table is complete (no writer in flight): a slot's key and
+// value are read by one 16-byte load
 __device__ unsigned long long hash_get(const Dev &d, unsigned long long gk)
 {
+    static_assert(sizeof(HashSlot) == 16, "one 16-byte load per slot");
     unsigned h = hash_slot(gk, d.hash_mask);
     for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
-        unsigned long long k = ldcg(&d.hash[h].key);
-        if (k == gk)
-            return ~ldcg(&d.hash[h].val_inv);
-        if (k == 0ull)
+        const ulonglong2 sl = __ldcg(reinterpret_cast<const ulonglong2 *>(d.hash + h));
+        if (sl.x == gk)
+            return ~sl.y;
+        if (sl.x == 0ull)
             return NO_KEY;
         h = (h + 1) & d.hash_mask;
     }
@@ -1162,9 +1179,8 @@ __device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigne
     n_surv = min(n_surv, (unsigned)SURV_SLOTS);
     // the road's own survivor slots
     grp.sync();
-    unsigned long long *slots = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = tid; i < n_surv; i += G::SIZE)
-        slots[i] = sm.S[i];
+        d.surv_pool[surv_at(d, g, i)] = sm.S[i];
     if (tid == 0) {
         d.surv_cnt[g] = (uint8_t)n_surv;
         if (n_surv)
@@ -1736,7 +1752,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             __syncwarp();
             if (surv) {
                 if (pos < SURV_SLOTS)
-                    d.surv_pool[(size_t)F.rd[ri].g * SURV_SLOTS + pos] = key;
+                    d.surv_pool[surv_at(d, F.rd[ri].g, pos)] = key;
                 else
                     raise_flag(d, FLAG_INTERNAL);
                 if ((same >> lane) == 1u)   // the last survivor of its road in this batch
@@ -1876,18 +1892,19 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
 
 __device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
 {
-    RoadRec rec = ldcg(d.roads + g);
+    const RoadRec rec = ldcg(d.roads + g);
+    const unsigned long long xm = ldcg(d.xmask + g);
     unsigned n[N_LAYERS];
+#pragma unroll
     for (unsigned l = 0; l < N_LAYERS; ++l)
         n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-    unsigned long long xm = ldcg(d.xmask + g);
     const uint16_t *co = d.coords + (size_t)g * 40;
     unsigned kept = 0;
-    unsigned long long *keys = d.surv_pool + (size_t)g * SURV_SLOTS;
     for (unsigned i = 0; i < cnt; ++i) {
-        unsigned long long key = ldcg(keys + i);
+        unsigned long long key = ldcg(d.surv_pool + surv_at(d, g, i));
         unsigned t = (unsigned)(key & 0x7FFFu);
         unsigned dl[N_LAYERS], v[N_LAYERS];
+#pragma unroll
         for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
             const unsigned q = divm(t, c_magic[n[l]]);
             dl[l] = t - q * n[l];
@@ -1895,15 +1912,18 @@ __device__ unsigned cross_check(const Dev &d, unsigned g, unsigned cnt)
             v[l] = ldcg(co + l * 8 + dl[l]);
         }
         bool dropped = false;
-        for (unsigned t = 0; t < 10 && !dropped; ++t) {
-            unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
+#pragma unroll
+        for (unsigned t = 0; t < 10; ++t) {
+            if (dropped)
+                break;
+            const unsigned l0 = triple_l(t, 0), l1 = triple_l(t, 1), l2 = triple_l(t, 2);
             bool flagged = ((xm >> (8 * l0 + dl[l0])) & 1ull) && ((xm >> (8 * l1 + dl[l1])) & 1ull) &&
                            ((xm >> (8 * l2 + dl[l2])) & 1ull);
             if (flagged && hash_get(d, group_key(rec.event, t, v[l0], v[l1], v[l2])) < key)
                 dropped = true;
         }
         if (!dropped)
-            keys[kept++] = key;
+            d.surv_pool[surv_at(d, g, kept++)] = key;
     }
     return kept;
 }
@@ -1935,39 +1955,53 @@ __device__ void p4_finish(const Dev &d, unsigned n_chunks)
     }
 }
 
-// Track of survivor idx of road g, written to output slot pos.
-template <bool PLAIN>
-__device__ void emit_track(const Dev &d, unsigned g, unsigned idx, unsigned long long pos)
+// hit d (0..7) of a layer's eight 16-bit coordinates held in one uint4
+__device__ __forceinline__ unsigned coord_of(const uint4 &r, unsigned d)
 {
-    const RoadRec rec = ldcg(d.roads + g);
-    unsigned n[N_LAYERS];
-    for (unsigned l = 0; l < N_LAYERS; ++l)
-        n[l] = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
-    const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
+    const unsigned w = d < 4 ? (d < 2 ? r.x : r.y) : (d < 6 ? r.z : r.w);
+    return (w >> (16 * (d & 1u))) & 0xFFFFu;
+}
+
+// The track of key `key` of road g (record rec, coordinate row rw: the
+// road's 40 coordinates as five 16-byte words), written to output slot pos.
+// The loops are unrolled (registers, no local arrays).
+template <bool PLAIN>
+__device__ void build_track(const Dev &d, unsigned g, const RoadRec &rec, const uint4 (&rw)[N_LAYERS],
+                            unsigned long long key, unsigned long long pos)
+{
     const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
-    const uint16_t *co = d.coords + (size_t)g * 40;
-    const unsigned long long key = ldcg(d.surv_pool + (size_t)g * SURV_SLOTS + idx);
+    int F[3][6], q[3];
+    if (!PLAIN) {
+#pragma unroll
+        for (unsigned k = 0; k < 3; ++k) {
+#pragma unroll
+            for (unsigned jj = 0; jj < 6; ++jj)
+                F[k][jj] = __ldg(&cs->F[k][jj]);
+            q[k] = __ldg(&cs->q[k]);
+        }
+    }
+    const unsigned excl = min((rec.pk >> 20) & 7u, 4u);
     const unsigned comb = (unsigned)(key & 0x7FFFu);
+    unsigned v[N_LAYERS];
+    unsigned rest = comb;
+#pragma unroll
+    for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
+        const unsigned n = max(min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS), 1u);
+        const unsigned qq = divm(rest, c_magic[n]);
+        const unsigned dl = rest - qq * n;
+        rest = qq;
+        v[l] = coord_of(rw[l], dl);
+    }
     svt_track t;
     t.event = rec.event;
     t.road = (uint16_t)(rec.pk >> 24);
     t.comb = (uint16_t)comb;
     t.pad = 0;
     t.chi2 = (long long)(key >> 23);
-    int x[6];
     unsigned long long hits = 0;
-    unsigned j = 0, rest = comb;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {   // mixed-radix digits of comb
-        const unsigned q = divm(rest, c_magic[n[l]]);
-        const unsigned dl = rest - q * n[l];
-        rest = q;
-        const unsigned v = ldcg(co + l * 8 + dl);
-        hits |= (unsigned long long)v << (12 * l);
-        if (l != excl)
-            x[j++] = (int)v;
-    }
-    x[4] = rec.curv;
-    x[5] = rec.phi;
+#pragma unroll
+    for (unsigned l = 0; l < N_LAYERS; ++l)
+        hits |= (unsigned long long)v[l] << (12 * l);
     t.hits = hits;
     if (PLAIN) {
         const unsigned long long ci = ldcg(d.comb_off + g) + comb;
@@ -1975,15 +2009,38 @@ __device__ void emit_track(const Dev &d, unsigned g, unsigned idx, unsigned long
         t.p[1] = ldcg(d.fit_p + 3 * ci + 1);
         t.p[2] = ldcg(d.fit_p + 3 * ci + 2);
     } else {
+        // the fit's inputs: the four layers other than excl, in order, then
+        // curvature and phi
+        const int x[6] = {(int)(excl == 0 ? v[1] : v[0]), (int)(excl <= 1 ? v[2] : v[1]),
+                          (int)(excl <= 2 ? v[3] : v[2]), (int)(excl <= 3 ? v[4] : v[3]), rec.curv, rec.phi};
+#pragma unroll
         for (unsigned k = 0; k < 3; ++k) {
             int acc = 0;
+#pragma unroll
             for (unsigned jj = 0; jj < 6; ++jj)
-                acc += (int)__ldg(&cs->F[k][jj]) * x[jj];
-            t.p[k] = (acc >> 12) + __ldg(&cs->q[k]);
+                acc += F[k][jj] * x[jj];
+            t.p[k] = (acc >> 12) + q[k];
         }
     }
     if (pos < d.max_tracks)
         d.tracks[pos] = t;
+}
+
+// Track of survivor idx of road g, written to output slot pos: the road's
+// record, the key and the coordinate row go out together (none depends on
+// another).
+template <bool PLAIN>
+__device__ void emit_track(const Dev &d, unsigned g, unsigned idx, unsigned long long pos)
+{
+    static_assert(sizeof(uint16_t) * 40 == N_LAYERS * sizeof(uint4), "a coordinate row is five 16-byte words");
+    const RoadRec rec = ldcg(d.roads + g);
+    const unsigned long long key = ldcg(d.surv_pool + surv_at(d, g, idx));
+    const uint4 *row = reinterpret_cast<const uint4 *>(d.coords + (size_t)g * 40);
+    uint4 rw[N_LAYERS];
+#pragma unroll
+    for (unsigned l = 0; l < N_LAYERS; ++l)
+        rw[l] = ldcg(row + l);
+    build_track<PLAIN>(d, g, rec, rw, key, pos);
 }
 
 // road of survivor i of a chunk: the last r with s_first[r] <= i (a road
@@ -2050,13 +2107,51 @@ __device__ void p4_cand_phase(const Dev &d)
 
 // P5 of the persistent kernel: the tracks in road order, split evenly over
 // the CTAs.  Every CTA scans the chunk totals itself (no CTA scans for the
-// others), takes survivors [S b / grid, S (b + 1) / grid) of the S in all,
-// and scans the survivor counts of the chunks that hold them.
+// others) and takes survivors [S b / grid, S (b + 1) / grid) of the S in all.
+// The survivor counts of the roads that hold them are loaded at once, eight
+// roads per thread (P5_GROUP chunks at a time), and scanned into a table of
+// first survivors, which places each survivor at its road.
+constexpr unsigned P5_PER_THREAD = 8;
+constexpr unsigned P5_ROADS = BLOCK * P5_PER_THREAD;
+constexpr unsigned P5_GROUP = P5_ROADS / ROAD_CHUNK;   // chunks per pass
+static_assert(P5_ROADS % ROAD_CHUNK == 0, "whole chunks per pass");
+
+constexpr unsigned P5_STAGE = 448;   // roads whose records and coordinates are staged at once
+
+struct P5Smem {
+    unsigned first[P5_ROADS + 1];   // first survivor of each road of the pass, from its start
+    unsigned long long at[2];       // the chunk holding survivor lo, and its first survivor
+    RoadRec rec[P5_STAGE];          // staged roads: records
+    uint4 row[P5_STAGE * N_LAYERS]; // and coordinate rows
+};
+
+// the last road r of [lo, hi) with first[r] <= k (the road of survivor k)
+__device__ __forceinline__ unsigned p5_road(const unsigned *first, unsigned lo, unsigned hi, unsigned k)
+{
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (first[mid] <= k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// survivor counts of roads g .. g + 7 (0 from n_roads on), one byte each
+__device__ __forceinline__ unsigned long long load_counts8(const Dev &d, unsigned g, unsigned n_roads)
+{
+    if (g + P5_PER_THREAD <= n_roads)
+        return ldcg(reinterpret_cast<const unsigned long long *>(d.surv_cnt + g));
+    unsigned long long v = 0;
+    for (unsigned k = 0; k < P5_PER_THREAD && g + k < n_roads; ++k)
+        v |= (unsigned long long)ldcg(d.surv_cnt + g + k) << (8 * k);
+    return v;
+}
+
 __device__ void p5_phase(const Dev &d, unsigned char *smem)
 {
-    unsigned *s_first = reinterpret_cast<unsigned *>(smem);   // ROAD_CHUNK + 1 words
-    unsigned long long *s_at = reinterpret_cast<unsigned long long *>(smem + 2048);   // chunk, its first survivor
-    static_assert(sizeof(unsigned) * (ROAD_CHUNK + 1) <= 2048, "chunk scan below the start");
+    P5Smem &s = *reinterpret_cast<P5Smem *>(smem);
     const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
     const unsigned n_chunks = min((n_roads + ROAD_CHUNK - 1) / ROAD_CHUNK, d.max_chunks_r);
     // each thread sums a contiguous range of chunk totals
@@ -2085,32 +2180,66 @@ __device__ void p5_phase(const Dev &d, unsigned char *smem)
             pre += t;
             ++c;
         }
-        s_at[0] = c;
-        s_at[1] = pre;
+        s.at[0] = c;
+        s.at[1] = pre;
     }
     __syncthreads();
-    unsigned c = (unsigned)s_at[0];
-    unsigned long long pre = s_at[1];
+    unsigned c = (unsigned)s.at[0];
+    unsigned long long pre = s.at[1];   // first survivor of chunk c
     while (pre < hi && c < n_chunks) {
-        const unsigned g_me = c * ROAD_CHUNK + threadIdx.x;
-        const unsigned cnt_me = g_me < n_roads ? ldcg(d.surv_cnt + g_me) : 0u;
+        const unsigned g0 = c * ROAD_CHUNK, gt = g0 + threadIdx.x * P5_PER_THREAD;
+        const unsigned long long cnt8 = load_counts8(d, gt, n_roads);
+        unsigned mysum = 0;
+#pragma unroll
+        for (unsigned k = 0; k < P5_PER_THREAD; ++k)
+            mysum += (unsigned)(cnt8 >> (8 * k)) & 0xFFu;
         unsigned long long tot;
-        const unsigned ex2 = (unsigned)block_excl_scan(cnt_me, &tot);
-        s_first[threadIdx.x] = ex2;
+        unsigned run = (unsigned)block_excl_scan(mysum, &tot);
+#pragma unroll
+        for (unsigned k = 0; k < P5_PER_THREAD; ++k) {
+            s.first[threadIdx.x * P5_PER_THREAD + k] = run;
+            run += (unsigned)(cnt8 >> (8 * k)) & 0xFFu;
+        }
         if (threadIdx.x == 0) {
-            s_first[ROAD_CHUNK] = (unsigned)tot;
-            if (tot != ldcg(d.rchunk_sum + c))
-                raise_flag(d, FLAG_INTERNAL);   // the counts and the chunk total disagree
+            s.first[P5_ROADS] = (unsigned)tot;
+            unsigned long long chk = 0;   // the counts and the chunk totals agree
+            for (unsigned k = 0; k < P5_GROUP && c + k < n_chunks; ++k)
+                chk += ldcg(d.rchunk_sum + c + k);
+            if (chk != tot)
+                raise_flag(d, FLAG_INTERNAL);
         }
         __syncthreads();
         const unsigned long long a = lo > pre ? lo : pre, b = hi < pre + tot ? hi : pre + tot;
-        for (unsigned long long i = a + threadIdx.x; i < b; i += BLOCK) {
-            const unsigned k = (unsigned)(i - pre), r = chunk_road(s_first, k);
-            emit_track<false>(d, c * ROAD_CHUNK + r, k - s_first[r], i);
+        if (a < b) {
+            // survivors ka .. kb of the pass lie in roads r_lo .. r_hi; their
+            // records and coordinate rows are staged with coalesced loads,
+            // P5_STAGE roads at a time
+            const unsigned ka = (unsigned)(a - pre), kb = (unsigned)(b - 1 - pre);
+            const unsigned r_lo = p5_road(s.first, 0, P5_ROADS, ka), r_hi = p5_road(s.first, 0, P5_ROADS, kb);
+            for (unsigned rb = r_lo; rb <= r_hi; rb += P5_STAGE) {
+                const unsigned re = min(rb + P5_STAGE, r_hi + 1), nr = re - rb;
+                for (unsigned j = threadIdx.x; j < nr; j += BLOCK)
+                    s.rec[j] = ldcg(d.roads + g0 + rb + j);
+                const uint4 *rows = reinterpret_cast<const uint4 *>(d.coords + (size_t)(g0 + rb) * 40);
+                for (unsigned j = threadIdx.x; j < nr * N_LAYERS; j += BLOCK)
+                    s.row[j] = ldcg(rows + j);
+                __syncthreads();
+                const unsigned k0 = max(ka, s.first[rb]), k1 = min(kb + 1, s.first[re]);
+                for (unsigned k = k0 + threadIdx.x; k < k1; k += BLOCK) {
+                    const unsigned r = p5_road(s.first, rb, re, k), g = g0 + r;
+                    const unsigned long long key = ldcg(d.surv_pool + surv_at(d, g, k - s.first[r]));
+                    uint4 rw[N_LAYERS];
+#pragma unroll
+                    for (unsigned l = 0; l < N_LAYERS; ++l)
+                        rw[l] = s.row[(r - rb) * N_LAYERS + l];
+                    build_track<false>(d, g, s.rec[r - rb], rw, key, pre + k);
+                }
+                __syncthreads();   // the stage is refilled next
+            }
         }
         pre += tot;
-        ++c;
-        __syncthreads();   // s_first is refilled next
+        c += P5_GROUP;
+        __syncthreads();   // the table is refilled next
     }
 }
 
@@ -2383,11 +2512,14 @@ static size_t p3_smem()
     return a > b ? a : b;
 }
 
+static_assert(sizeof(P5Smem) <= WARPS * P3_WARP_BYTES, "the output stage needs no more shared memory than the fit");
+
 size_t persistent_smem_bytes()
 {
-    size_t a = p2_smem(), b = p3_smem(), c = sizeof(ScanSmem);
+    size_t a = p2_smem(), b = p3_smem(), c = sizeof(ScanSmem), e = sizeof(P5Smem);
     a = a > b ? a : b;
-    return a > c ? a : c;
+    a = a > c ? a : c;
+    return a > e ? a : e;
 }
 
 static int plain_grid()
