@@ -61,7 +61,7 @@ struct RoadRec {
     uint32_t pk;
     int16_t curv, phi;
     uint16_t set;
-    uint16_t pad;
+    uint16_t cta;   // 1: fitted by a whole CTA (listed in big_list), not by a warp's run
 };
 
 // Cross-road group table slot: key = (event + 1, triple, three coordinates),

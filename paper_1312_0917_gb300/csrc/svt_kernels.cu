@@ -749,12 +749,15 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         const unsigned k = kb + threadIdx.x / ROAD_THREADS;
         const uint32_t pk = k < nr ? s.pk[k] : 0u;
         unsigned lo = 0, hi = 0;   // flagged hits of layers 0..3 and of layer 4
+        unsigned rep = 0;          // a coordinate repeated within a layer
         for (unsigned l = sub; l < N_LAYERS && k < nr; l += ROAD_THREADS) {
             const unsigned n = (pk >> (4 * l)) & 15u;
             unsigned m = 0;
             for (unsigned dd = 0; dd < n; ++dd) {
                 const unsigned v = s.coord[k][l * 8 + dd];
                 m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
+                for (unsigned x = 0; x < dd; ++x)
+                    rep |= s.coord[k][l * 8 + x] == v;
             }
             if (l < 4)
                 lo |= m << (8 * l);
@@ -763,6 +766,7 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
         }
         lo = group_or(lo);
         hi = group_or(hi);
+        rep = group_or(rep);
         const unsigned long long xm = ((unsigned long long)hi << 32) | lo;
         const unsigned layers = ((lo & 0xFFu) != 0) + ((lo & 0xFF00u) != 0) + ((lo & 0xFF0000u) != 0) +
                                 ((lo >> 24) != 0) + (hi != 0);
@@ -776,14 +780,18 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
                 r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
                 r.phi = (int16_t)(s.cp[k] >> 16);
                 r.set = s.set[k];
-                r.pad = 0;
-                d.roads[g] = r;
-                d.xmask[g] = xm;
-                d.surv_cnt[g] = 0;
                 unsigned long long N;
                 unsigned N4;
                 road_sizes(pk, N, N4);
-                if (N > 0 && N4 > (unsigned)d.small_n4) {   // fitted by a whole CTA
+                // fitted by a whole CTA: roads with more distinct fits than a
+                // warp's run takes, and cross-road candidates with a repeated
+                // coordinate (they publish over raw hits)
+                const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep));
+                r.cta = big ? 1 : 0;
+                d.roads[g] = r;
+                d.xmask[g] = xm;
+                d.surv_cnt[g] = 0;
+                if (big) {
                     unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
                     if (i < d.max_roads)
                         d.big_list[i] = g;
@@ -821,22 +829,9 @@ __device__ void p2_phase(const Dev &d, unsigned char *smem)
 }
 
 // ---------------------------------------------------------------------------
-// P3: fit + cut + road-local hit-warrior, warp or CTA per road
+// P3: fit + cut + road-local hit-warrior: runs of roads per warp (the flat
+// path), the roads listed in P2 per CTA (fit_road)
 // ---------------------------------------------------------------------------
-
-struct WarpGroup {
-    static constexpr unsigned SIZE = 32;
-    __device__ unsigned rank() const { return lane_id(); }
-    __device__ void sync() const { __syncwarp(); }
-    // position of a flagged thread among this tile's flagged threads; *total
-    __device__ unsigned excl_count(bool f, unsigned *total) const
-    {
-        unsigned m = __ballot_sync(FULL_MASK, f);
-        *total = __popc(m);
-        return __popc(m & lanemask_lt());
-    }
-    __device__ bool any(bool p) const { return __any_sync(FULL_MASK, p); }
-};
 
 struct BlockGroup {
     static constexpr unsigned SIZE = BLOCK;
@@ -1286,17 +1281,8 @@ struct P3Big {
     uint8_t canon[40];
     unsigned cnt[WARPS + 1];
 };
-struct P3Warp {
-    int4 A[32];
-    unsigned long long S[SURV_SLOTS];
-    unsigned long long Q[QTAB_SMALL];
-    unsigned long long K[N4_SMALL_MAX];
-    svt_const_set cs;
-    uint16_t co[40];
-    uint8_t canon[40];
-};
 
-// The 24 words of the constant set of a road record (svt_const_set is 96 B).
+// The words of the constant set of a road record.
 __device__ __forceinline__ const uint32_t *const_words(const Dev &d, unsigned set)
 {
     return reinterpret_cast<const uint32_t *>(d.consts + min(set, (unsigned)(N_SETS - 1)));
@@ -1308,22 +1294,32 @@ static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane
 // P3, flat path: a warp fits a run of small roads together, one lane per
 // table entry across the roads of the run (fit, pair tables, survivors), so
 // the per-road work is spread over the lanes instead of repeated per road.
-// It takes roads with no cross-road candidate flag and no repeated
-// coordinate in a layer; other small roads go through fit_road.
+// A coordinate repeated within a fitted layer makes the pair tables take
+// canonical hits (the lowest index with the same coordinate); a cross-road
+// candidate with a repeated coordinate goes through fit_road.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
 
 // One road of a run, in the warp's shared memory.
 struct FlatRoad {
-    unsigned g, N4, E, kb, qb, ab, ne, key_hi, set;
-    unsigned event, excl, nl, Se, cand;   // nl: hits per layer, 4 bits each; Se: comb stride of excl
+    unsigned g, N4, E, kb, qb, ab, key_hi, set;
+    unsigned event, nl, Se;       // nl: hits per layer, 4 bits each; Se: comb stride of excl
+    unsigned xl;                  // excluded layer (bits 0..2), cross-road candidate (bit 3), hits
+                                  // of the excluded layer (bits 4..7), layer of fitted slot j
+                                  // (bits 8 + 3j .. 10 + 3j)
     int curv, phi;
-    unsigned m[4], L[4], st[4], SL[4], aoff[4];
+    unsigned m[4], st[4], SL[4], aoff[4];
     unsigned off[6];
     unsigned M[3];                // magic divisors of m[0..2]
+    unsigned cm[4];               // canonical hit (the lowest index with the same coordinate) of
+                                  // each hit of fitted slot j, 3 bits each
     unsigned long long cb;        // plain mode: first combination of the road
 };
+__device__ __forceinline__ unsigned fr_excl(const FlatRoad &r) { return r.xl & 7u; }
+__device__ __forceinline__ unsigned fr_ne(const FlatRoad &r) { return (r.xl >> 4) & 15u; }
+__device__ __forceinline__ unsigned fr_layer(const FlatRoad &r, unsigned j) { return (r.xl >> (8 + 3 * j)) & 7u; }
+constexpr unsigned CANON_ID = 0xFAC688u;   // hit x -> x for x < 8, 3 bits each
 
 struct P3Flat {
     int4 A[FLAT_A];                       // partial chi-square sums, [ab + aoff[j] + hit]
@@ -1383,6 +1379,7 @@ __device__ __forceinline__ FlatIndex flat_index(unsigned first, unsigned sub)
 __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
 {
     const FlatRoad &r = F.rd[ri];
+    const unsigned excl = fr_excl(r);
     const unsigned long long xm = ldcg(d.xmask + r.g);
     unsigned fl[N_LAYERS], cnt[10], total = 0;
     for (unsigned l = 0; l < N_LAYERS; ++l) {
@@ -1404,11 +1401,11 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
         const unsigned dsel[3] = {nth_bit(fl[lt[0]], rem % p0), nth_bit(fl[lt[1]], (rem / p0) % p1),
                                   nth_bit(fl[lt[2]], rem / (p0 * p1))};
         unsigned long long mn = NO_KEY;
-        if (lt[0] != r.excl && lt[1] != r.excl && lt[2] != r.excl) {
+        if (lt[0] != excl && lt[1] != excl && lt[2] != excl) {
             // the free fitted slot runs over its hits, the three others are fixed
             unsigned fb = 0, free_slot = 0 + 1 + 2 + 3;
             for (unsigned q = 0; q < 3; ++q) {
-                const unsigned sq_ = lt[q] - (lt[q] > r.excl);
+                const unsigned sq_ = lt[q] - (lt[q] > excl);
                 free_slot -= sq_;
                 fb += dsel[q] * r.st[sq_];
             }
@@ -1421,13 +1418,13 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
             // coordinate (the index itself, canonical) and the pair table
             unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
             for (unsigned q = 0; q < 3; ++q) {
-                if (lt[q] == r.excl) {
+                if (lt[q] == excl) {
                     de = dsel[q];
                 } else if (fa == 4) {
-                    fa = lt[q] - (lt[q] > r.excl);
+                    fa = lt[q] - (lt[q] > excl);
                     da = dsel[q];
                 } else {
-                    fb = lt[q] - (lt[q] > r.excl);
+                    fb = lt[q] - (lt[q] > excl);
                     db = dsel[q];
                 }
             }
@@ -1447,10 +1444,8 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
     __syncwarp();
 }
 
-// Fit roads g0 .. g0 + R - 1 (R <= WARP_ROADS) with one warp.  `region` is
-// the warp's shared memory, seen as P3Flat for the flat sub-runs and then as
-// P3Warp for the roads that fit_road takes.  Roads whose distinct fits exceed
-// small_n4 are skipped (a CTA fits them).
+// Fit roads g0 .. g0 + R - 1 (R <= WARP_ROADS) with one warp; `region` is
+// the warp's shared memory.  Roads marked in P2 for a whole CTA are skipped.
 template <bool PLAIN>
 __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsigned R,
                         unsigned long long &npass)
@@ -1470,11 +1465,11 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         F.co[idx / 40][idx % 40] = ldcg(d.coords + (size_t)g0 * 40 + idx);
     __syncwarp();
 
-    // lane i < R: the shape of road i and whether the flat path takes it
-    const bool small = lane < R && N > 0 && N4 <= (unsigned)d.small_n4;
+    // lane i < R: the shape of road i (a road the CTAs fit is skipped)
+    const bool small = lane < R && N > 0 && !rec.cta;
     FlatRoad fr;
     unsigned E = 0, asum = 0;
-    bool flat = false;
+    bool flat = false, dup_fit = false;
     if (small) {
         const uint32_t pk = rec.pk;
         const unsigned excl = min((pk >> 20) & 7u, 4u);
@@ -1484,11 +1479,24 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             S5[l] = S;
             S *= n[l];
         }
+        // canonical hits of each fitted layer; a repeated coordinate makes
+        // the pair tables take canonical indices (dup_fit)
         unsigned j = 0, st = 1;
+        unsigned xl = excl | (((pk >> 23) & 1u) << 3) | (n[excl] << 4);
+        dup_fit = false;
         for (unsigned l = 0; l < N_LAYERS; ++l) {
             if (l == excl)
                 continue;
-            fr.L[j] = l;
+            xl |= l << (8 + 3 * j);
+            unsigned map = CANON_ID;
+            for (unsigned x = 1; x < n[l]; ++x) {
+                unsigned c = x;
+                for (unsigned y = x; y-- > 0;)   // the lowest equal index wins
+                    c = F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y] ? y : c;
+                map = (map & ~(7u << (3 * x))) | (c << (3 * x));
+            }
+            fr.cm[j] = map;
+            dup_fit = dup_fit || map != CANON_ID;
             fr.m[j] = n[l];
             fr.st[j] = st;
             fr.SL[j] = S5[l];
@@ -1505,25 +1513,21 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             fr.M[s] = c_magic[fr.m[s]];
         fr.g = g0 + lane;
         fr.event = rec.event;
-        fr.excl = excl;
+        fr.xl = xl;
         fr.nl = pk & 0xFFFFFu;
         fr.Se = S5[excl];
-        fr.cand = (pk >> 23) & 1u;
         fr.N4 = N4;
         fr.E = E;
-        fr.ne = n[excl];
         fr.key_hi = rec.pk >> 24;
         fr.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
         fr.curv = rec.curv;
         fr.phi = rec.phi;
         fr.cb = PLAIN ? ldcg(d.comb_off + g0 + lane) : 0ull;
-        // a coordinate repeated within a layer needs the canonical-index path
-        bool dup = false;
-        for (unsigned l = 0; l < N_LAYERS; ++l)
-            for (unsigned x = 1; x < n[l]; ++x)
-                for (unsigned y = 0; y < x; ++y)
-                    dup = dup || F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y];
-        flat = !dup && N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
+        // every road a warp takes fits the tables: N4 <= small_n4 <= FLAT_K,
+        // and then E <= QTAB_SMALL and asum <= 32
+        flat = N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
+        if (!flat)
+            raise_flag(d, FLAG_INTERNAL);
     }
 
     // flat sub-runs: a prefix of the remaining flat roads that fits the tables
@@ -1544,6 +1548,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         }
         const bool take = mine && ik <= FLAT_K && iq <= FLAT_Q && ia <= FLAT_A;
         const unsigned sub = __ballot_sync(FULL_MASK, take);   // the first roads left
+        const bool sdup = __any_sync(FULL_MASK, take && dup_fit);
         const unsigned s1 = 31 - __clz(sub);
         const unsigned nk = __shfl_sync(FULL_MASK, ik, s1), nq = __shfl_sync(FULL_MASK, iq, s1),
                        na = __shfl_sync(FULL_MASK, ia, s1);
@@ -1565,7 +1570,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 const unsigned local = t - r.ab;
                 const unsigned j = (local >= r.aoff[1]) + (local >= r.aoff[2]) + (local >= r.aoff[3]);
                 const unsigned dd = local - r.aoff[j];
-                const int h = F.co[ri][r.L[j] * 8 + dd];
+                const int h = F.co[ri][fr_layer(r, j) * 8 + dd];
                 const svt_const_set *cs = d.consts + r.set;
                 int4 a;
                 a.x = (int)__ldg(&cs->C[0][j]) * h;
@@ -1627,13 +1632,20 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                     const int sz = a0.z + a1.z + a2.z + a3.z;
                     const long long chi2 = sq(sx >> 12) + sq(sy >> 12) + sq(sz >> 12);
                     const bool pass = chi2 <= cut;
-                    npass += pass ? r.ne : 0u;
+                    npass += pass ? fr_ne(r) : 0u;
                     key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
                 }
+                // pair tables take canonical hits (a sub-run with a repeated
+                // coordinate maps them; elsewhere they are the hits)
+                unsigned fd[4] = {f0, f1, f2, f3};
+                if (sdup) {
+#pragma unroll
+                    for (unsigned jj = 0; jj < 4; ++jj)
+                        fd[jj] = (r.cm[jj] >> (3 * fd[jj])) & 7u;
+                }
                 F.K[t] = key;
-                F.dig[t] = (uint16_t)(f0 | (f1 << 3) | (f2 << 6) | (f3 << 9) | (ri << 12));
+                F.dig[t] = (uint16_t)(fd[0] | (fd[1] << 3) | (fd[2] << 6) | (fd[3] << 9) | (ri << 12));
                 if (key != NO_KEY) {
-                    const unsigned fd[4] = {f0, f1, f2, f3};
                     const unsigned hi = (unsigned)(key >> 32);
                     maybe = true;
 #pragma unroll
@@ -1780,7 +1792,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         // which read whole keys from the pair tables.  Without a tie the low
         // words were not taken: each table's minimum high word belongs to
         // one key, which writes its low word.
-        const unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && fr.cand);
+        const unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && (fr.xl & 8u));
         if (cands && !ties) {
             for (unsigned t = lane; t < nq; t += 32)
                 F.Ql[t] = 0xFFFFFFFFu;
@@ -1809,41 +1821,15 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         __syncwarp();
     }
 
-    // the other small roads of the run, one at a time
-    unsigned rest = __ballot_sync(FULL_MASK, small && !flat);
-    if (!rest)
-        return;
-    P3Warp &W = *reinterpret_cast<P3Warp *>(region);
-    WarpGroup grp;
-    RoadSmem sm{W.A, W.co, &W.cs, W.canon, W.Q, W.K, W.S};
-    uint32_t *cst = reinterpret_cast<uint32_t *>(&W.cs);
-    while (rest) {
-        const unsigned i = __ffs(rest) - 1;
-        rest &= rest - 1;
-        const unsigned g = g0 + i;
-        RoadRec ri;
-        ri.event = __shfl_sync(FULL_MASK, rec.event, i);
-        ri.pk = __shfl_sync(FULL_MASK, rec.pk, i);
-        ri.curv = (int16_t)__shfl_sync(FULL_MASK, (int)rec.curv, i);
-        ri.phi = (int16_t)__shfl_sync(FULL_MASK, (int)rec.phi, i);
-        ri.set = (uint16_t)__shfl_sync(FULL_MASK, (unsigned)rec.set, i);
-        ri.pad = 0;
-        W.co[lane] = ldcg(d.coords + (size_t)g * 40 + lane);
-        if (lane < 8)
-            W.co[32 + lane] = ldcg(d.coords + (size_t)g * 40 + 32 + lane);
-        if (lane < CONST_WORDS)
-            cst[lane] = __ldg(const_words(d, ri.set) + lane);
-        __syncwarp();
-        fit_road<WarpGroup, PLAIN>(d, grp, sm, g, ri, npass);
-    }
 }
 
-// shared memory of one warp in the warp part of P3 (P3Flat, then P3Warp)
-constexpr size_t P3_WARP_BYTES = ((sizeof(P3Flat) > sizeof(P3Warp) ? sizeof(P3Flat) : sizeof(P3Warp)) + 15) / 16 * 16;
+// shared memory of one warp in the warp part of P3
+constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 
-// Roads with more than small_n4 distinct fits (listed in P2) are fitted by a
-// whole CTA; then every warp takes runs of WARP_ROADS consecutive roads and
-// fits the others itself (fit_run).
+// The roads listed in P2 (more than small_n4 distinct fits, or a cross-road
+// candidate with a repeated coordinate) are fitted by a whole CTA; then every
+// warp takes runs of WARP_ROADS consecutive roads and fits the others itself
+// (fit_run).
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
