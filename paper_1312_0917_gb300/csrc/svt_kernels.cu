@@ -234,6 +234,14 @@ __device__ unsigned grab(const Dev &d, int q)
     return s_item;
 }
 
+// Work queue q where every CTA's first item is its own index: the queue
+// hands out items gridDim.x, gridDim.x + 1, ... (one claim per later item,
+// none at the start, when every CTA would claim at once on one counter)
+__device__ __forceinline__ unsigned grab_after_first(const Dev &d, int q)
+{
+    return gridDim.x + grab(d, q);
+}
+
 // Grid barrier of the persistent kernel.  All CTAs are co-resident
 // (cooperative launch).  The wait is bounded by d.wait_ns; on expiry the CTA
 // raises FLAG_TIMEOUT and every CTA that sees the flag stops working.
@@ -821,7 +829,7 @@ __device__ void p2_phase(const Dev &d, unsigned char *smem)
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_chunks; i += gridDim.x * BLOCK)
         d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
-    for (unsigned e = grab(d, Q_P2); e < n_items; e = grab(d, Q_P2))
+    for (unsigned e = blockIdx.x; e < n_items; e = grab_after_first(d, Q_P2))
         p2_event(d, e, smem, n_comb);
     n_comb = block_sum(n_comb);
     if (threadIdx.x == 0 && n_comb)
@@ -1841,7 +1849,7 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
         BlockGroup grp{s.cnt};
         RoadSmem sm{s.A, s.co, &s.cs, s.canon, s.Q, s.K, s.S};
         uint32_t *cst = reinterpret_cast<uint32_t *>(&s.cs);
-        for (unsigned i = grab(d, qbig); i < n_big; i = grab(d, qbig)) {
+        for (unsigned i = blockIdx.x; i < n_big; i = grab_after_first(d, qbig)) {
             const unsigned g = min(ldcg(d.big_list + i), d.max_roads - 1);
             if (threadIdx.x < 40)
                 s.co[threadIdx.x] = ldcg(d.coords + (size_t)g * 40 + threadIdx.x);
@@ -1856,15 +1864,15 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     {
         unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
-        while (true) {
-            unsigned c = 0;
-            if (lane_id() == 0)
-                c = atomicAdd(&d.ctrl->q[qsmall], 1u);
-            c = __shfl_sync(FULL_MASK, c, 0);
-            if (c >= n_runs)
-                break;
+        // a warp's first run is its own index; the queue hands out the rest
+        const unsigned n_warps = gridDim.x * WARPS;
+        for (unsigned c = blockIdx.x * WARPS + warp_id(); c < n_runs;) {
             const unsigned g0 = c * WARP_ROADS;
             fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
+            unsigned nc = 0;
+            if (lane_id() == 0)
+                nc = n_warps + atomicAdd(&d.ctrl->q[qsmall], 1u);
+            c = __shfl_sync(FULL_MASK, nc, 0);
         }
     }
     npass = block_sum(npass);
