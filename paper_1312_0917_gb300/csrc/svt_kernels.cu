@@ -27,6 +27,8 @@
 // is floor division by 4096, and floor(s / 4096) + k == floor((s + 4096 k) /
 // 4096).  chi2 < 2^38, so the track key (chi2 << 23 | road << 15 | comb)
 // is a 61-bit integer ordered like (chi2, road, comb).
+#include <cstddef>
+
 #include "svt_internal.h"
 
 namespace svt {
@@ -1309,21 +1311,27 @@ static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane
 
 constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
 
-// One road of a run, in the warp's shared memory.
-struct FlatRoad {
-    unsigned g, N4, E, kb, qb, ab, key_hi, set;
-    unsigned event, nl, Se;       // nl: hits per layer, 4 bits each; Se: comb stride of excl
-    unsigned xl;                  // excluded layer (bits 0..2), cross-road candidate (bit 3), hits
-                                  // of the excluded layer (bits 4..7), layer of fitted slot j
-                                  // (bits 8 + 3j .. 10 + 3j)
-    int curv, phi;
+// One road of a run, in the warp's shared memory.  The fields the per-entry
+// passes read are grouped in 16-byte words (vector loads).
+struct alignas(16) FlatRoad {
+    unsigned kb, ab, qb, key_hi;  // first key, partial sum and pair-table entry; road bits of a key
     unsigned m[4], st[4], SL[4], aoff[4];
     unsigned off[6];
     unsigned M[3];                // magic divisors of m[0..2]
+    unsigned xl;                  // excluded layer (bits 0..2), cross-road candidate (bit 3), hits
+                                  // of the excluded layer (bits 4..7), layer of fitted slot j
+                                  // (bits 8 + 3j .. 10 + 3j)
+    unsigned g, N4, E, set;
+    unsigned event, nl, Se;       // nl: hits per layer, 4 bits each; Se: comb stride of excl
+    int curv, phi;
+    unsigned pad;
     unsigned cm[4];               // canonical hit (the lowest index with the same coordinate) of
                                   // each hit of fitted slot j, 3 bits each
     unsigned long long cb;        // plain mode: first combination of the road
 };
+static_assert(offsetof(FlatRoad, m) % 16 == 0 && offsetof(FlatRoad, off) % 16 == 0 &&
+                  offsetof(FlatRoad, cm) % 16 == 0,
+              "16-byte groups");
 __device__ __forceinline__ unsigned fr_excl(const FlatRoad &r) { return r.xl & 7u; }
 __device__ __forceinline__ unsigned fr_ne(const FlatRoad &r) { return (r.xl >> 4) & 15u; }
 __device__ __forceinline__ unsigned fr_layer(const FlatRoad &r, unsigned j) { return (r.xl >> (8 + 3 * j)) & 7u; }
