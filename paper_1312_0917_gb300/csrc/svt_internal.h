@@ -61,7 +61,8 @@ struct RoadRec {
     uint32_t pk;
     int16_t curv, phi;
     uint16_t set;
-    uint16_t cta;   // 1: fitted by a whole CTA (listed in big_list), not by a warp's run
+    uint16_t cta;   // bit 0: fitted by a whole CTA (listed in big_list), not by a warp's run;
+                    // bit 1: a coordinate repeated within a layer
 };
 
 // Cross-road group table slot: key = (event + 1, triple, three coordinates),

@@ -797,7 +797,7 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
                 // warp's run takes, and cross-road candidates with a repeated
                 // coordinate (they publish over raw hits)
                 const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep));
-                r.cta = big ? 1 : 0;
+                r.cta = (big ? 1 : 0) | (rep ? 2 : 0);
                 d.roads[g] = r;
                 d.xmask[g] = xm;
                 d.surv_cnt[g] = 0;
@@ -1347,6 +1347,7 @@ struct P3Flat {
     uint16_t co[WARP_ROADS][40];
     unsigned cnt[WARP_ROADS];             // survivors found so far
 };
+static_assert(offsetof(P3Flat, co) % 16 == 0, "coordinate rows are copied in 16-byte words");
 
 // the six pairs of fitted slots (a, b)
 __device__ __forceinline__ unsigned pair_a(unsigned p) { return (0x211000u >> (4 * p)) & 15u; }
@@ -1477,12 +1478,16 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         rec = ldcg(d.roads + g0 + lane);
         road_sizes(rec.pk, N, N4);
     }
-    for (unsigned idx = lane; idx < R * 40; idx += 32)
-        F.co[idx / 40][idx % 40] = ldcg(d.coords + (size_t)g0 * 40 + idx);
+    {   // 80 bytes per road, five 16-byte words
+        const uint4 *src = reinterpret_cast<const uint4 *>(d.coords + (size_t)g0 * 40);
+        uint4 *dst = reinterpret_cast<uint4 *>(&F.co[0][0]);
+        for (unsigned idx = lane; idx < R * N_LAYERS; idx += 32)
+            dst[idx] = ldcg(src + idx);
+    }
     __syncwarp();
 
     // lane i < R: the shape of road i (a road the CTAs fit is skipped)
-    const bool small = lane < R && N > 0 && !rec.cta;
+    const bool small = lane < R && N > 0 && !(rec.cta & 1u);
     FlatRoad fr;
     unsigned E = 0, asum = 0;
     bool flat = false, dup_fit = false;
@@ -1505,7 +1510,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 continue;
             xl |= l << (8 + 3 * j);
             unsigned map = CANON_ID;
-            for (unsigned x = 1; x < n[l]; ++x) {
+            for (unsigned x = 1; x < ((rec.cta & 2u) ? n[l] : 0u); ++x) {   // P2 flags repeated coordinates
                 unsigned c = x;
                 for (unsigned y = x; y-- > 0;)   // the lowest equal index wins
                     c = F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y] ? y : c;
