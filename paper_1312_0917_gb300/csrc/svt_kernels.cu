@@ -545,8 +545,28 @@ struct P2Smem {
     uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
     uint32_t multi[N_LAYERS][128];
     unsigned long long err;               // smallest fault of this event (encoded)
-    uint32_t n_ep, n_seg;
+    uint32_t n_ep, n_seg, last_ep;
+    unsigned long long nx_w0, nx_w1;      // the CTA's next event: its words, first road, index
+    uint32_t nx_r0, nx_e;
 };
+
+// The CTA's next event, claimed by thread 0 while the current one is
+// unpacked: the claim goes out at the start, the event's word and road
+// offsets are loaded midway, and they are published at the end.
+struct P2Next {
+    unsigned claim, e, r0;
+    unsigned long long w0, w1;
+};
+
+// words [w0, w1] and first road r0 of item e (the item after the last event
+// is the truncated tail)
+__device__ __forceinline__ void event_span(const Dev &d, unsigned e, unsigned n_events, unsigned long long &w0,
+                                           unsigned long long &w1, unsigned &r0)
+{
+    w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
+    w1 = e >= n_events ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
+    r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
+}
 
 constexpr unsigned ROAD_THREADS = 4;                      // threads per road in P2
 constexpr unsigned ROADS_PER_PASS = BLOCK / ROAD_THREADS;
@@ -655,20 +675,39 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
 }
 
 // Unpack event e (CTA-wide); adds the event's combinations to n_comb.
-__device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned long long &n_comb)
+__device__ __forceinline__ void p2_publish_next(P2Smem &s, const P2Next &nx)
+{
+    if (threadIdx.x == 0) {
+        s.nx_e = nx.e;
+        s.nx_w0 = nx.w0;
+        s.nx_w1 = nx.w1;
+        s.nx_r0 = nx.r0;
+    }
+}
+
+__device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsigned long long w1, unsigned r0,
+                         unsigned n_events, unsigned n_items, unsigned char *smem, unsigned long long &n_comb,
+                         P2Next &nx)
 {
     P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
-    const unsigned n_events = ldcg(&d.ctrl->n_events);
     const bool tail = e >= n_events;
-    unsigned long long w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
-    unsigned long long w1 = tail ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
-    unsigned r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
-
     if (threadIdx.x == 0) {
+        nx.claim = atomicAdd(&d.ctrl->q[Q_P2], 1u);   // used midway
         s.err = ~0ull;
         s.n_ep = 0;
     }
-    __syncthreads();
+    // the hit slots and the coordinate bitmaps start at zero (the scan's
+    // barriers order these stores before their first use)
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(&s.coord[0][0]);
+        static_assert(sizeof(s.coord) % 16 == 0 && offsetof(P2Smem, coord) % 16 == 0, "16-byte stores");
+        for (unsigned i = threadIdx.x; i < sizeof(s.coord) / 16; i += BLOCK)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
+            (&s.seen[0][0])[i] = 0;
+            (&s.multi[0][0])[i] = 0;
+        }
+    }
     // road boundaries: ranks of the EP words of [w0, w1].  Each thread takes
     // a run of up to 64 consecutive words per round (one block scan).
     unsigned running = 0;
@@ -688,6 +727,8 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
             for (unsigned u = 0; u < 8; ++u)
                 bits |= (unsigned long long)((w[u] >> 30) & 1u) << (j0 + u);
         }
+        if (w1 >= a && w1 - a < per)   // the event's last word: an EP word or not
+            s.last_ep = (unsigned)(bits >> (w1 - a)) & 1u;
         unsigned long long tot;
         unsigned k = running + (unsigned)block_excl_scan((unsigned long long)__popcll(bits), &tot);
         for (; bits; bits &= bits - 1, ++k)
@@ -695,7 +736,7 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
                 s.end[k] = (uint32_t)(a + (unsigned)(__ffsll((long long)bits) - 1));
         running += (unsigned)tot;
     }
-    bool last_ep = (__ldg(d.words + w1) >> 30) & 1u;
+    const bool last_ep = s.last_ep != 0;   // written before the last scan's barriers
     unsigned n_seg = running + (last_ep ? 0u : 1u);
     if (threadIdx.x == 0)
         s.n_ep = running;
@@ -705,9 +746,6 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
     unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
 
     // decode: four threads per road; unused hit slots stay 0
-    for (unsigned i = threadIdx.x; i < nr * 40; i += BLOCK)
-        (&s.coord[0][0])[i] = 0;
-    __syncthreads();
     unsigned long long err = ~0ull;
     const unsigned sub = threadIdx.x % ROAD_THREADS;
     for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
@@ -720,17 +758,20 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
     if (lane_id() == 0 && err != ~0ull)
         atomicMin(&s.err, err);
     __syncthreads();
-    if (threadIdx.x == 0 && s.err != ~0ull)
-        atomicMax(&d.ctrl->err_inv, ~s.err);
-    if (tail)
+    if (threadIdx.x == 0) {
+        if (s.err != ~0ull)
+            atomicMax(&d.ctrl->err_inv, ~s.err);
+        // the next event: its offsets are loaded now, published at the end
+        nx.e = gridDim.x + nx.claim;
+        if (nx.e < n_items)
+            event_span(d, nx.e, n_events, nx.w0, nx.w1, nx.r0);
+    }
+    if (tail) {
+        p2_publish_next(s, nx);
         return;
+    }
 
     // cross-road flags: coordinates present in >= 2 roads on the same layer
-    for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
-        (&s.seen[0][0])[i] = 0;
-        (&s.multi[0][0])[i] = 0;
-    }
-    __syncthreads();
     // four threads per road (layers sub and sub + 4): each distinct
     // coordinate of a layer marks the event's bitmap; a second road with it
     // sets the multi bit
@@ -815,24 +856,45 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned char *smem, unsigned
             }
         }
     }
-    for (unsigned i = threadIdx.x; i < nr * 40; i += BLOCK) {
-        const unsigned k = i / 40, g = r0 + k;
-        if (k < s.n_ep && g < d.max_roads)
-            d.coords[(size_t)r0 * 40 + i] = (&s.coord[0][0])[i];
+    {   // 16 bytes per store (a road's row is five 16-byte words)
+        uint4 *dst = reinterpret_cast<uint4 *>(d.coords + (size_t)r0 * 40);
+        const uint4 *src = reinterpret_cast<const uint4 *>(&s.coord[0][0]);
+        for (unsigned i = threadIdx.x; i < nr * N_LAYERS; i += BLOCK) {
+            const unsigned k = i / N_LAYERS, g = r0 + k;
+            if (k < s.n_ep && g < d.max_roads)
+                dst[i] = src[i];
+        }
     }
+    p2_publish_next(s, nx);
 }
 
 // P2 over the event queue; one combination-count atomic per CTA
 __device__ void p2_phase(const Dev &d, unsigned char *smem)
 {
-    const unsigned n_items = ldcg(&d.ctrl->n_events) + ldcg(&d.ctrl->has_tail);
+    P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
+    const unsigned n_events = ldcg(&d.ctrl->n_events);
+    const unsigned n_items = n_events + ldcg(&d.ctrl->has_tail);
     // survivor totals of the road chunks start at zero (the fit adds to them)
     const unsigned n_chunks = min((ldcg(&d.ctrl->n_roads) + ROAD_CHUNK - 1) / ROAD_CHUNK, d.max_chunks_r);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_chunks; i += gridDim.x * BLOCK)
         d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
-    for (unsigned e = blockIdx.x; e < n_items; e = grab_after_first(d, Q_P2))
-        p2_event(d, e, smem, n_comb);
+    // the CTA's first event is its own index; each event claims the next
+    if (threadIdx.x == 0) {
+        s.nx_e = blockIdx.x;
+        if (blockIdx.x < n_items)
+            event_span(d, blockIdx.x, n_events, s.nx_w0, s.nx_w1, s.nx_r0);
+    }
+    __syncthreads();
+    P2Next nx{0u, 0u, 0u, 0ull, 0ull};
+    for (;;) {
+        const unsigned e = s.nx_e, r0 = s.nx_r0;
+        const unsigned long long w0 = s.nx_w0, w1 = s.nx_w1;
+        if (e >= n_items)
+            break;
+        p2_event(d, e, w0, w1, r0, n_events, n_items, smem, n_comb, nx);
+        __syncthreads();   // the next event is published
+    }
     n_comb = block_sum(n_comb);
     if (threadIdx.x == 0 && n_comb)
         atomicAdd(&d.ctrl->n_comb, n_comb);
