@@ -189,7 +189,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
-        !dalloc(c, &d.cand_list, L.max_roads) &&
+        !dalloc(c, &d.cand_bits, L.max_roads / 32 + 1) &&
         !dalloc(c, &d.surv_pool, (size_t)L.max_roads * SURV_SLOTS) &&
         !dalloc(c, &d.surv_cnt, L.max_roads) &&
         !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&

@@ -42,7 +42,7 @@ struct Ctrl {
     unsigned int has_tail;        // words after the last EE
     unsigned int n_roads;         // roads of complete events
     unsigned int n_big;           // roads fitted by a whole CTA (list length)
-    unsigned int n_cand;          // cross-road candidate roads (list length)
+    unsigned int pad_c;
     unsigned int hash_used;       // claimed slots of the group table
     unsigned int q[12];           // work-queue heads
     unsigned int bar;             // grid barrier arrivals
@@ -86,7 +86,8 @@ struct Dev {
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]
     uint32_t *big_list;                                           // [max_roads]
-    uint32_t *cand_list;                                          // [max_roads]
+    uint32_t *cand_bits;                                          // [max_roads / 32 + 1] cross-road
+                                                                  // candidate roads, one bit each
     unsigned long long *surv_pool;                                // [SURV_SLOTS][max_roads] road survivors
                                                                   // (slot-major: see surv_at)
     uint8_t *surv_cnt;                                            // [max_roads]

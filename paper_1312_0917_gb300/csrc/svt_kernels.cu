@@ -474,6 +474,10 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
     below = block_sum(below);
     const unsigned n_ee = (unsigned)(all >> 32), n_ep = (unsigned)all;
     const bool fits = n_ee <= d.max_events && n_ep <= d.max_roads;
+    // the candidate bits of this batch's roads start at zero (P2 sets them)
+    if (fits)
+        for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_ep / 32 + 1; i += gridDim.x * BLOCK)
+            d.cand_bits[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctrl *c = d.ctrl;
         c->n_events = n_ee;
@@ -847,11 +851,8 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
                     if (i < d.max_roads)
                         d.big_list[i] = g;
                 }
-                if (N > 0 && cand) {   // checked against the other roads' groups after the fit
-                    unsigned i = atomicAdd(&d.ctrl->n_cand, 1u);
-                    if (i < d.max_roads)
-                        d.cand_list[i] = g;
-                }
+                if (N > 0 && cand)   // checked against the other roads' groups after the fit
+                    atomicOr(&d.cand_bits[g >> 5], 1u << (g & 31u));
                 n_comb += N;
             }
         }
@@ -2151,25 +2152,27 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_
     __syncthreads();   // s_first is reused by the next chunk
 }
 
-// P4 of the persistent kernel: the cross-road hit-warrior over the listed
-// candidate roads only (the others keep their survivors).  A road that
-// loses survivors takes them off its chunk's total.
+// P4 of the persistent kernel: the cross-road hit-warrior over the
+// candidate roads only (P2 sets their bits; the others keep their
+// survivors).  A road that loses survivors takes them off its chunk's total.
 __device__ void p4_cand_phase(const Dev &d)
 {
-    const unsigned n_cand = min(ldcg(&d.ctrl->n_cand), d.max_roads);
     const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
-    // candidate i goes to CTA i % grid: the few candidates are spread out
-    for (unsigned i = threadIdx.x * gridDim.x + blockIdx.x; i < n_cand; i += gridDim.x * BLOCK) {
-        const unsigned g = ldcg(d.cand_list + i);
-        if (g >= n_roads)
-            continue;   // a road of the truncated tail: not fitted
-        const unsigned cnt = ldcg(d.surv_cnt + g);
-        if (!cnt)
-            continue;
-        const unsigned kept = cross_check(d, g, cnt);
-        if (kept != cnt) {
-            d.surv_cnt[g] = (uint8_t)kept;
-            atomicSub(&d.rchunk_sum[g / ROAD_CHUNK], cnt - kept);
+    const unsigned n_words = (n_roads + 31) / 32;
+    // bit word w goes to CTA w % grid: the few candidates are spread out
+    for (unsigned w = threadIdx.x * gridDim.x + blockIdx.x; w < n_words; w += gridDim.x * BLOCK) {
+        for (unsigned bits = ldcg(d.cand_bits + w); bits; bits &= bits - 1) {
+            const unsigned g = w * 32 + (unsigned)(__ffs(bits) - 1);
+            if (g >= n_roads)
+                continue;   // a road of the truncated tail: not fitted
+            const unsigned cnt = ldcg(d.surv_cnt + g);
+            if (!cnt)
+                continue;
+            const unsigned kept = cross_check(d, g, cnt);
+            if (kept != cnt) {
+                d.surv_cnt[g] = (uint8_t)kept;
+                atomicSub(&d.rchunk_sum[g / ROAD_CHUNK], cnt - kept);
+            }
         }
     }
 }

@@ -43,7 +43,7 @@ constexpr size_t OFF_COORDS = OFF_ROADS + up256(sizeof(RoadRec) * S_ROADS);
 constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS);
 constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
 constexpr size_t OFF_CAND = OFF_BIG + up256(sizeof(uint32_t) * S_ROADS);
-constexpr size_t OFF_SURV = OFF_CAND + up256(sizeof(uint32_t) * S_ROADS);
+constexpr size_t OFF_SURV = OFF_CAND + up256(sizeof(uint32_t) * (S_ROADS / 32 + 1));
 constexpr size_t OFF_SCNT = OFF_SURV + up256(sizeof(unsigned long long) * SURV_SLOTS * S_ROADS);
 constexpr size_t OFF_RCH = OFF_SCNT + up256(S_ROADS);                                 // 2 x [S_CHUNKS_R] u32
 constexpr size_t OFF_CCH = OFF_RCH + up256(2 * sizeof(uint32_t) * S_CHUNKS_R);       // 2 x [S_CHUNKS_R] u64
@@ -146,7 +146,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.coords = reinterpret_cast<uint16_t *>(b + OFF_COORDS);
     d.xmask = reinterpret_cast<unsigned long long *>(b + OFF_XMASK);
     d.big_list = reinterpret_cast<uint32_t *>(b + OFF_BIG);
-    d.cand_list = reinterpret_cast<uint32_t *>(b + OFF_CAND);
+    d.cand_bits = reinterpret_cast<uint32_t *>(b + OFF_CAND);
     d.surv_pool = reinterpret_cast<unsigned long long *>(b + OFF_SURV);
     d.surv_cnt = reinterpret_cast<uint8_t *>(b + OFF_SCNT);
     uint32_t *rch = reinterpret_cast<uint32_t *>(b + OFF_RCH);
