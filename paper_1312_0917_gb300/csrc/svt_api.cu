@@ -106,7 +106,8 @@ cudaError_t enqueue(svt_ctx *c, int mode, cudaStream_t s, int *launches)
     if (e)
         return e;
     if (c->hash_dirty) {
-        if ((e = cudaMemsetAsync(c->d.hash, 0, sizeof(HashSlot) * (size_t)(c->d.hash_mask + 1), s)))
+        if ((e = cudaMemsetAsync(c->d.hash, 0, sizeof(HashSlot) * (size_t)(c->d.hash_mask + 1), s)) ||
+            (e = cudaMemsetAsync(c->d.hash_bits, 0, sizeof(uint32_t) * (c->d.hash_mask / 32 + 1), s)))
             return e;
         c->hash_dirty = false;
     }
@@ -194,10 +195,11 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.surv_cnt, L.max_roads) &&
         !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&
         !dalloc(c, &d.cchunk_sum, d.max_chunks_r) && !dalloc(c, &d.cchunk_off, d.max_chunks_r) &&
-        !dalloc(c, &d.hash, L.hash_slots) && !dalloc(c, &d.hash_used, L.hash_slots) &&
+        !dalloc(c, &d.hash, L.hash_slots) && !dalloc(c, &d.hash_bits, L.hash_slots / 32 + 1) &&
         !dalloc(c, &d.comb_off, L.max_roads) && !dalloc(c, &d.tracks, L.max_tracks) &&
         cudaMallocHost(&c->h_ctrl, sizeof(Ctrl)) == cudaSuccess &&
         cudaMemset(d.hash, 0, sizeof(HashSlot) * (size_t)L.hash_slots) == cudaSuccess &&
+        cudaMemset(d.hash_bits, 0, sizeof(uint32_t) * (L.hash_slots / 32 + 1)) == cudaSuccess &&
         cudaMemset(d.ctrl, 0, sizeof(Ctrl)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
         free_all(c);

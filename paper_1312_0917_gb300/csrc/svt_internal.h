@@ -94,7 +94,7 @@ struct Dev {
     uint32_t *rchunk_sum, *rchunk_off;                            // [max_chunks_r]
     unsigned long long *cchunk_sum, *cchunk_off;                  // [max_chunks_r]
     HashSlot *hash;
-    uint32_t *hash_used;
+    uint32_t *hash_bits;   // [hash_mask / 32 + 1] claimed slots of the group table, one bit each
     uint32_t hash_mask;
     unsigned long long *comb_off;                                 // plain: [max_roads]
     unsigned long long *fit_key;                                  // plain: [max_combs]

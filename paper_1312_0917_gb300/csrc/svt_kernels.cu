@@ -1040,10 +1040,9 @@ __device__ void hash_min(const Dev &d, unsigned long long gk, unsigned long long
     unsigned h = hash_slot(gk, d.hash_mask);
     for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
         unsigned long long prev = atomicCAS(&d.hash[h].key, 0ull, gk);
-        if (prev == 0ull) {
-            unsigned u = atomicAdd(&d.ctrl->hash_used, 1u);
-            if (u <= d.hash_mask)
-                d.hash_used[u] = h;
+        if (prev == 0ull) {   // a new slot: marked for clearing (no value awaited)
+            atomicOr(&d.hash_bits[h >> 5], 1u << (h & 31u));
+            atomicAdd(&d.ctrl->hash_used, 1u);
         }
         if (prev == 0ull || prev == gk) {
             atomicMax(&d.hash[h].val_inv, ~key);
@@ -2315,13 +2314,23 @@ __device__ void p5_phase(const Dev &d, unsigned char *smem)
     }
 }
 
-__device__ void clear_hash(const Dev &d, unsigned i)
+// Leave the group table empty: every claimed slot (its bit) is cleared, with
+// its bit.  Run by the whole grid once every lookup is done.
+__device__ void clear_hash(const Dev &d)
 {
-    unsigned n = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
-    if (i < n) {
-        unsigned h = ldcg(d.hash_used + i);
-        d.hash[h].key = 0ull;
-        d.hash[h].val_inv = 0ull;
+    if (ldcg(&d.ctrl->hash_used) == 0)
+        return;
+    const unsigned n_words = d.hash_mask / 32 + 1;
+    for (unsigned w = blockIdx.x * BLOCK + threadIdx.x; w < n_words; w += gridDim.x * BLOCK) {
+        unsigned bits = ldcg(d.hash_bits + w);
+        if (!bits)
+            continue;
+        d.hash_bits[w] = 0;
+        for (; bits; bits &= bits - 1) {
+            const unsigned h = w * 32 + (unsigned)(__ffs(bits) - 1);
+            d.hash[h].key = 0ull;
+            d.hash[h].val_inv = 0ull;
+        }
     }
 }
 
@@ -2335,7 +2344,6 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     extern __shared__ __align__(16) unsigned char smem[];
     if (d.skip_arrival && blockIdx.x == 0)
         return;   // test hook: this CTA never arrives at the first barrier
-    const unsigned nb = gridDim.x;
     stamp(d, 0);
 
     scan_count(d);
@@ -2366,9 +2374,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     stamp(d, 5);
     p5_phase(d, smem);
     // every lookup is done (barrier above): leave the group table empty
-    const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
-    for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += nb * BLOCK)
-        clear_hash(d, i);
+    clear_hash(d);
     if (threadIdx.x == 0)
         atomicMax(&d.ctrl->t_phase[6], globaltimer_ns());
 }
@@ -2545,9 +2551,7 @@ __global__ void __launch_bounds__(BLOCK) k_p5(Dev d)
         for (unsigned c = grab(d, Q_P5); c < n_chunks; c = grab(d, Q_P5))
             p5_item<true>(d, c, n_roads, s_first);
     // the previous kernels' lookups are done: leave the group table empty
-    const unsigned nh = min(ldcg(&d.ctrl->hash_used), d.hash_mask + 1);
-    for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < nh; i += gridDim.x * BLOCK)
-        clear_hash(d, i);
+    clear_hash(d);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)

@@ -49,7 +49,7 @@ constexpr size_t OFF_RCH = OFF_SCNT + up256(S_ROADS);                           
 constexpr size_t OFF_CCH = OFF_RCH + up256(2 * sizeof(uint32_t) * S_CHUNKS_R);       // 2 x [S_CHUNKS_R] u64
 constexpr size_t OFF_HASH = OFF_CCH + up256(2 * sizeof(unsigned long long) * S_CHUNKS_R);
 constexpr size_t OFF_HUSED = OFF_HASH + up256(sizeof(HashSlot) * S_HASH);
-constexpr size_t ARENA_BYTES = OFF_HUSED + up256(sizeof(uint32_t) * S_HASH);
+constexpr size_t ARENA_BYTES = OFF_HUSED + up256(sizeof(uint32_t) * (S_HASH / 32 + 1));
 static_assert(ARENA_BYTES < (8u << 20), "the static arena stays modest (under 8 MB)");
 
 }  // namespace
@@ -156,7 +156,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.cchunk_sum = cch;
     d.cchunk_off = cch + S_CHUNKS_R;
     d.hash = reinterpret_cast<HashSlot *>(b + OFF_HASH);
-    d.hash_used = reinterpret_cast<uint32_t *>(b + OFF_HUSED);
+    d.hash_bits = reinterpret_cast<uint32_t *>(b + OFF_HUSED);
     d.hash_mask = S_HASH - 1;
     d.tracks = d_tracks;
     d.cut = chi2_cut;
@@ -168,7 +168,8 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     int launches = 0;
     if (cudaMemcpyAsync(b + OFF_CONSTS, sets, sizeof(svt_const_set) * N_SETS, cudaMemcpyHostToDevice, s) ||
         cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s) ||
-        (da->hash_dirty && cudaMemsetAsync(d.hash, 0, sizeof(HashSlot) * S_HASH, s)) ||
+        (da->hash_dirty && (cudaMemsetAsync(d.hash, 0, sizeof(HashSlot) * S_HASH, s) ||
+                            cudaMemsetAsync(d.hash_bits, 0, sizeof(uint32_t) * (S_HASH / 32 + 1), s))) ||
         launch_persistent(d, s, 0, 0, &launches))
         return SVT_E_CUDA;
     Ctrl h;
