@@ -583,35 +583,31 @@ __device__ __forceinline__ unsigned group_or(unsigned x)
     return x;
 }
 
-// Decode road k of the event (words [start, end]) with the four threads of
-// its group; `sub` (0..3) takes a quarter of the words.  Every lane of the
-// warp calls it (`active` false for lanes without a road).  Hit d of layer l
-// is the d-th hit word of that layer in the road: each thread counts its
-// quarter's hits per layer, an exclusive scan over the group gives the ranks.
-__device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, unsigned sub,
-                            unsigned long long start, unsigned long long end, unsigned long long &err)
+// decode_road for a warp with a road of 256 words or more (malformed input
+// only): per-layer counters, eight loads in flight, words reloaded (L1) in
+// pass 2.  The whole warp takes this path (its shuffles span the warp).
+__device__ void decode_road_long(const Dev &d, P2Smem &s, unsigned k, unsigned sub, unsigned start,
+                                 unsigned len, unsigned qa, unsigned qb, uint32_t &hdr, uint32_t &cw,
+                                 uint32_t &pw, unsigned (&total)[N_LAYERS], unsigned long long &err)
 {
-    const unsigned long long len = active && end >= start ? end - start + 1 : 0;
-    const unsigned long long per = (len + ROAD_THREADS - 1) / ROAD_THREADS;
-    const unsigned long long qa = min(sub * per, len), qb = min(qa + per, len);
+    const uint32_t *rw = d.words + start;
     unsigned c[N_LAYERS] = {0, 0, 0, 0, 0};
-    uint32_t hdr = 0, cw = 0, pw = 0;
     // pass 1: grammar, the road's first three words, hits per layer
-    for (unsigned long long base = qa; base < qb; base += 8) {
+    for (unsigned base = qa; base < qb; base += 8) {
         uint32_t wb[8];
 #pragma unroll
-        for (unsigned u = 0; u < 8; ++u)   // eight loads in flight
-            wb[u] = base + u < qb ? __ldg(d.words + start + base + u) : 0u;
+        for (unsigned u = 0; u < 8; ++u)
+            wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
 #pragma unroll
         for (unsigned u = 0; u < 8; ++u) {
-            const unsigned long long q = base + u;
+            const unsigned q = base + u;
             if (q >= qb)
                 break;
             const uint32_t w = wb[u];
             const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
             if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
                 (ep && q < 2))
-                err = min(err, ((start + q) << 8) | RANK_BAD);
+                err = min(err, ((unsigned long long)(start + q) << 8) | RANK_BAD);
             if (q == 0)
                 hdr = w;
             else if (q == 1)
@@ -625,7 +621,7 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
         }
     }
     // ranks: exclusive scan of the per-layer counts over the group
-    unsigned rank[N_LAYERS], total[N_LAYERS];
+    unsigned rank[N_LAYERS];
 #pragma unroll
     for (unsigned l = 0; l < N_LAYERS; ++l) {
         unsigned inc = c[l];
@@ -638,18 +634,16 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
         rank[l] = inc - c[l];
         total[l] = __shfl_sync(FULL_MASK, inc, ROAD_THREADS - 1, ROAD_THREADS);
     }
-    hdr = group_or(hdr);
-    cw = group_or(cw);
-    pw = group_or(pw);
+    (void)len;
     // pass 2: place the hits (the words are in L1)
-    for (unsigned long long base = max(qa, 3ull); base < qb; base += 8) {
+    for (unsigned base = max(qa, 3u); base < qb; base += 8) {
         uint32_t wb[8];
 #pragma unroll
         for (unsigned u = 0; u < 8; ++u)
-            wb[u] = base + u < qb ? __ldg(d.words + start + base + u) : 0u;
+            wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
 #pragma unroll
         for (unsigned u = 0; u < 8; ++u) {
-            const unsigned long long q = base + u;
+            const unsigned q = base + u;
             if (q >= qb)
                 break;
             const uint32_t w = wb[u];
@@ -662,11 +656,114 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
                 if (type == l)
                     r = rank[l]++;
             if (r >= MAX_HITS)
-                err = min(err, ((start + q) << 8) | RANK_LIMIT);
+                err = min(err, ((unsigned long long)(start + q) << 8) | RANK_LIMIT);
             else
                 s.coord[k][type * 8 + r] = (uint16_t)(w & 0xFFFu);
         }
     }
+}
+
+// Decode road k of the event: words [start, end] (absolute positions, below
+// 2^31), four threads per road, thread `sub` taking a quarter of the words.
+// Every lane of the warp calls it (`active` false for lanes without a road).
+// Pass 1 checks the grammar and counts the hits per layer; a scan over the
+// four threads gives each hit its rank in its layer; pass 2 places the hits
+// (unused hit slots stay 0).  When every road of the warp is shorter than
+// 256 words, the counts and ranks of layers 0..3 are packed in 8-bit fields
+// of one word (no field can overflow) and a thread's words stay in
+// registers between the passes when it has at most four; otherwise
+// (malformed long roads) per-layer counters are used.
+__device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, unsigned sub,
+                            unsigned start, unsigned end, unsigned long long &err)
+{
+    const unsigned len = active && end >= start ? end - start + 1 : 0u;
+    const unsigned per = (len + ROAD_THREADS - 1) / ROAD_THREADS;
+    const unsigned qa = min(sub * per, len), qb = min(qa + per, len);
+    const uint32_t *rw = d.words + start;
+    uint32_t hdr = 0, cw = 0, pw = 0;
+    unsigned total[N_LAYERS];
+    if (__all_sync(FULL_MASK, len < 256)) {
+        unsigned cnt = 0, c4 = 0;   // hits of layers 0..3 (8 bits each) and of layer 4
+        uint32_t wb[4];
+        for (unsigned base = qa; base < qb; base += 4) {
+#pragma unroll
+            for (unsigned u = 0; u < 4; ++u)   // four loads in flight
+                wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
+#pragma unroll
+            for (unsigned u = 0; u < 4; ++u) {
+                const unsigned q = base + u;
+                if (q >= qb)
+                    break;
+                const uint32_t w = wb[u];
+                const unsigned type = (w >> 27) & 7u;
+                bool bad;
+                if (q < 3) {   // header (type 7), curvature (5), phi (6); no EP in the first two
+                    bad = type != ((0x657u >> (4 * q)) & 15u) || (q < 2 && ((w >> 30) & 1u));
+                    hdr = q == 0 ? w : hdr;
+                    cw = q == 1 ? w : cw;
+                    pw = q == 2 ? w : pw;
+                } else {
+                    bad = type > 4;
+                    cnt += type < 4 ? 1u << (8 * type) : 0u;
+                    c4 += type == 4;
+                }
+                if (bad)
+                    err = min(err, ((unsigned long long)(start + q) << 8) | RANK_BAD);
+            }
+        }
+        // ranks: exclusive scan of the counts over the four threads
+        unsigned ic = cnt, i4 = c4;
+#pragma unroll
+        for (unsigned o = 1; o < ROAD_THREADS; o <<= 1) {
+            const unsigned vc = __shfl_up_sync(FULL_MASK, ic, o, ROAD_THREADS);
+            const unsigned v4 = __shfl_up_sync(FULL_MASK, i4, o, ROAD_THREADS);
+            if (sub >= o) {
+                ic += vc;
+                i4 += v4;
+            }
+        }
+        const unsigned tc = __shfl_sync(FULL_MASK, ic, ROAD_THREADS - 1, ROAD_THREADS);
+        total[4] = __shfl_sync(FULL_MASK, i4, ROAD_THREADS - 1, ROAD_THREADS);
+#pragma unroll
+        for (unsigned l = 0; l < 4; ++l)
+            total[l] = (tc >> (8 * l)) & 0xFFu;
+        unsigned rk = ic - cnt, r4 = i4 - c4;
+        // pass 2: place the hits
+        const bool held = per <= 4;
+        for (unsigned base = qa; base < qb; base += 4) {
+            if (!held) {
+#pragma unroll
+                for (unsigned u = 0; u < 4; ++u)
+                    wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
+            }
+#pragma unroll
+            for (unsigned u = 0; u < 4; ++u) {
+                const unsigned q = base + u;
+                if (q >= qb)
+                    break;
+                const uint32_t w = wb[u];
+                const unsigned type = (w >> 27) & 7u;
+                if (q < 3 || type > 4)
+                    continue;
+                unsigned r;
+                if (type < 4) {
+                    r = (rk >> (8 * type)) & 0xFFu;
+                    rk += 1u << (8 * type);
+                } else {
+                    r = r4++;
+                }
+                if (r >= MAX_HITS)
+                    err = min(err, ((unsigned long long)(start + q) << 8) | RANK_LIMIT);
+                else
+                    s.coord[k][type * 8 + r] = (uint16_t)(w & 0xFFFu);
+            }
+        }
+    } else {
+        decode_road_long(d, s, k, sub, start, len, qa, qb, hdr, cw, pw, total, err);
+    }
+    hdr = group_or(hdr);
+    cw = group_or(cw);
+    pw = group_or(pw);
     if (active && sub == 0) {
         const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
         const unsigned excl = min((hdr >> 7) & 7u, 4u);
@@ -755,8 +852,8 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
     for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
         const unsigned k = kb + threadIdx.x / ROAD_THREADS;
         const bool active = k < nr;
-        decode_road(d, s, active, k, sub, !active || k == 0 ? w0 : (unsigned long long)s.end[k - 1] + 1,
-                    !active ? w0 : k < running ? (unsigned long long)s.end[k] : w1, err);
+        decode_road(d, s, active, k, sub, !active || k == 0 ? (unsigned)w0 : s.end[k - 1] + 1u,
+                    !active ? (unsigned)w0 : k < running ? s.end[k] : (unsigned)w1, err);
     }
     err = warp_min_u64(err);
     if (lane_id() == 0 && err != ~0ull)

@@ -185,6 +185,15 @@ def malformed_streams():
         "late_fault_after_good_events": big[:-5] + [big[-5] | (1 << 20)] + big[-4:],
         "limit_then_bad": road([(2, i) for i in range(9)]) + [hit(0, 1) | (1 << 13)] + good,
         "trailing_road_after_ee": good + road([(1, 1)]),
+        # roads of 256 words or more (only malformed ones can be that long)
+        # take the decoder's per-layer counting path
+        "long_road_limit": road([(2, i % 4096) for i in range(300)], last_of_event=True),
+        "long_road_among_short": road([(0, 1)]) + road([(1, i % 4096) for i in range(300)]) +
+                                 road([(0, 2)], last_of_event=True),
+        "long_road_bad_after_limit": (lambda r: r[:200] + [r[200] | (1 << 13)] + r[201:])(
+            road([(3, i % 4096) for i in range(300)], last_of_event=True)),
+        "long_road_bad_before_limit": (lambda r: r[:5] + [r[5] | (1 << 13)] + r[6:])(
+            road([(3, i % 4096) for i in range(300)], last_of_event=True)),
     }
     return cases
 
