@@ -31,6 +31,21 @@ constexpr unsigned long long NO_KEY = ~0ull;
 enum : unsigned { RANK_BAD = 1, RANK_LIMIT = 2, RANK_TRUNC = 3 };
 enum : unsigned { FLAG_CAPACITY = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4 };
 
+// The output stage's copy of each set's F and q: 24 int32 words per set
+// (F row by row, q, three zero words), so a set is six 16-byte loads.
+constexpr int FIT_WORDS = 24;
+inline void fit_words(const svt_const_set *sets, int32_t *out)
+{
+    for (int s = 0; s < N_SETS; ++s) {
+        int32_t *o = out + s * FIT_WORDS;
+        for (int j = 0; j < 18; ++j)
+            o[j] = sets[s].F[j / 6][j % 6];
+        for (int j = 0; j < 3; ++j)
+            o[18 + j] = sets[s].q[j];
+        o[21] = o[22] = o[23] = 0;
+    }
+}
+
 // Per-batch control block in device memory; zeroed by the host before each
 // batch.  Queue counters hand out work items; `bar` counts grid-barrier
 // arrivals of the persistent kernel.
@@ -86,6 +101,8 @@ struct Dev {
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]
     uint32_t *big_list;                                           // [max_roads]
+    int4 *fitc;            // [N_SETS][6]: F and q of each set as int32 (18 + 3 + 3 pad), written
+                           // with the constants (fit_words); read-only in the kernels
     uint32_t *cand_bits;                                          // [max_roads / 32 + 1] cross-road
                                                                   // candidate roads, one bit each
     unsigned long long *surv_pool;                                // [SURV_SLOTS][max_roads] road survivors

@@ -2135,15 +2135,23 @@ template <bool PLAIN>
 __device__ void build_track(const Dev &d, unsigned g, const RoadRec &rec, const uint4 (&rw)[N_LAYERS],
                             unsigned long long key, unsigned long long pos)
 {
-    const svt_const_set *cs = d.consts + min((unsigned)rec.set, (unsigned)(N_SETS - 1));
     int F[3][6], q[3];
-    if (!PLAIN) {
+    if (!PLAIN) {   // six 16-byte loads of the set's F and q
+        static_assert(FIT_WORDS == 24, "six 16-byte words per set");
+        const int4 *fc = d.fitc + 6 * min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+        int4 v[6];
+#pragma unroll
+        for (unsigned i = 0; i < 6; ++i)
+            v[i] = __ldg(fc + i);
+        const int f[24] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w,
+                           v[2].x, v[2].y, v[2].z, v[2].w, v[3].x, v[3].y, v[3].z, v[3].w,
+                           v[4].x, v[4].y, v[4].z, v[4].w, v[5].x, v[5].y, v[5].z, v[5].w};
 #pragma unroll
         for (unsigned k = 0; k < 3; ++k) {
 #pragma unroll
             for (unsigned jj = 0; jj < 6; ++jj)
-                F[k][jj] = __ldg(&cs->F[k][jj]);
-            q[k] = __ldg(&cs->q[k]);
+                F[k][jj] = f[6 * k + jj];
+            q[k] = f[18 + k];
         }
     }
     const unsigned excl = min((rec.pk >> 20) & 7u, 4u);

@@ -16,6 +16,7 @@
 #include "svt_ctx.h"
 
 #include <cstdlib>
+#include <vector>
 #include <mutex>
 
 using namespace svt;
@@ -43,7 +44,8 @@ constexpr size_t OFF_COORDS = OFF_ROADS + up256(sizeof(RoadRec) * S_ROADS);
 constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS);
 constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
 constexpr size_t OFF_CAND = OFF_BIG + up256(sizeof(uint32_t) * S_ROADS);
-constexpr size_t OFF_SURV = OFF_CAND + up256(sizeof(uint32_t) * (S_ROADS / 32 + 1));
+constexpr size_t OFF_FITC = OFF_CAND + up256(sizeof(uint32_t) * (S_ROADS / 32 + 1));
+constexpr size_t OFF_SURV = OFF_FITC + up256(sizeof(int4) * 6 * N_SETS);
 constexpr size_t OFF_SCNT = OFF_SURV + up256(sizeof(unsigned long long) * SURV_SLOTS * S_ROADS);
 constexpr size_t OFF_RCH = OFF_SCNT + up256(S_ROADS);                                 // 2 x [S_CHUNKS_R] u32
 constexpr size_t OFF_CCH = OFF_RCH + up256(2 * sizeof(uint32_t) * S_CHUNKS_R);       // 2 x [S_CHUNKS_R] u64
@@ -147,6 +149,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.xmask = reinterpret_cast<unsigned long long *>(b + OFF_XMASK);
     d.big_list = reinterpret_cast<uint32_t *>(b + OFF_BIG);
     d.cand_bits = reinterpret_cast<uint32_t *>(b + OFF_CAND);
+    d.fitc = reinterpret_cast<int4 *>(b + OFF_FITC);
     d.surv_pool = reinterpret_cast<unsigned long long *>(b + OFF_SURV);
     d.surv_cnt = reinterpret_cast<uint8_t *>(b + OFF_SCNT);
     uint32_t *rch = reinterpret_cast<uint32_t *>(b + OFF_RCH);
@@ -166,7 +169,10 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     // what must start at zero: the control block every batch, the group
     // table on the first batch and after one that did not finish
     int launches = 0;
+    std::vector<int32_t> fw((size_t)N_SETS * FIT_WORDS);   // lives until the stream is synchronized below
+    fit_words(sets, fw.data());
     if (cudaMemcpyAsync(b + OFF_CONSTS, sets, sizeof(svt_const_set) * N_SETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d.fitc, fw.data(), sizeof(int32_t) * fw.size(), cudaMemcpyHostToDevice, s) ||
         cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s) ||
         (da->hash_dirty && (cudaMemsetAsync(d.hash, 0, sizeof(HashSlot) * S_HASH, s) ||
                             cudaMemsetAsync(d.hash_bits, 0, sizeof(uint32_t) * (S_HASH / 32 + 1), s))) ||
