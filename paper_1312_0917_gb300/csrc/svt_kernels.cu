@@ -1474,8 +1474,9 @@ constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
 // passes read are grouped in 16-byte words (vector loads).
 struct alignas(16) FlatRoad {
     unsigned kb, ab, qb, key_hi;  // first key, partial sum and pair-table entry; road bits of a key
-    unsigned m[4], st[4], SL[4], aoff[4];
-    unsigned off[6];
+    unsigned m[4], st[4], SL[4], aoff[4];   // aoff: first partial sum of fitted slot j
+    unsigned off[6];              // first entry of pair table p (aoff and off are rebased on the
+                                  // sub-run's tables in the shared copy)
     unsigned M[3];                // magic divisors of m[0..2]
     unsigned xl;                  // excluded layer (bits 0..2), cross-road candidate (bit 3), hits
                                   // of the excluded layer (bits 4..7), layer of fitted slot j
@@ -1497,7 +1498,7 @@ __device__ __forceinline__ unsigned fr_layer(const FlatRoad &r, unsigned j) { re
 constexpr unsigned CANON_ID = 0xFAC688u;   // hit x -> x for x < 8, 3 bits each
 
 struct P3Flat {
-    int4 A[FLAT_A];                       // partial chi-square sums, [ab + aoff[j] + hit]
+    int4 A[FLAT_A];                       // partial chi-square sums, [aoff[j] + hit]
     unsigned long long K[FLAT_K];         // keys of distinct fits, [kb + f]
     unsigned Qh[FLAT_Q], Ql[FLAT_Q];      // pair tables, [qb + off[p] + x * m_b + y]: high and
                                           // low word of the minimum key (all ones = none)
@@ -1607,7 +1608,7 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
             unsigned p = 0;
             while (p < 5 && !(pair_a(p) == fa && pair_b(p) == fb))
                 ++p;
-            const unsigned idx = r.qb + r.off[p] + da * r.m[fb] + db;
+            const unsigned idx = r.off[p] + da * r.m[fb] + db;
             mn = ((unsigned long long)F.Qh[idx] << 32) | F.Ql[idx];
             if (mn != NO_KEY)
                 mn += (unsigned long long)de * r.Se;
@@ -1628,6 +1629,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 {
     P3Flat &F = *reinterpret_cast<P3Flat *>(region);
     const unsigned lane = lane_id();
+    unsigned np32 = 0;   // passing combinations of the run (at most 8 x 256 x 8)
 
     // the run's records and coordinates
     RoadRec rec = {};
@@ -1738,6 +1740,13 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             fr.ab = ia - asum;
             F.rd[lane] = fr;
             F.cnt[lane] = 0;
+            // the shared record's offsets are rebased on the sub-run's tables
+#pragma unroll
+            for (unsigned p = 0; p < 6; ++p)
+                F.rd[lane].off[p] = fr.off[p] + fr.qb;
+#pragma unroll
+            for (unsigned jj = 0; jj < 4; ++jj)
+                F.rd[lane].aoff[jj] = fr.aoff[jj] + fr.ab;
         }
         const FlatIndex xk = flat_index(ik - N4, sub), xa = flat_index(ia - asum, sub);
         __syncwarp();
@@ -1747,9 +1756,8 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
             for (unsigned t = lane; t < na; t += 32) {
                 const unsigned ri = xa.owner(t);
                 const FlatRoad &r = F.rd[ri];
-                const unsigned local = t - r.ab;
-                const unsigned j = (local >= r.aoff[1]) + (local >= r.aoff[2]) + (local >= r.aoff[3]);
-                const unsigned dd = local - r.aoff[j];
+                const unsigned j = (t >= r.aoff[1]) + (t >= r.aoff[2]) + (t >= r.aoff[3]);
+                const unsigned dd = t - r.aoff[j];
                 const int h = F.co[ri][fr_layer(r, j) * 8 + dd];
                 const svt_const_set *cs = d.consts + r.set;
                 int4 a;
@@ -1805,14 +1813,14 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 if (PLAIN) {
                     key = ldcg(d.fit_key + r.cb + comb);
                 } else {
-                    const int4 a0 = F.A[r.ab + r.aoff[0] + f0], a1 = F.A[r.ab + r.aoff[1] + f1];
-                    const int4 a2 = F.A[r.ab + r.aoff[2] + f2], a3 = F.A[r.ab + r.aoff[3] + f3];
+                    const int4 a0 = F.A[r.aoff[0] + f0], a1 = F.A[r.aoff[1] + f1];
+                    const int4 a2 = F.A[r.aoff[2] + f2], a3 = F.A[r.aoff[3] + f3];
                     const int sx = a0.x + a1.x + a2.x + a3.x;
                     const int sy = a0.y + a1.y + a2.y + a3.y;
                     const int sz = a0.z + a1.z + a2.z + a3.z;
                     const long long chi2 = sq(sx >> 12) + sq(sy >> 12) + sq(sz >> 12);
                     const bool pass = chi2 <= cut;
-                    npass += pass ? fr_ne(r) : 0u;
+                    np32 += pass ? fr_ne(r) : 0u;
                     key = pass ? make_key(chi2, r.key_hi, comb) : NO_KEY;
                 }
                 // pair tables take canonical hits (a sub-run with a repeated
@@ -1831,7 +1839,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
-                        const unsigned old = atomicMin(&F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]], hi);
+                        const unsigned old = atomicMin(&F.Qh[r.off[p] + fd[a] * r.m[b] + fd[b]], hi);
                         maybe = maybe && old >= hi;
                         tie = tie || old == hi;
                     }
@@ -1866,7 +1874,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
-                        cand = cand && F.Qh[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == hi;
+                        cand = cand && F.Qh[r.off[p] + fd[a] * r.m[b] + fd[b]] == hi;
                     }
                 }
                 const unsigned cb = __ballot_sync(FULL_MASK, cand);
@@ -1895,7 +1903,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 #pragma unroll
                         for (unsigned p = 0; p < 6; ++p) {
                             const unsigned a = pair_a(p), b = pair_b(p);
-                            const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                            const unsigned idx = r.off[p] + fd[a] * r.m[b] + fd[b];
                             if (F.Qh[idx] == hi)
                                 atomicMin(&F.Ql[idx], lo);
                             else
@@ -1930,7 +1938,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 #pragma unroll
                     for (unsigned p = 0; p < 6; ++p) {
                         const unsigned a = pair_a(p), b = pair_b(p);
-                        surv = surv && F.Ql[r.qb + r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
+                        surv = surv && F.Ql[r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
                     }
                 }
                 if (surv)
@@ -1988,7 +1996,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 #pragma unroll
                 for (unsigned p = 0; p < 6; ++p) {
                     const unsigned a = pair_a(p), b = pair_b(p);
-                    const unsigned idx = r.qb + r.off[p] + fd[a] * r.m[b] + fd[b];
+                    const unsigned idx = r.off[p] + fd[a] * r.m[b] + fd[b];
                     if (F.Qh[idx] == hi)
                         F.Ql[idx] = (unsigned)key;
                 }
@@ -2000,7 +2008,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         todo &= ~sub;
         __syncwarp();
     }
-
+    npass += np32;
 }
 
 // shared memory of one warp in the warp part of P3
