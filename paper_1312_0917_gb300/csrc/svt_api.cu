@@ -190,7 +190,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
-        !dalloc(c, &d.cand_bits, L.max_roads / 32 + 1) && !dalloc(c, &d.fitc, N_SETS * 6) &&
+        !dalloc(c, &d.cand_bits, L.max_roads / 32 + 1) && !dalloc(c, &d.fitc, N_SETS * SET_INT4) &&
         !dalloc(c, &d.surv_pool, (size_t)L.max_roads * SURV_SLOTS) &&
         !dalloc(c, &d.surv_cnt, L.max_roads) &&
         !dalloc(c, &d.rchunk_sum, d.max_chunks_r) && !dalloc(c, &d.rchunk_off, d.max_chunks_r) &&
@@ -239,7 +239,7 @@ int svt_load_constants(svt_ctx *c, const svt_const_set *sets, uint32_t n_sets, i
             return SVT_E_INVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<int32_t> fw((size_t)N_SETS * FIT_WORDS);
+    std::vector<int32_t> fw((size_t)N_SETS * SET_INT4 * 4);
     fit_words(sets, fw.data());
     if (cudaSetDevice(c->device) ||
         cudaMemcpyAsync(const_cast<svt_const_set *>(c->d.consts), sets, sizeof(svt_const_set) * N_SETS,

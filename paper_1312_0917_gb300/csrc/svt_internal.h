@@ -31,18 +31,27 @@ constexpr unsigned long long NO_KEY = ~0ull;
 enum : unsigned { RANK_BAD = 1, RANK_LIMIT = 2, RANK_TRUNC = 3 };
 enum : unsigned { FLAG_CAPACITY = 1, FLAG_TIMEOUT = 2, FLAG_INTERNAL = 4 };
 
-// The output stage's copy of each set's F and q: 24 int32 words per set
-// (F row by row, q, three zero words), so a set is six 16-byte loads.
-constexpr int FIT_WORDS = 24;
+// The kernels' copy of each set's constants as int32 in 16-byte words, 14
+// per set: words 0..5 hold F row by row, then q and three zeros (the output
+// stage's six loads); words 6..11 hold column j of C, (C[0][j], C[1][j],
+// C[2][j], 0); word 12 holds (k[0], k[1], k[2], 0); word 13 is zero.
+constexpr int SET_INT4 = 14;
+constexpr int SET_C = 6;   // first word of the C columns
 inline void fit_words(const svt_const_set *sets, int32_t *out)
 {
     for (int s = 0; s < N_SETS; ++s) {
-        int32_t *o = out + s * FIT_WORDS;
+        int32_t *o = out + s * SET_INT4 * 4;
+        for (int j = 0; j < SET_INT4 * 4; ++j)
+            o[j] = 0;
         for (int j = 0; j < 18; ++j)
             o[j] = sets[s].F[j / 6][j % 6];
         for (int j = 0; j < 3; ++j)
             o[18 + j] = sets[s].q[j];
-        o[21] = o[22] = o[23] = 0;
+        for (int j = 0; j < 6; ++j)
+            for (int r = 0; r < 3; ++r)
+                o[4 * (SET_C + j) + r] = sets[s].C[r][j];
+        for (int r = 0; r < 3; ++r)
+            o[4 * (SET_C + 6) + r] = sets[s].k[r];
     }
 }
 
@@ -101,7 +110,7 @@ struct Dev {
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]
     uint32_t *big_list;                                           // [max_roads]
-    int4 *fitc;            // [N_SETS][6]: F and q of each set as int32 (18 + 3 + 3 pad), written
+    int4 *fitc;            // [N_SETS][SET_INT4]: the constants as int32 in 16-byte words, written
                            // with the constants (fit_words); read-only in the kernels
     uint32_t *cand_bits;                                          // [max_roads / 32 + 1] cross-road
                                                                   // candidate roads, one bit each

@@ -1759,19 +1759,19 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 const unsigned j = (t >= r.aoff[1]) + (t >= r.aoff[2]) + (t >= r.aoff[3]);
                 const unsigned dd = t - r.aoff[j];
                 const int h = F.co[ri][fr_layer(r, j) * 8 + dd];
-                const svt_const_set *cs = d.consts + r.set;
+                // column j of the set's C (one 16-byte load; columns 4, 5 and k for slot 0)
+                const int4 *cc = d.fitc + SET_INT4 * r.set + SET_C;
+                const int4 cj = __ldg(cc + j);
                 int4 a;
-                a.x = (int)__ldg(&cs->C[0][j]) * h;
-                a.y = (int)__ldg(&cs->C[1][j]) * h;
-                a.z = (int)__ldg(&cs->C[2][j]) * h;
+                a.x = cj.x * h;
+                a.y = cj.y * h;
+                a.z = cj.z * h;
                 a.w = 0;
                 if (j == 0) {   // curvature, phi and 4096 * offset ride on slot 0
-                    a.x += (int)__ldg(&cs->C[0][4]) * r.curv + (int)__ldg(&cs->C[0][5]) * r.phi +
-                           4096 * __ldg(&cs->k[0]);
-                    a.y += (int)__ldg(&cs->C[1][4]) * r.curv + (int)__ldg(&cs->C[1][5]) * r.phi +
-                           4096 * __ldg(&cs->k[1]);
-                    a.z += (int)__ldg(&cs->C[2][4]) * r.curv + (int)__ldg(&cs->C[2][5]) * r.phi +
-                           4096 * __ldg(&cs->k[2]);
+                    const int4 c4 = __ldg(cc + 4), c5 = __ldg(cc + 5), kk = __ldg(cc + 6);
+                    a.x += c4.x * r.curv + c5.x * r.phi + 4096 * kk.x;
+                    a.y += c4.y * r.curv + c5.y * r.phi + 4096 * kk.y;
+                    a.z += c4.z * r.curv + c5.z * r.phi + 4096 * kk.z;
                 }
                 F.A[t] = a;
             }
@@ -2145,8 +2145,7 @@ __device__ void build_track(const Dev &d, unsigned g, const RoadRec &rec, const 
 {
     int F[3][6], q[3];
     if (!PLAIN) {   // six 16-byte loads of the set's F and q
-        static_assert(FIT_WORDS == 24, "six 16-byte words per set");
-        const int4 *fc = d.fitc + 6 * min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+        const int4 *fc = d.fitc + SET_INT4 * min((unsigned)rec.set, (unsigned)(N_SETS - 1));
         int4 v[6];
 #pragma unroll
         for (unsigned i = 0; i < 6; ++i)

@@ -45,7 +45,7 @@ constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS)
 constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
 constexpr size_t OFF_CAND = OFF_BIG + up256(sizeof(uint32_t) * S_ROADS);
 constexpr size_t OFF_FITC = OFF_CAND + up256(sizeof(uint32_t) * (S_ROADS / 32 + 1));
-constexpr size_t OFF_SURV = OFF_FITC + up256(sizeof(int4) * 6 * N_SETS);
+constexpr size_t OFF_SURV = OFF_FITC + up256(sizeof(int4) * SET_INT4 * N_SETS);
 constexpr size_t OFF_SCNT = OFF_SURV + up256(sizeof(unsigned long long) * SURV_SLOTS * S_ROADS);
 constexpr size_t OFF_RCH = OFF_SCNT + up256(S_ROADS);                                 // 2 x [S_CHUNKS_R] u32
 constexpr size_t OFF_CCH = OFF_RCH + up256(2 * sizeof(uint32_t) * S_CHUNKS_R);       // 2 x [S_CHUNKS_R] u64
@@ -169,7 +169,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     // what must start at zero: the control block every batch, the group
     // table on the first batch and after one that did not finish
     int launches = 0;
-    std::vector<int32_t> fw((size_t)N_SETS * FIT_WORDS);   // lives until the stream is synchronized below
+    std::vector<int32_t> fw((size_t)N_SETS * SET_INT4 * 4);   // lives until the stream is synchronized below
     fit_words(sets, fw.data());
     if (cudaMemcpyAsync(b + OFF_CONSTS, sets, sizeof(svt_const_set) * N_SETS, cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(d.fitc, fw.data(), sizeof(int32_t) * fw.size(), cudaMemcpyHostToDevice, s) ||
