@@ -113,7 +113,8 @@ __device__ __forceinline__ bool word_ok(uint32_t w)
 // combinations of a road (product of its five hit counts) and its distinct
 // fits (product over the four fitted layers: the excluded layer's hit does not
 // enter the fit), from RoadRec::pk
-__device__ __forceinline__ void road_sizes(uint32_t pk, unsigned long long &N, unsigned &N4)
+// combinations N (at most 8^5) and distinct fits N4 of a road record
+__device__ __forceinline__ void road_sizes(uint32_t pk, unsigned &N, unsigned &N4)
 {
     const unsigned excl = (pk >> 20) & 7u;
     N = 1;
@@ -182,6 +183,39 @@ __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned lon
     unsigned long long r = s_w[warp_id()] + inc - v;
     if (total)
         *total = s_w[WARPS];
+    __syncthreads();
+    return r;
+}
+
+// the same for one unsigned per thread (32-bit sums)
+__device__ unsigned block_excl_scan32(unsigned v, unsigned *total)
+{
+    __shared__ unsigned s_w32[WARPS + 1];
+    unsigned inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned n = __shfl_up_sync(FULL_MASK, inc, o);
+        if ((int)lane_id() >= o)
+            inc += n;
+    }
+    if (lane_id() == 31)
+        s_w32[warp_id()] = inc;
+    __syncthreads();
+    if (warp_id() == 0) {
+        const unsigned x = lane_id() < WARPS ? s_w32[lane_id()] : 0u;
+        unsigned xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned n = __shfl_up_sync(FULL_MASK, xi, o);
+            if ((int)lane_id() >= o)
+                xi += n;
+        }
+        if (lane_id() < WARPS)
+            s_w32[lane_id()] = xi - x;
+        if (lane_id() == WARPS - 1)
+            s_w32[WARPS] = xi;
+    }
+    __syncthreads();
+    const unsigned r = s_w32[warp_id()] + inc - v;
+    *total = s_w32[WARPS];
     __syncthreads();
     return r;
 }
@@ -809,33 +843,33 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
             (&s.multi[0][0])[i] = 0;
         }
     }
-    // road boundaries: ranks of the EP words of [w0, w1].  Each thread takes
-    // a run of up to 64 consecutive words per round (one block scan).
+    // road boundaries: ranks of the EP words of [w0, w1] (positions below
+    // 2^31).  Each thread takes a run of up to 64 consecutive words per round
+    // (one block scan).
     unsigned running = 0;
-    for (unsigned long long rw = w0; rw <= w1; rw += (unsigned long long)BLOCK * 64) {
-        const unsigned long long len = min(w1 + 1 - rw, (unsigned long long)BLOCK * 64);
-        const unsigned per = (unsigned)((len + BLOCK - 1) / BLOCK);
-        const unsigned long long a = rw + (unsigned long long)threadIdx.x * per;
+    const unsigned e0 = (unsigned)w0, e1 = (unsigned)w1;
+    for (unsigned rw = e0; rw <= e1; rw += BLOCK * 64) {
+        const unsigned len = min(e1 + 1 - rw, (unsigned)(BLOCK * 64));
+        const unsigned per = (len + BLOCK - 1) / BLOCK;
+        const unsigned a = rw + threadIdx.x * per, lim = min(per, len - min(threadIdx.x * per, len));
         unsigned long long bits = 0;
-        for (unsigned j0 = 0; j0 < per; j0 += 8) {   // eight loads in flight
-            uint32_t w[8];
+        for (unsigned j0 = 0; j0 < lim; j0 += 4) {   // four loads in flight
+            uint32_t w[4];
 #pragma unroll
-            for (unsigned u = 0; u < 8; ++u) {
-                const unsigned long long i = a + j0 + u;
-                w[u] = (j0 + u < per && i < rw + len) ? __ldg(d.words + i) : 0u;
-            }
+            for (unsigned u = 0; u < 4; ++u)
+                w[u] = j0 + u < lim ? __ldg(d.words + a + j0 + u) : 0u;
 #pragma unroll
-            for (unsigned u = 0; u < 8; ++u)
+            for (unsigned u = 0; u < 4; ++u)
                 bits |= (unsigned long long)((w[u] >> 30) & 1u) << (j0 + u);
         }
-        if (w1 >= a && w1 - a < per)   // the event's last word: an EP word or not
-            s.last_ep = (unsigned)(bits >> (w1 - a)) & 1u;
-        unsigned long long tot;
-        unsigned k = running + (unsigned)block_excl_scan((unsigned long long)__popcll(bits), &tot);
+        if (e1 >= a && e1 - a < lim)   // the event's last word: an EP word or not
+            s.last_ep = (unsigned)(bits >> (e1 - a)) & 1u;
+        unsigned tot;
+        unsigned k = running + block_excl_scan32((unsigned)__popcll(bits), &tot);
         for (; bits; bits &= bits - 1, ++k)
             if (k < MAX_ROADS_EV)
-                s.end[k] = (uint32_t)(a + (unsigned)(__ffsll((long long)bits) - 1));
-        running += (unsigned)tot;
+                s.end[k] = a + (unsigned)(__ffsll((long long)bits) - 1);
+        running += tot;
     }
     const bool last_ep = s.last_ep != 0;   // written before the last scan's barriers
     unsigned n_seg = running + (last_ep ? 0u : 1u);
@@ -932,8 +966,7 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
                 r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
                 r.phi = (int16_t)(s.cp[k] >> 16);
                 r.set = s.set[k];
-                unsigned long long N;
-                unsigned N4;
+                unsigned N, N4;
                 road_sizes(pk, N, N4);
                 // fitted by a whole CTA: roads with more distinct fits than a
                 // warp's run takes, and cross-road candidates with a repeated
@@ -1633,8 +1666,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 
     // the run's records and coordinates
     RoadRec rec = {};
-    unsigned long long N = 0;
-    unsigned N4 = 0;
+    unsigned N = 0, N4 = 0;
     if (lane < R) {
         rec = ldcg(d.roads + g0 + lane);
         road_sizes(rec.pk, N, N4);
