@@ -1521,6 +1521,7 @@ struct alignas(16) FlatRoad {
     unsigned cm[4];               // canonical hit (the lowest index with the same coordinate) of
                                   // each hit of fitted slot j, 3 bits each
     unsigned long long cb;        // plain mode: first combination of the road
+    unsigned long long xm;        // cross-road candidates: the road's flagged hits (xmask)
 };
 static_assert(offsetof(FlatRoad, m) % 16 == 0 && offsetof(FlatRoad, off) % 16 == 0 &&
                   offsetof(FlatRoad, cm) % 16 == 0,
@@ -1590,7 +1591,7 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
 {
     const FlatRoad &r = F.rd[ri];
     const unsigned excl = fr_excl(r);
-    const unsigned long long xm = ldcg(d.xmask + r.g);
+    const unsigned long long xm = r.xm;
     unsigned fl[N_LAYERS], cnt[10], total = 0;
     for (unsigned l = 0; l < N_LAYERS; ++l) {
         const unsigned n = (r.nl >> (4 * l)) & 15u;
@@ -1737,6 +1738,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         fr.curv = rec.curv;
         fr.phi = rec.phi;
         fr.cb = PLAIN ? ldcg(d.comb_off + g0 + lane) : 0ull;
+        fr.xm = ((pk >> 23) & 1u) ? ldcg(d.xmask + g0 + lane) : 0ull;   // loaded with the run
         // every road a warp takes fits the tables: N4 <= small_n4 <= FLAT_K,
         // and then E <= QTAB_SMALL and asum <= 32
         flat = N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
