@@ -1680,65 +1680,67 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
     }
     __syncwarp();
 
-    // lane i < R: the shape of road i (a road the CTAs fit is skipped)
+    // lane i < R: the shape of road i (a road the CTAs fit is skipped),
+    // written straight into the road's record in shared memory (slot i in
+    // every sub-run), so that no per-lane array needs local memory
     const bool small = lane < R && N > 0 && !(rec.cta & 1u);
-    FlatRoad fr;
-    unsigned E = 0, asum = 0;
+    unsigned E = 0, asum = 0, xl = 0;
     bool flat = false, dup_fit = false;
     if (small) {
+        FlatRoad &w = F.rd[lane];
         const uint32_t pk = rec.pk;
         const unsigned excl = min((pk >> 20) & 7u, 4u);
-        unsigned n[N_LAYERS], S5[N_LAYERS], S = 1;
+        // fitted slots: the layers other than excl, in order.  Canonical hits
+        // of each fitted layer: a repeated coordinate makes the pair tables
+        // take canonical indices (dup_fit)
+        unsigned S = 1, Se = 1, ne = 0, j = 0, st = 1;
+        xl = excl | (((pk >> 23) & 1u) << 3);
         for (unsigned l = 0; l < N_LAYERS; ++l) {
-            n[l] = min((pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
-            S5[l] = S;
-            S *= n[l];
-        }
-        // canonical hits of each fitted layer; a repeated coordinate makes
-        // the pair tables take canonical indices (dup_fit)
-        unsigned j = 0, st = 1;
-        unsigned xl = excl | (((pk >> 23) & 1u) << 3) | (n[excl] << 4);
-        dup_fit = false;
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
-            if (l == excl)
-                continue;
-            xl |= l << (8 + 3 * j);
-            unsigned map = CANON_ID;
-            for (unsigned x = 1; x < ((rec.cta & 2u) ? n[l] : 0u); ++x) {   // P2 flags repeated coordinates
-                unsigned c = x;
-                for (unsigned y = x; y-- > 0;)   // the lowest equal index wins
-                    c = F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y] ? y : c;
-                map = (map & ~(7u << (3 * x))) | (c << (3 * x));
+            const unsigned nl_ = min((pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
+            if (l == excl) {
+                Se = S;
+                ne = nl_;
+            } else {
+                xl |= l << (8 + 3 * j);
+                unsigned map = CANON_ID;
+                for (unsigned x = 1; x < ((rec.cta & 2u) ? nl_ : 0u); ++x) {   // P2 flags repeated coordinates
+                    unsigned c = x;
+                    for (unsigned y = x; y-- > 0;)   // the lowest equal index wins
+                        c = F.co[lane][l * 8 + x] == F.co[lane][l * 8 + y] ? y : c;
+                    map = (map & ~(7u << (3 * x))) | (c << (3 * x));
+                }
+                w.cm[j] = map;
+                dup_fit = dup_fit || map != CANON_ID;
+                w.m[j] = nl_;
+                w.st[j] = st;
+                w.SL[j] = S;
+                w.aoff[j] = asum;
+                asum += nl_;
+                st *= nl_;
+                ++j;
             }
-            fr.cm[j] = map;
-            dup_fit = dup_fit || map != CANON_ID;
-            fr.m[j] = n[l];
-            fr.st[j] = st;
-            fr.SL[j] = S5[l];
-            fr.aoff[j] = asum;
-            asum += n[l];
-            st *= n[l];
-            ++j;
+            S *= nl_;
         }
+        xl |= ne << 4;
         for (unsigned p = 0; p < 6; ++p) {
-            fr.off[p] = E;
-            E += fr.m[pair_a(p)] * fr.m[pair_b(p)];
+            w.off[p] = E;
+            E += w.m[pair_a(p)] * w.m[pair_b(p)];
         }
-        for (unsigned s = 0; s < 3; ++s)
-            fr.M[s] = c_magic[fr.m[s]];
-        fr.g = g0 + lane;
-        fr.event = rec.event;
-        fr.xl = xl;
-        fr.nl = pk & 0xFFFFFu;
-        fr.Se = S5[excl];
-        fr.N4 = N4;
-        fr.E = E;
-        fr.key_hi = rec.pk >> 24;
-        fr.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
-        fr.curv = rec.curv;
-        fr.phi = rec.phi;
-        fr.cb = PLAIN ? ldcg(d.comb_off + g0 + lane) : 0ull;
-        fr.xm = ((pk >> 23) & 1u) ? ldcg(d.xmask + g0 + lane) : 0ull;   // loaded with the run
+        for (unsigned q = 0; q < 3; ++q)
+            w.M[q] = c_magic[w.m[q]];
+        w.g = g0 + lane;
+        w.event = rec.event;
+        w.xl = xl;
+        w.nl = pk & 0xFFFFFu;
+        w.Se = Se;
+        w.N4 = N4;
+        w.E = E;
+        w.key_hi = rec.pk >> 24;
+        w.set = min((unsigned)rec.set, (unsigned)(N_SETS - 1));
+        w.curv = rec.curv;
+        w.phi = rec.phi;
+        w.cb = PLAIN ? ldcg(d.comb_off + g0 + lane) : 0ull;
+        w.xm = ((pk >> 23) & 1u) ? ldcg(d.xmask + g0 + lane) : 0ull;   // loaded with the run
         // every road a warp takes fits the tables: N4 <= small_n4 <= FLAT_K,
         // and then E <= QTAB_SMALL and asum <= 32
         flat = N4 <= FLAT_K && E <= FLAT_Q && asum <= FLAT_A;
@@ -1768,19 +1770,19 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         const unsigned s1 = 31 - __clz(sub);
         const unsigned nk = __shfl_sync(FULL_MASK, ik, s1), nq = __shfl_sync(FULL_MASK, iq, s1),
                        na = __shfl_sync(FULL_MASK, ia, s1);
-        if (take) {
-            fr.kb = ik - N4;
-            fr.qb = iq - E;
-            fr.ab = ia - asum;
-            F.rd[lane] = fr;
-            F.cnt[lane] = 0;
-            // the shared record's offsets are rebased on the sub-run's tables
+        if (take) {   // the road's record joins the sub-run: offsets rebased on its tables
+            FlatRoad &w = F.rd[lane];
+            const unsigned qb = iq - E, ab = ia - asum;
+            w.kb = ik - N4;
+            w.qb = qb;
+            w.ab = ab;
 #pragma unroll
             for (unsigned p = 0; p < 6; ++p)
-                F.rd[lane].off[p] = fr.off[p] + fr.qb;
+                w.off[p] += qb;
 #pragma unroll
             for (unsigned jj = 0; jj < 4; ++jj)
-                F.rd[lane].aoff[jj] = fr.aoff[jj] + fr.ab;
+                w.aoff[jj] += ab;
+            F.cnt[lane] = 0;
         }
         const FlatIndex xk = flat_index(ik - N4, sub), xa = flat_index(ia - asum, sub);
         __syncwarp();
@@ -2014,7 +2016,7 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         // which read whole keys from the pair tables.  Without a tie the low
         // words were not taken: each table's minimum high word belongs to
         // one key, which writes its low word.
-        const unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && (fr.xl & 8u));
+        const unsigned cands = __ballot_sync(FULL_MASK, ((sub >> lane) & 1u) && (xl & 8u));
         if (cands && !ties) {
             for (unsigned t = lane; t < nq; t += 32)
                 F.Ql[t] = 0xFFFFFFFFu;
