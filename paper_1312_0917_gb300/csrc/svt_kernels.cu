@@ -1591,30 +1591,45 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
 {
     const FlatRoad &r = F.rd[ri];
     const unsigned excl = fr_excl(r);
-    const unsigned long long xm = r.xm;
-    unsigned fl[N_LAYERS], cnt[10], total = 0;
+    // flagged hits of layer l: byte l of flp (no arrays indexed at run time)
+    unsigned long long flp = 0;
+#pragma unroll
     for (unsigned l = 0; l < N_LAYERS; ++l) {
         const unsigned n = (r.nl >> (4 * l)) & 15u;
-        fl[l] = (unsigned)(xm >> (8 * l)) & ((1u << n) - 1u);
+        flp |= (r.xm & ((unsigned long long)((1u << n) - 1u) << (8 * l)));
     }
-    for (unsigned t = 0; t < 10; ++t) {
-        cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) * __popc(fl[c_triple[t][2]]);
-        total += cnt[t];
-    }
+    const auto fl = [flp](unsigned l) { return (unsigned)(flp >> (8 * l)) & 0xFFu; };
+    const auto groups = [&fl](unsigned t) {   // groups of triple t
+        return __popc(fl(triple_l(t, 0))) * __popc(fl(triple_l(t, 1))) * __popc(fl(triple_l(t, 2)));
+    };
+    unsigned total = 0;
+#pragma unroll
+    for (unsigned t = 0; t < 10; ++t)
+        total += groups(t);
     for (unsigned gi = lane_id(); gi < total; gi += 32) {
         unsigned t = 0, rem = gi;
-        while (t < 9 && rem >= cnt[t]) {
-            rem -= cnt[t];
-            ++t;
+        bool found = false;
+#pragma unroll
+        for (unsigned tt = 0; tt < 10; ++tt) {   // the triple of group gi
+            const unsigned c = groups(tt);
+            if (!found) {
+                if (rem < c) {
+                    t = tt;
+                    found = true;
+                } else {
+                    rem -= c;
+                }
+            }
         }
-        const unsigned lt[3] = {c_triple[t][0], c_triple[t][1], c_triple[t][2]};
-        const unsigned p0 = __popc(fl[lt[0]]), p1 = __popc(fl[lt[1]]);
-        const unsigned dsel[3] = {nth_bit(fl[lt[0]], rem % p0), nth_bit(fl[lt[1]], (rem / p0) % p1),
-                                  nth_bit(fl[lt[2]], rem / (p0 * p1))};
+        const unsigned lt[3] = {triple_l(t, 0), triple_l(t, 1), triple_l(t, 2)};
+        const unsigned f0 = fl(lt[0]), f1 = fl(lt[1]), f2 = fl(lt[2]);
+        const unsigned p0 = __popc(f0), p1 = __popc(f1);
+        const unsigned dsel[3] = {nth_bit(f0, rem % p0), nth_bit(f1, (rem / p0) % p1), nth_bit(f2, rem / (p0 * p1))};
         unsigned long long mn = NO_KEY;
         if (lt[0] != excl && lt[1] != excl && lt[2] != excl) {
             // the free fitted slot runs over its hits, the three others are fixed
             unsigned fb = 0, free_slot = 0 + 1 + 2 + 3;
+#pragma unroll
             for (unsigned q = 0; q < 3; ++q) {
                 const unsigned sq_ = lt[q] - (lt[q] > excl);
                 free_slot -= sq_;
@@ -1628,6 +1643,7 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
             // the excluded layer in the triple: its lowest hit index of the
             // coordinate (the index itself, canonical) and the pair table
             unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
+#pragma unroll
             for (unsigned q = 0; q < 3; ++q) {
                 if (lt[q] == excl) {
                     de = dsel[q];
