@@ -579,6 +579,7 @@ struct P2Smem {
     uint32_t pk[MAX_ROADS_EV];            // RoadRec::pk without the candidate bit
     uint32_t cp[MAX_ROADS_EV];            // curv | phi << 16
     uint16_t set[MAX_ROADS_EV];
+    uint8_t rep[MAX_ROADS_EV];            // a coordinate repeated within a layer of the road
     uint16_t coord[MAX_ROADS_EV][40];     // [road][layer * 8 + hit]
     uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
     uint32_t multi[N_LAYERS][128];
@@ -806,6 +807,7 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
                   (min(total[3], mh) << 12) | (min(total[4], mh) << 16) | (excl << 20) | ((k & 255u) << 24);
         s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
         s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
+        s.rep[k] = 0;   // set by the bitmap step
     }
 }
 
@@ -924,6 +926,8 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
                     const unsigned bit = 1u << (v & 31u);
                     if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
                         atomicOr(&s.multi[l][v >> 5], bit);
+                } else {
+                    s.rep[k] = 1;
                 }
             }
         }
@@ -935,15 +939,13 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         const unsigned k = kb + threadIdx.x / ROAD_THREADS;
         const uint32_t pk = k < nr ? s.pk[k] : 0u;
         unsigned lo = 0, hi = 0;   // flagged hits of layers 0..3 and of layer 4
-        unsigned rep = 0;          // a coordinate repeated within a layer
+        const bool rep = k < nr && s.rep[k] != 0;   // a coordinate repeated within a layer
         for (unsigned l = sub; l < N_LAYERS && k < nr; l += ROAD_THREADS) {
             const unsigned n = (pk >> (4 * l)) & 15u;
             unsigned m = 0;
             for (unsigned dd = 0; dd < n; ++dd) {
                 const unsigned v = s.coord[k][l * 8 + dd];
                 m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
-                for (unsigned x = 0; x < dd; ++x)
-                    rep |= s.coord[k][l * 8 + x] == v;
             }
             if (l < 4)
                 lo |= m << (8 * l);
@@ -952,7 +954,6 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         }
         lo = group_or(lo);
         hi = group_or(hi);
-        rep = group_or(rep);
         const unsigned long long xm = ((unsigned long long)hi << 32) | lo;
         const unsigned layers = ((lo & 0xFFu) != 0) + ((lo & 0xFF00u) != 0) + ((lo & 0xFF0000u) != 0) +
                                 ((lo >> 24) != 0) + (hi != 0);
