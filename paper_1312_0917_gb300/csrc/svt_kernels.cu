@@ -220,6 +220,27 @@ __device__ unsigned block_excl_scan32(unsigned v, unsigned *total)
     return r;
 }
 
+// block-wide sums of two unsigned long long per thread, one exchange
+__device__ void block_sum2(unsigned long long &a, unsigned long long &b)
+{
+    __shared__ unsigned long long s_ab[2 * WARPS];   // a of each warp, then b
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane_id() == 0) {
+        s_ab[warp_id()] = a;
+        s_ab[WARPS + warp_id()] = b;
+    }
+    __syncthreads();
+    a = 0;
+    b = 0;
+#pragma unroll
+    for (unsigned w = 0; w < WARPS; ++w) {
+        a += s_ab[w];
+        b += s_ab[WARPS + w];
+    }
+    __syncthreads();
+}
+
 __device__ unsigned long long block_sum(unsigned long long v)
 {
     unsigned long long t;
@@ -504,8 +525,7 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
         all += v;
         below += i < blockIdx.x ? v : 0ull;
     }
-    all = block_sum(all);
-    below = block_sum(below);
+    block_sum2(all, below);
     const unsigned n_ee = (unsigned)(all >> 32), n_ep = (unsigned)all;
     const bool fits = n_ee <= d.max_events && n_ep <= d.max_roads;
     // the candidate bits of this batch's roads start at zero (P2 sets them)
@@ -539,16 +559,16 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
         __syncthreads();
         // thread t: words 32t .. 32t + 31 of the tile (zero past the slice)
         const unsigned t0 = threadIdx.x * SCAN_PT;
-        unsigned ee = 0, ep = 0;
+        unsigned cnt = 0;   // EE count in the high half, EP count in the low half (a tile: < 2^16)
 #pragma unroll
         for (unsigned k = 0; k < SCAN_PT; ++k) {
             const uint32_t x = s.w[scan_pad(t0 + k)];
-            ee += x >> 31;
-            ep += (x >> 30) & 1u;
+            cnt += ((x >> 31) << 16) | ((x >> 30) & 1u);
         }
-        unsigned long long tot;
-        const unsigned long long ex = block_excl_scan(((unsigned long long)ee << 32) | ep, &tot);
-        unsigned my_ev = ev + (unsigned)(ex >> 32), my_rd = rd + (unsigned)ex;
+        static_assert(SCAN_TILE < 65536, "tile counts fit 16 bits");
+        unsigned tot;
+        const unsigned ex = block_excl_scan32(cnt, &tot);
+        unsigned my_ev = ev + (ex >> 16), my_rd = rd + (ex & 0xFFFFu);
 #pragma unroll
         for (unsigned k = 0; k < SCAN_PT; ++k) {
             const uint32_t x = s.w[scan_pad(t0 + k)];
@@ -563,8 +583,8 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
                 ++my_ev;
             }
         }
-        ev += (unsigned)(tot >> 32);
-        rd += (unsigned)tot;
+        ev += tot >> 16;
+        rd += tot & 0xFFFFu;
         __syncthreads();   // the tile buffer is refilled next
     }
     return true;
