@@ -268,6 +268,19 @@ def test_capacity_errors(consts, cuts):
     c.close()
 
 
+def test_word_limit_of_contexts_and_servers(consts, cuts):
+    """A batch holds fewer than 2^31 words: larger limits are refused at
+    creation (SVT_E_INVAL) for contexts and servers alike."""
+    with pytest.raises(B.SvtError) as e:
+        B.Context(0, max_words=1 << 31)
+    assert e.value.code == B.E_INVAL
+    with pytest.raises(B.SvtError) as e:
+        B.Server(consts, cuts["small"], n_slots=1, max_words=1 << 31)
+    assert e.value.code == B.E_INVAL
+    c = B.Context(0, max_words=(1 << 20) + 1)   # a limit below 2^31 is accepted
+    c.close()
+
+
 def test_timeout_is_reported_and_context_survives(consts, cuts, orc):
     """A CTA that never arrives at the first grid barrier: the others' bounded
     waits run out (1 ms), the batch ends with SVT_E_TIMEOUT, and the next
