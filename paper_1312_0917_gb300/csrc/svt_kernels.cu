@@ -932,12 +932,15 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
     // four threads per road (layers sub and sub + 4): each distinct
     // coordinate of a layer marks the event's bitmap; a second road with it
     // sets the multi bit
+    // Thread q of a road takes layer q and the hits q, q + 4 of layer 4.
+    static_assert(ROAD_THREADS == 4 && N_LAYERS == 5, "four threads per road: layers 0..3, then layer 4 shared");
     for (unsigned i = threadIdx.x; i < nr * ROAD_THREADS; i += BLOCK) {
-        const unsigned k = i / ROAD_THREADS;
+        const unsigned k = i / ROAD_THREADS, q = i % ROAD_THREADS;
         const uint32_t pk = s.pk[k];
-        for (unsigned l = i % ROAD_THREADS; l < N_LAYERS; l += ROAD_THREADS) {
+        for (unsigned pass = 0; pass < 2; ++pass) {
+            const unsigned l = pass ? 4u : q;
             const unsigned n = (pk >> (4 * l)) & 15u;
-            for (unsigned dd = 0; dd < n; ++dd) {
+            for (unsigned dd = pass ? q : 0u; dd < n; dd += pass ? ROAD_THREADS : 1u) {
                 const unsigned v = s.coord[k][l * 8 + dd];
                 bool first = true;
                 for (unsigned x = 0; x < dd; ++x)
@@ -960,17 +963,19 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         const uint32_t pk = k < nr ? s.pk[k] : 0u;
         unsigned lo = 0, hi = 0;   // flagged hits of layers 0..3 and of layer 4
         const bool rep = k < nr && s.rep[k] != 0;   // a coordinate repeated within a layer
-        for (unsigned l = sub; l < N_LAYERS && k < nr; l += ROAD_THREADS) {
+        // thread sub: layer sub, and the hits sub, sub + 4 of layer 4
+        for (unsigned pass = 0; pass < 2 && k < nr; ++pass) {
+            const unsigned l = pass ? 4u : sub;
             const unsigned n = (pk >> (4 * l)) & 15u;
             unsigned m = 0;
-            for (unsigned dd = 0; dd < n; ++dd) {
+            for (unsigned dd = pass ? sub : 0u; dd < n; dd += pass ? ROAD_THREADS : 1u) {
                 const unsigned v = s.coord[k][l * 8 + dd];
                 m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
             }
-            if (l < 4)
-                lo |= m << (8 * l);
-            else
+            if (pass)
                 hi = m;
+            else
+                lo = m << (8 * l);
         }
         lo = group_or(lo);
         hi = group_or(hi);
