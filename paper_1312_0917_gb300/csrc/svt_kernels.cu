@@ -928,11 +928,10 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         return;
     }
 
-    // cross-road flags: coordinates present in >= 2 roads on the same layer
-    // four threads per road (layers sub and sub + 4): each distinct
-    // coordinate of a layer marks the event's bitmap; a second road with it
-    // sets the multi bit
-    // Thread q of a road takes layer q and the hits q, q + 4 of layer 4.
+    // cross-road flags: coordinates present in >= 2 roads on the same layer.
+    // Each distinct coordinate of a road's layer marks the event's bitmap; a
+    // second road with it sets the multi bit.  Thread q of a road takes
+    // layer q and the hits q, q + 4 of layer 4.
     static_assert(ROAD_THREADS == 4 && N_LAYERS == 5, "four threads per road: layers 0..3, then layer 4 shared");
     for (unsigned i = threadIdx.x; i < nr * ROAD_THREADS; i += BLOCK) {
         const unsigned k = i / ROAD_THREADS, q = i % ROAD_THREADS;
@@ -956,8 +955,8 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         }
     }
     __syncthreads();
-    // the road records (four threads per road: layers sub and sub + 4, the
-    // first thread writes), then the coordinates (coalesced)
+    // the road records (four threads per road: layer sub and a share of
+    // layer 4; the first thread writes), then the coordinates (coalesced)
     for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
         const unsigned k = kb + threadIdx.x / ROAD_THREADS;
         const uint32_t pk = k < nr ? s.pk[k] : 0u;
