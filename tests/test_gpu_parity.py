@@ -325,3 +325,46 @@ def test_autotune_keeps_the_fastest_and_the_tracks(ctx, orc, consts, cuts):
     assert st == B.OK
     assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["uneven"]))
     ctx.set_launch(0, 0)
+
+
+def test_two_contexts_taking_batches_in_turn(ctx, consts, cuts):
+    """The end-to-end pattern of the benchmark: two contexts on two streams,
+    batch i + 1 copied in and launched before batch i's tracks are read back
+    (their cooperative kernels queue behind each other).  Every batch equals
+    the same batch run alone."""
+    import torch
+    batches = [synth.make_batch("scaled", seed=s, n_events=400) for s in (11, 12, 13, 14, 15)]
+    ctx.load_constants(consts, cuts["scaled"])
+    ctx.use_graph(False)
+    ref = []
+    for b in batches:
+        st, t, _ = run_gpu(ctx, b.words, B.PERSISTENT)
+        assert st == B.OK
+        ref.append(t.tobytes())
+    ctxs = [ctx, B.Context(0)]
+    ctxs[1].load_constants(consts, cuts["scaled"])
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    h = [torch.from_numpy(b.words.view(np.int32)).pin_memory() for b in batches]
+    n_max = max(len(b.words) for b in batches)
+    d = [torch.empty(n_max, dtype=torch.int32, device="cuda") for _ in range(2)]
+    try:
+        for graph in (False, True):
+            for c in ctxs:
+                c.use_graph(graph)
+
+            def submit(i):
+                k = i % 2
+                with torch.cuda.stream(streams[k]):
+                    d[k][:h[i].numel()].copy_(h[i], non_blocking=True)
+                assert ctxs[k].unpack(d[k], h[i].numel(), streams[k]) == B.OK
+                B.check(ctxs[k].fit_events(B.PERSISTENT, streams[k]), "svt_fit_events")
+
+            submit(0)
+            for i in range(len(batches)):
+                if i + 1 < len(batches):
+                    submit(i + 1)
+                st, t = ctxs[i % 2].get_tracks(stream=streams[i % 2])
+                assert st == B.OK and t.tobytes() == ref[i], (graph, i)
+    finally:
+        ctx.use_graph(False)
+        ctxs[1].close()
