@@ -1696,6 +1696,34 @@ __device__ void flat_publish(const Dev &d, const P3Flat &F, unsigned ri)
     __syncwarp();
 }
 
+// Survivors of one pass of a flat sub-run (every lane of the warp calls it):
+// lane flags `surv` with its key and its road's lane ri (entries in order).
+// A road's survivors take its slots in entry order.
+__device__ __forceinline__ void flat_emit(const Dev &d, P3Flat &F, bool surv, unsigned ri,
+                                          unsigned long long key)
+{
+    const unsigned lane = lane_id();
+    if (!surv)
+        ri = WARP_ROADS + lane;   // distinct per lane unless a survivor
+    const unsigned sv = __ballot_sync(FULL_MASK, surv);
+    if (!sv)
+        return;
+    const unsigned same = __match_any_sync(FULL_MASK, ri) & sv;
+    unsigned pos = 0;
+    if (surv)
+        pos = F.cnt[ri] + __popc(same & lanemask_lt());
+    __syncwarp();
+    if (surv) {
+        if (pos < SURV_SLOTS)
+            d.surv_pool[surv_at(d, F.rd[ri].g, pos)] = key;
+        else
+            raise_flag(d, FLAG_INTERNAL);
+        if ((same >> lane) == 1u)   // the last survivor of its road in this pass
+            F.cnt[ri] = pos + 1;
+    }
+    __syncwarp();
+}
+
 // Fit roads g0 .. g0 + R - 1 (R <= WARP_ROADS) with one warp; `region` is
 // the warp's shared memory.  Roads marked in P2 for a whole CTA are skipped.
 template <bool PLAIN>
@@ -1931,8 +1959,9 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         __syncwarp();
 
         // candidates: keys whose high word is the minimum of all six
-        // tables, listed in entry order over the partial sums (no longer
-        // needed).  Without a tie a candidate is a survivor.
+        // tables.  Without a tie a candidate is a survivor and is written at
+        // once; after a tie the candidates are listed in entry order over the
+        // partial sums (no longer needed) for the low-word test.
         uint16_t *cl = reinterpret_cast<uint16_t *>(F.A);
         static_assert(sizeof(F.A) >= FLAT_K * sizeof(uint16_t), "candidate list fits over A");
         unsigned ncand = 0;
@@ -1941,11 +1970,15 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                 const unsigned i = base + lane;
                 bool cand = false;
                 unsigned t = 0;
+                unsigned long long key = NO_KEY;
+                unsigned ri = 0;
                 if (i < nmaybe) {
                     t = ml[i];
-                    const unsigned hi = (unsigned)(F.K[t] >> 32);
+                    key = F.K[t];
+                    const unsigned hi = (unsigned)(key >> 32);
                     const unsigned dg = F.dig[t];
-                    const FlatRoad &r = F.rd[dg >> 12];
+                    ri = dg >> 12;
+                    const FlatRoad &r = F.rd[ri];
                     const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
                     cand = true;
 #pragma unroll
@@ -1954,10 +1987,9 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
                         cand = cand && F.Qh[r.off[p] + fd[a] * r.m[b] + fd[b]] == hi;
                     }
                 }
-                const unsigned cb = __ballot_sync(FULL_MASK, cand);
-                if (cand)
-                    cl[ncand + __popc(cb & lanemask_lt())] = (uint16_t)t;
-                ncand += __popc(cb);
+                // without a tie a candidate is a survivor: written now (the
+                // maybe keys are in entry order)
+                flat_emit(d, F, cand, ri, key);
             }
         } else {
             // a tie: the low words start empty (the list over them is
@@ -1996,46 +2028,29 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
         }
         __syncwarp();
 
-        // survivors: candidates that hold the minimum of all six tables.  A
-        // road's survivors take its slots in entry order.
+        // after a tie: survivors are the candidates that also hold the low
+        // word of all six tables (in entry order)
         for (unsigned base = 0; base < ncand; base += 32) {
             const unsigned i = base + lane;
-            unsigned ri = WARP_ROADS + lane;   // distinct per lane unless a survivor
+            unsigned ri = 0;
             bool surv = false;
             unsigned long long key = NO_KEY;
             if (i < ncand) {
                 const unsigned t = cl[i];
                 const unsigned dg = F.dig[t];
-                const FlatRoad &r = F.rd[dg >> 12];
+                ri = dg >> 12;
+                const FlatRoad &r = F.rd[ri];
                 const unsigned fd[4] = {dg & 7u, (dg >> 3) & 7u, (dg >> 6) & 7u, (dg >> 9) & 7u};
                 key = F.K[t];
                 const unsigned lo = (unsigned)key;
                 surv = true;
-                if (ties) {
 #pragma unroll
-                    for (unsigned p = 0; p < 6; ++p) {
-                        const unsigned a = pair_a(p), b = pair_b(p);
-                        surv = surv && F.Ql[r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
-                    }
+                for (unsigned p = 0; p < 6; ++p) {
+                    const unsigned a = pair_a(p), b = pair_b(p);
+                    surv = surv && F.Ql[r.off[p] + fd[a] * r.m[b] + fd[b]] == lo;
                 }
-                if (surv)
-                    ri = dg >> 12;
             }
-            const unsigned sv = __ballot_sync(FULL_MASK, surv);
-            const unsigned same = __match_any_sync(FULL_MASK, ri) & sv;
-            unsigned pos = 0;
-            if (surv)
-                pos = F.cnt[ri] + __popc(same & lanemask_lt());
-            __syncwarp();
-            if (surv) {
-                if (pos < SURV_SLOTS)
-                    d.surv_pool[surv_at(d, F.rd[ri].g, pos)] = key;
-                else
-                    raise_flag(d, FLAG_INTERNAL);
-                if ((same >> lane) == 1u)   // the last survivor of its road in this batch
-                    F.cnt[ri] = pos + 1;
-            }
-            __syncwarp();
+            flat_emit(d, F, surv, ri, key);
         }
         {
             // survivor counts of the sub-run's roads, and their sums per road
