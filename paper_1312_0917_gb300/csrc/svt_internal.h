@@ -17,12 +17,10 @@ constexpr int MAX_ROADS_EV = 256;          // format limit: roads per event
 constexpr int MAX_HITS = 8;                // format limit: hits per layer per road
 constexpr int N_LAYERS = 5;
 constexpr int N_SETS = 360;                // 12 wedges x 6 barrels x 5 excluded layers
-constexpr int SURV_SLOTS = 64;             // survivors per road are <= 64 (see fit_road)
+constexpr int SURV_SLOTS = 64;             // survivors per road are <= 64 (see box_road)
 constexpr int ROAD_CHUNK = 256;            // roads per output work item
 constexpr int WARP_ROADS = 8;              // roads per work item of a fitting warp
-constexpr int N4_MAX = 4096;               // distinct fits per road: 8^4
 constexpr int N4_SMALL_MAX = 256;          // largest road a single warp takes
-constexpr int QTAB_BIG = 384;              // pair tables, sum_{a<b} m_a m_b for 8^4
 constexpr int QTAB_SMALL = 160;            // the same sum for any road with N4 <= 256
 constexpr unsigned long long NO_KEY = ~0ull;
 

@@ -1058,118 +1058,14 @@ __device__ void p2_phase(const Dev &d, unsigned char *smem)
 
 // ---------------------------------------------------------------------------
 // P3: fit + cut + road-local hit-warrior: runs of roads per warp (the flat
-// path), the roads listed in P2 per CTA (fit_road)
+// path), the roads listed in P2 one per warp (the box path)
 // ---------------------------------------------------------------------------
 
-struct BlockGroup {
-    static constexpr unsigned SIZE = BLOCK;
-    unsigned *s_cnt;   // WARPS + 1 entries
-    __device__ unsigned rank() const { return threadIdx.x; }
-    __device__ void sync() const { __syncthreads(); }
-    __device__ unsigned excl_count(bool f, unsigned *total) const
-    {
-        unsigned m = __ballot_sync(FULL_MASK, f);
-        __syncthreads();
-        if (lane_id() == 0)
-            s_cnt[warp_id()] = __popc(m);
-        __syncthreads();
-        unsigned before = 0, all = 0;
-        for (unsigned w = 0; w < WARPS; ++w) {
-            unsigned c = s_cnt[w];
-            before += w < warp_id() ? c : 0u;
-            all += c;
-        }
-        *total = all;
-        return before + __popc(m & lanemask_lt());
-    }
-    __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
-};
-
-// shared memory of one road
-struct RoadSmem {
-    int4 *A;                  // [32] partial chi-square sums of fitted slot j, hit d
-    uint16_t *co;             // [40] coordinates of the road (layer * 8 + hit)
-    const svt_const_set *cs;  // the road's constant set (a copy in shared memory)
-    uint8_t *canon;           // [40] lowest hit index with the same coordinate, per layer
-    unsigned long long *Q;    // pair tables
-    unsigned long long *K;    // key of each distinct fit (excluded-layer hit 0)
-    unsigned long long *S;    // [64] road-local survivors in comb order
-};
-
-// Everything about one road that every thread of its group uses.
-struct RoadInfo {
-    unsigned g, event, rie, excl, cand;
-    unsigned n[N_LAYERS];
-    unsigned m[4], L[4], st[4];      // fitted slots: size, layer, 4-D stride
-    unsigned slot_of[N_LAYERS];      // fitted slot of a layer (4 = excluded)
-    unsigned S5[N_LAYERS];           // combination stride of each layer
-    unsigned M[3];                   // magic divisors of m[0..2]
-    unsigned N4, off[7];             // distinct fits; pair-table offsets
-    int curv, phi;
-};
-
-// pair p -> slots (a, b), complement (c, e)
-__device__ __constant__ unsigned char c_pair[6][4] = {
-    {0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 3}, {1, 3, 0, 2}, {2, 3, 0, 1}};
-// the ten layer triples
-__device__ __constant__ unsigned char c_triple[10][3] = {
-    {0, 1, 2}, {0, 1, 3}, {0, 1, 4}, {0, 2, 3}, {0, 2, 4},
-    {0, 3, 4}, {1, 2, 3}, {1, 2, 4}, {1, 3, 4}, {2, 3, 4}};
 // the same triples as constants the compiler folds in unrolled loops: layer
 // k of triple t
 __device__ __forceinline__ unsigned triple_l(unsigned t, unsigned k)
 {
     return (unsigned)(((k == 0 ? 0x2111000000ull : k == 1 ? 0x3322322111ull : 0x4443443432ull) >> (4 * t)) & 15u);
-}
-
-__device__ __forceinline__ void load_road(const Dev &d, unsigned g, const RoadRec &rec, RoadInfo &r)
-{
-    r.g = g;
-    r.event = rec.event;
-    r.rie = rec.pk >> 24;
-    r.excl = min((rec.pk >> 20) & 7u, 4u);
-    r.cand = (rec.pk >> 23) & 1u;
-    unsigned S = 1;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        r.n[l] = min((rec.pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
-        r.S5[l] = S;
-        S *= r.n[l];
-    }
-    unsigned j = 0, st = 1;
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        if (l == r.excl) {
-            r.slot_of[l] = 4;
-            continue;
-        }
-        r.slot_of[l] = j;
-        r.L[j] = l;
-        r.m[j] = r.n[l];
-        r.st[j] = st;
-        st *= r.n[l];
-        ++j;
-    }
-    r.N4 = st;
-    for (unsigned s = 0; s < 3; ++s)
-        r.M[s] = c_magic[r.m[s]];
-    r.off[0] = 0;
-    for (unsigned p = 0; p < 6; ++p)
-        r.off[p + 1] = r.off[p] + r.m[c_pair[p][0]] * r.m[c_pair[p][1]];
-    r.curv = rec.curv;
-    r.phi = rec.phi;
-}
-
-__device__ __forceinline__ void digits4(const RoadInfo &r, unsigned f, unsigned &f0, unsigned &f1,
-                                        unsigned &f2, unsigned &f3)
-{
-    unsigned q = divm(f, r.M[0]);
-    f0 = f - q * r.m[0];
-    unsigned t = q;
-    q = divm(t, r.M[1]);
-    f1 = t - q * r.m[1];
-    t = q;
-    q = divm(t, r.M[2]);
-    f2 = t - q * r.m[2];
-    f3 = q;
 }
 
 __device__ __forceinline__ unsigned long long make_key(long long chi2, unsigned rie, unsigned comb)
@@ -1239,291 +1135,13 @@ __device__ __forceinline__ unsigned nth_bit(unsigned mask, unsigned n)
     return __ffs(mask) - 1;
 }
 
-// Fit one road and decide its road-local survivors.
-//
-// Combinations t = (f, i): f the hits of the four fitted layers, i the hit of
-// the excluded layer e.  chi2 depends on f only, and comb(f, i) =
-// comb(f, 0) + i * S_e, so key(f, i) = key(f, 0) + i * S_e.  Within a road
-// (f, i > 0) is always dropped by (f, 0) (same chi2, lower comb, >= 4 shared
-// hits), and a lower key that shares >= 3 hits with (f, 0) exists iff one
-// exists among the (f', 0) that agree with f on >= 2 fitted layers.  So
-// (f, 0) survives the road-local warrior iff its key is the minimum of each
-// of the six pair tables Q_ab[c_a][c_b] = min key over f' with the same
-// coordinates on fitted slots a and b.  Survivors agree pairwise on at most
-// one fitted layer, so any two slots identify them: <= 8 x 8 = 64 per road.
-//
-// On entry sm.co holds the road's 40 coordinates, visible to the whole group;
-// `rec` is the road's record.  Adds the road's passing combinations to npass.
-template <class G, bool PLAIN>
-__device__ void fit_road(const Dev &d, const G &grp, const RoadSmem &sm, unsigned g, const RoadRec &rec,
-                         unsigned long long &npass)
-{
-    RoadInfo r;
-    load_road(d, g, rec, r);
-    const unsigned tid = grp.rank();
-    const unsigned ne = r.n[r.excl];
-
-    // canonical hit indices: the lowest index with the same coordinate
-    bool dup = false;
-    for (unsigned idx = tid; idx < 40; idx += G::SIZE) {
-        const unsigned l = idx >> 3, dd = idx & 7u;
-        unsigned c = dd;
-        if (dd < r.n[l]) {
-            const unsigned v = sm.co[idx];
-            unsigned eq = 0;
-#pragma unroll
-            for (unsigned x = 0; x < MAX_HITS; ++x)
-                eq |= (x < dd && sm.co[l * 8 + x] == v) ? 1u << x : 0u;
-            c = eq ? (unsigned)(__ffs(eq) - 1) : dd;
-        }
-        sm.canon[idx] = (uint8_t)c;
-        dup = dup || c != dd;
-    }
-    // partial chi-square sums of every fitted hit
-    if (!PLAIN) {
-        const svt_const_set *cs = sm.cs;
-        for (unsigned idx = tid; idx < 32; idx += G::SIZE) {
-            unsigned j = idx >> 3, dd = idx & 7u;
-            int4 a = make_int4(0, 0, 0, 0);
-            if (dd < r.m[j]) {
-                int h = sm.co[r.L[j] * 8 + dd];
-                a.x = (int)cs->C[0][j] * h;
-                a.y = (int)cs->C[1][j] * h;
-                a.z = (int)cs->C[2][j] * h;
-                if (j == 0) {   // curvature, phi and 4096 * offset ride on slot 0
-                    a.x += (int)cs->C[0][4] * r.curv + (int)cs->C[0][5] * r.phi + 4096 * cs->k[0];
-                    a.y += (int)cs->C[1][4] * r.curv + (int)cs->C[1][5] * r.phi + 4096 * cs->k[1];
-                    a.z += (int)cs->C[2][4] * r.curv + (int)cs->C[2][5] * r.phi + 4096 * cs->k[2];
-                }
-            }
-            sm.A[idx] = a;
-        }
-    }
-    grp.sync();
-    dup = grp.any(dup);
-
-    // keys of all distinct fits
-    const unsigned long long cbase = PLAIN ? ldcg(d.comb_off + g) : 0ull;
-    for (unsigned base = 0; base < r.N4; base += G::SIZE) {
-        unsigned f = base + tid;
-        if (f < r.N4) {
-            unsigned f0, f1, f2, f3;
-            digits4(r, f, f0, f1, f2, f3);
-            unsigned comb = f0 * r.S5[r.L[0]] + f1 * r.S5[r.L[1]] + f2 * r.S5[r.L[2]] +
-                            f3 * r.S5[r.L[3]];
-            unsigned long long key;
-            if (PLAIN) {
-                key = ldcg(d.fit_key + cbase + comb);
-            } else {
-                int4 a0 = sm.A[f0], a1 = sm.A[8 + f1], a2 = sm.A[16 + f2], a3 = sm.A[24 + f3];
-                int s0 = a0.x + a1.x + a2.x + a3.x;
-                int s1 = a0.y + a1.y + a2.y + a3.y;
-                int s2 = a0.z + a1.z + a2.z + a3.z;
-                long long chi2 = sq(s0 >> 12) + sq(s1 >> 12) + sq(s2 >> 12);
-                bool pass = chi2 <= d.cut;
-                npass += pass ? ne : 0u;
-                key = pass ? make_key(chi2, r.rie, comb) : NO_KEY;
-            }
-            sm.K[f] = key;
-        }
-    }
-    grp.sync();
-
-    // pair tables over raw hit indices
-    const unsigned E = r.off[6];
-    for (unsigned idx = tid; idx < E; idx += G::SIZE) {
-        unsigned p = 0;
-        while (idx >= r.off[p + 1])
-            ++p;
-        unsigned a = c_pair[p][0], b = c_pair[p][1], c = c_pair[p][2], e = c_pair[p][3];
-        unsigned local = idx - r.off[p];
-        unsigned x = local / r.m[b], y = local - x * r.m[b];
-        unsigned fb = x * r.st[a] + y * r.st[b];
-        unsigned long long mn = NO_KEY;
-        for (unsigned z = 0; z < r.m[c]; ++z)
-            for (unsigned w = 0; w < r.m[e]; ++w) {
-                unsigned long long k = sm.K[fb + z * r.st[c] + w * r.st[e]];
-                mn = k < mn ? k : mn;
-            }
-        sm.Q[idx] = mn;
-    }
-    grp.sync();
-    // equal coordinates within a layer: fold raw entries into canonical ones
-    if (dup) {
-        if (tid < 6) {
-            unsigned p = tid, a = c_pair[p][0], b = c_pair[p][1];
-            for (unsigned x = 0; x < r.m[a]; ++x)
-                for (unsigned y = 0; y < r.m[b]; ++y) {
-                    unsigned cx = sm.canon[r.L[a] * 8 + x], cy = sm.canon[r.L[b] * 8 + y];
-                    if (cx != x || cy != y) {
-                        unsigned long long &dst = sm.Q[r.off[p] + cx * r.m[b] + cy];
-                        unsigned long long v = sm.Q[r.off[p] + x * r.m[b] + y];
-                        dst = v < dst ? v : dst;
-                    }
-                }
-        }
-        grp.sync();
-    }
-
-    // road-local survivors, in f order (= comb order)
-    unsigned n_surv = 0;
-    for (unsigned base = 0; base < r.N4; base += G::SIZE) {
-        unsigned f = base + tid;
-        bool surv = false;
-        unsigned long long key = NO_KEY;
-        if (f < r.N4) {
-            key = sm.K[f];
-            surv = key != NO_KEY;
-            if (surv) {
-                unsigned fd[4];
-                digits4(r, f, fd[0], fd[1], fd[2], fd[3]);
-                unsigned cf[4];
-#pragma unroll
-                for (unsigned j = 0; j < 4; ++j)
-                    cf[j] = sm.canon[r.L[j] * 8 + fd[j]];
-#pragma unroll
-                for (unsigned p = 0; p < 6; ++p) {
-                    unsigned a = c_pair[p][0], b = c_pair[p][1];
-                    surv = surv && sm.Q[r.off[p] + cf[a] * r.m[b] + cf[b]] == key;
-                }
-            }
-        }
-        unsigned total;
-        unsigned pos = n_surv + grp.excl_count(surv, &total);
-        if (surv) {
-            if (pos < SURV_SLOTS)
-                sm.S[pos] = key;
-            else
-                raise_flag(d, FLAG_INTERNAL);
-        }
-        n_surv += total;
-    }
-    n_surv = min(n_surv, (unsigned)SURV_SLOTS);
-    // the road's own survivor slots
-    grp.sync();
-    for (unsigned i = tid; i < n_surv; i += G::SIZE)
-        d.surv_pool[surv_at(d, g, i)] = sm.S[i];
-    if (tid == 0) {
-        d.surv_cnt[g] = (uint8_t)n_surv;
-        if (n_surv)
-            atomicAdd(&d.rchunk_sum[g / ROAD_CHUNK], n_surv);
-    }
-
-    // cross-road candidates: publish the minimum of every group whose three
-    // coordinates all appear in another road of the event
-    if (r.cand) {
-        unsigned long long xm = ldcg(d.xmask + g);
-        unsigned fl[N_LAYERS];
-        for (unsigned l = 0; l < N_LAYERS; ++l) {
-            unsigned msk = 0;
-            for (unsigned x = 0; x < r.n[l]; ++x)
-                if (((xm >> (8 * l + x)) & 1ull) && sm.canon[l * 8 + x] == x)
-                    msk |= 1u << x;
-            fl[l] = msk;
-        }
-        unsigned cnt[10], total = 0;
-        for (unsigned t = 0; t < 10; ++t) {
-            cnt[t] = __popc(fl[c_triple[t][0]]) * __popc(fl[c_triple[t][1]]) *
-                     __popc(fl[c_triple[t][2]]);
-            total += cnt[t];
-        }
-        for (unsigned gi = tid; gi < total; gi += G::SIZE) {
-            unsigned t = 0, rem = gi;
-            while (rem >= cnt[t]) {
-                rem -= cnt[t];
-                ++t;
-            }
-            unsigned l0 = c_triple[t][0], l1 = c_triple[t][1], l2 = c_triple[t][2];
-            unsigned p0 = __popc(fl[l0]), p1 = __popc(fl[l1]);
-            unsigned i0 = rem % p0, i1 = (rem / p0) % p1, i2 = rem / (p0 * p1);
-            unsigned dsel[3] = {nth_bit(fl[l0], i0), nth_bit(fl[l1], i1), nth_bit(fl[l2], i2)};
-            unsigned lt[3] = {l0, l1, l2};
-            unsigned long long mn = NO_KEY;
-            if (l0 != r.excl && l1 != r.excl && l2 != r.excl) {
-                // the free fitted slot varies; the three others run over the
-                // raw hits of each selected coordinate
-                unsigned s[3], free_slot = 0 + 1 + 2 + 3;
-                for (unsigned q = 0; q < 3; ++q) {
-                    s[q] = r.slot_of[lt[q]];
-                    free_slot -= s[q];
-                }
-                for (unsigned x0 = 0; x0 < r.m[s[0]]; ++x0) {
-                    if (sm.canon[lt[0] * 8 + x0] != dsel[0])
-                        continue;
-                    for (unsigned x1 = 0; x1 < r.m[s[1]]; ++x1) {
-                        if (sm.canon[lt[1] * 8 + x1] != dsel[1])
-                            continue;
-                        for (unsigned x2 = 0; x2 < r.m[s[2]]; ++x2) {
-                            if (sm.canon[lt[2] * 8 + x2] != dsel[2])
-                                continue;
-                            unsigned fb = x0 * r.st[s[0]] + x1 * r.st[s[1]] + x2 * r.st[s[2]];
-                            for (unsigned z = 0; z < r.m[free_slot]; ++z) {
-                                unsigned long long k = sm.K[fb + z * r.st[free_slot]];
-                                mn = k < mn ? k : mn;
-                            }
-                        }
-                    }
-                }
-            } else {
-                // excluded layer in the triple: min over its hit class is the
-                // lowest index (canonical), the two fitted slots from Q
-                unsigned de = 0, fa = 4, fb = 4, da = 0, db = 0;
-                for (unsigned q = 0; q < 3; ++q) {
-                    if (lt[q] == r.excl) {
-                        de = dsel[q];
-                    } else if (fa == 4) {
-                        fa = r.slot_of[lt[q]];
-                        da = dsel[q];
-                    } else {
-                        fb = r.slot_of[lt[q]];
-                        db = dsel[q];
-                    }
-                }
-                unsigned p = 0;
-                while (!(c_pair[p][0] == fa && c_pair[p][1] == fb))
-                    ++p;
-                mn = sm.Q[r.off[p] + da * r.m[fb] + db];
-                if (mn != NO_KEY)
-                    mn += (unsigned long long)de * r.S5[r.excl];
-            }
-            if (mn != NO_KEY) {
-                unsigned v0 = sm.co[l0 * 8 + dsel[0]], v1 = sm.co[l1 * 8 + dsel[1]];
-                unsigned v2 = sm.co[l2 * 8 + dsel[2]];
-                hash_min(d, group_key(r.event, t, v0, v1, v2), mn);
-            }
-        }
-    }
-
-    grp.sync();
-}
-
-// per-CTA shared memory layout of P3
-struct P3Big {
-    int4 A[32];
-    unsigned long long S[SURV_SLOTS];
-    unsigned long long Q[QTAB_BIG];
-    unsigned long long K[N4_MAX];
-    svt_const_set cs;
-    uint16_t co[40];
-    uint8_t canon[40];
-    unsigned cnt[WARPS + 1];
-};
-
-// The words of the constant set of a road record.
-__device__ __forceinline__ const uint32_t *const_words(const Dev &d, unsigned set)
-{
-    return reinterpret_cast<const uint32_t *>(d.consts + min(set, (unsigned)(N_SETS - 1)));
-}
-constexpr unsigned CONST_WORDS = sizeof(svt_const_set) / 4;
-static_assert(CONST_WORDS <= 32, "a warp loads a constant set, one word per lane");
-
 // ---------------------------------------------------------------------------
 // P3, flat path: a warp fits a run of small roads together, one lane per
 // table entry across the roads of the run (fit, pair tables, survivors), so
 // the per-road work is spread over the lanes instead of repeated per road.
 // A coordinate repeated within a fitted layer makes the pair tables take
 // canonical hits (the lowest index with the same coordinate); a cross-road
-// candidate with a repeated coordinate goes through fit_road.
+// candidate with a repeated coordinate goes through the box path.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned FLAT_K = N4_SMALL_MAX, FLAT_Q = QTAB_SMALL, FLAT_A = 64;
@@ -2106,38 +1724,466 @@ __device__ void fit_run(const Dev &d, unsigned char *region, unsigned g0, unsign
 // shared memory of one warp in the warp part of P3
 constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 
+// ---------------------------------------------------------------------------
+// P3, box path: one warp fits one listed road (more distinct fits than
+// small_n4, or a cross-road candidate with a repeated coordinate).
+//
+// Hits with one coordinate in one layer are one hit for the warrior (hits
+// are shared by value), and among fits with the same coordinates the lowest
+// hit index has the lowest comb.  So every pair-table minimum and every
+// road-local survivor takes canonical hits only (the lowest index of each
+// coordinate), and the warp works on the box of canonical fits.  The four
+// fitted slots get roles (a, b, c, e); in pass p, lane t = 32 p + lane takes
+// the pair (x, y) = (t mod m_a, t div m_a) of slots a and b and loops over
+// (z, w) of slots c and e.  The six pair tables (minimum key over the fits
+// with the same canonical hits on two slots) come out of that one loop:
+//   T_ab[x][y]  the lane's minimum over its own fits
+//   T_ce[z][w]  the minimum over the lanes at each step (warp reduction)
+//   T_ac, T_bc  the lane's minimum over w at each z, folded over the lanes
+//   T_ae, T_be  the lane's minimum over z for each w, folded at the end
+// A fit survives the road-local warrior iff its key is the minimum of all
+// six (see the flat path); it is then the minimum of its pair (x, y), so a
+// pair has at most one candidate and a road at most 64 survivors.
+// ---------------------------------------------------------------------------
+
+enum { T_AB = 0, T_CE, T_AC, T_BC, T_AE, T_BE, N_TAB };
+
+struct P3Box {
+    unsigned long long T[N_TAB][64];   // pair tables, [u * 8 + v] (u: the first role's hit)
+    unsigned long long TB[2][64];      // T_ce of each pass, [pass][z * 8 + w]
+    int4 A[4][8];                      // slot j, canonical hit k: chi-square partial sums (x, y,
+                                       // z) and comb part (w); slot 0 also carries curvature, phi,
+                                       // 4096 k and the road bits of the key
+    uint16_t co[40];                   // the road's coordinates, [layer * 8 + hit]
+    uint8_t raw[4][8];                 // raw hit index of canonical hit k of slot j
+    uint8_t rank[4][8];                // canonical hit (class) of raw hit d of slot j
+    uint8_t mult[4][8];                // raw hits sharing the coordinate of canonical hit k
+};
+static_assert(offsetof(P3Box, A) % 16 == 0 && offsetof(P3Box, co) % 16 == 0, "16-byte rows");
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b)
+{
+    return b < a ? b : a;
+}
+
+// hits of layer l of a road record (clamped to the format limit)
+__device__ __forceinline__ unsigned hits_of(uint32_t pk, unsigned l)
+{
+    return min((pk >> (4 * l)) & 15u, (unsigned)MAX_HITS);
+}
+
+// Key of a fit from its summed partials s: (chi2, road bits and comb), or
+// NO_KEY when it fails the cut.  s.x, s.y, s.z are 4096 times the three
+// chi-square components before the floor (exact in int32, see the header);
+// s.w is road << 15 | comb.
+__device__ __forceinline__ unsigned long long box_key(const int4 &s, long long cut, bool &pass)
+{
+    const long long chi2 = sq(s.x >> 12) + sq(s.y >> 12) + sq(s.z >> 12);
+    pass = chi2 <= cut;
+    return pass ? (((unsigned long long)chi2 << 23) | (unsigned)s.w) : NO_KEY;
+}
+
+__device__ __forceinline__ int4 add4(const int4 &a, const int4 &b)
+{
+    return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Shape of a road in the box path, the same in every lane.
+struct BoxShape {
+    unsigned mpk;              // canonical hits of fitted slot j in bits 4j .. 4j + 3
+    unsigned ra, rb, rc, re;   // the slots in roles a, b, c, e
+    unsigned ma, mb, mc, me;   // their canonical hits
+    unsigned ne;               // raw hits of the excluded layer
+    unsigned long long cb;     // plain mode: first combination of the road
+    __device__ unsigned m(unsigned s) const { return (mpk >> (4 * s)) & 15u; }
+};
+
+// One pass over the pairs (x, y) of slots a and b: lane t = 32 p + lane.
+// DUP: the road has repeated coordinates (passing counts are weighted by the
+// raw fits each canonical fit stands for).
+template <bool PLAIN, bool DUP>
+__device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p, unsigned &np)
+{
+    const unsigned lane = lane_id();
+    const unsigned ma = sh.ma, mb = sh.mb, mc = sh.mc, me = sh.me;
+    const unsigned t = p * 32 + lane;
+    const bool act = t < ma * mb;
+    const unsigned y = act ? divm(t, c_magic[ma]) : 0u, x = act ? t - y * ma : 0u;
+    const int4 pab = add4(B.A[sh.ra][x], B.A[sh.rb][y]);
+    const unsigned wab = DUP ? (unsigned)B.mult[sh.ra][x] * B.mult[sh.rb][y] : 1u;
+    const long long cut = d.cut;
+    unsigned long long qab = NO_KEY, rw[MAX_HITS];
+#pragma unroll
+    for (unsigned w = 0; w < MAX_HITS; ++w)
+        rw[w] = NO_KEY;
+    for (unsigned z = 0; z < mc; ++z) {
+        const int4 pz = add4(pab, B.A[sh.rc][z]);
+        const unsigned wz = DUP ? wab * B.mult[sh.rc][z] : 1u;
+        unsigned long long rz = NO_KEY;
+#pragma unroll
+        for (unsigned w = 0; w < MAX_HITS; ++w) {
+            if (w < me) {
+                const int4 s = add4(pz, B.A[sh.re][w]);
+                unsigned long long key;
+                if (PLAIN) {
+                    key = act ? ldcg(d.fit_key + sh.cb + (unsigned)s.w) : NO_KEY;
+                } else {
+                    bool pass;
+                    key = box_key(s, cut, pass);
+                    if (!act)
+                        key = NO_KEY;
+                    if (act && pass)
+                        np += DUP ? wz * B.mult[sh.re][w] : 1u;
+                }
+                rz = umin64(rz, key);
+                rw[w] = umin64(rw[w], key);
+                // T_ce at (z, w): the minimum over the lanes, high word first
+                const unsigned hi = (unsigned)(key >> 32);
+                const unsigned mh = __reduce_min_sync(FULL_MASK, hi);
+                const unsigned ml = __reduce_min_sync(FULL_MASK, hi == mh ? (unsigned)key : 0xFFFFFFFFu);
+                if (lane == 0)
+                    B.TB[p][z * 8 + w] = ((unsigned long long)mh << 32) | ml;
+            }
+        }
+        qab = umin64(qab, rz);
+        if (act) {
+            atomicMin(&B.T[T_AC][x * 8 + z], rz);
+            atomicMin(&B.T[T_BC][y * 8 + z], rz);
+        }
+    }
+    if (act) {
+        B.T[T_AB][x * 8 + y] = qab;
+#pragma unroll
+        for (unsigned w = 0; w < MAX_HITS; ++w)
+            if (w < me) {
+                atomicMin(&B.T[T_AE][x * 8 + w], rw[w]);
+                atomicMin(&B.T[T_BE][y * 8 + w], rw[w]);
+            }
+    }
+}
+
+// the table holding the minima over slots p and q (p != q) and the index of
+// canonical hits (kp, kq) in it
+__device__ __forceinline__ unsigned box_tab(const BoxShape &sh, unsigned p, unsigned kp, unsigned q, unsigned kq,
+                                            unsigned &idx)
+{
+    const auto role = [&sh](unsigned s) {
+        return s == sh.ra ? 0u : s == sh.rb ? 1u : s == sh.rc ? 2u : 3u;
+    };
+    unsigned r1 = role(p), r2 = role(q), k1 = kp, k2 = kq;
+    if (r1 > r2) {
+        const unsigned tr = r1, tk = k1;
+        r1 = r2;
+        k1 = k2;
+        r2 = tr;
+        k2 = tk;
+    }
+    idx = k1 * 8 + k2;
+    // role pairs (0,1) ab, (2,3) ce, (0,2) ac, (1,2) bc, (0,3) ae, (1,3) be
+    return r1 == 0 && r2 == 1 ? T_AB : r1 == 2 ? T_CE : r2 == 2 ? (r1 == 0 ? T_AC : T_BC) : (r1 == 0 ? T_AE : T_BE);
+}
+
+// Fit road g with one warp (see above); adds its passing combinations to npass.
+template <bool PLAIN>
+__device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsigned long long &npass)
+{
+    P3Box &B = *reinterpret_cast<P3Box *>(region);
+    const unsigned lane = lane_id();
+    const RoadRec rec = ldcg(d.roads + g);
+    const uint32_t pk = rec.pk;
+    const unsigned excl = min((pk >> 20) & 7u, 4u);
+    __syncwarp();   // the region's previous user is done
+    if (lane < N_LAYERS)   // 80 bytes of coordinates, five 16-byte words
+        reinterpret_cast<uint4 *>(B.co)[lane] = ldcg(reinterpret_cast<const uint4 *>(d.coords + (size_t)g * 40) + lane);
+    for (unsigned i = lane; i < N_TAB * 64; i += 32)
+        (&B.T[0][0])[i] = NO_KEY;
+    __syncwarp();
+
+    // lane 8 j + h: raw hit h of fitted slot j.  Canonical hits, their ranks
+    // and multiplicities, and the partial sums of the canonical hits.
+    const unsigned j = lane >> 3, h = lane & 7u;
+    const unsigned L = j + (j >= excl);
+    const unsigned nj = hits_of(pk, L);
+    const bool valid = h < nj;
+    unsigned cls = h;   // the lowest index with the same coordinate
+    if (valid) {
+        const unsigned v = B.co[L * 8 + h];
+        for (unsigned x = h; x-- > 0;)
+            cls = B.co[L * 8 + x] == v ? x : cls;
+    }
+    const bool canon = valid && cls == h;
+    const unsigned cm = __ballot_sync(FULL_MASK, canon);
+    const bool dup = __ballot_sync(FULL_MASK, valid) != cm;
+    const unsigned mine = (cm >> (8 * j)) & 0xFFu;
+    const unsigned same = __match_any_sync(FULL_MASK, valid ? j * 8 + cls : 32u + lane);
+    const unsigned k = __popc(mine & ((1u << h) - 1u));
+    if (valid)
+        B.rank[j][h] = (uint8_t)__popc(mine & ((1u << cls) - 1u));
+    BoxShape sh;
+    sh.mpk = 0;
+#pragma unroll
+    for (unsigned s = 0; s < 4; ++s)
+        sh.mpk |= (unsigned)__popc((cm >> (8 * s)) & 0xFFu) << (4 * s);
+    sh.ne = hits_of(pk, excl);
+    sh.cb = PLAIN ? ldcg(d.comb_off + g) : 0ull;
+    if (canon) {
+        unsigned SL = 1;   // comb stride of layer L
+        for (unsigned l = 0; l < L; ++l)
+            SL *= hits_of(pk, l);
+        B.raw[j][k] = (uint8_t)h;
+        B.mult[j][k] = (uint8_t)__popc(same);
+        int4 a = make_int4(0, 0, 0, (int)(h * SL));
+        if (!PLAIN) {
+            const int4 *cc = d.fitc + SET_INT4 * min((unsigned)rec.set, (unsigned)(N_SETS - 1)) + SET_C;
+            const int4 cj = __ldg(cc + j);
+            const int hv = B.co[L * 8 + h];
+            a.x = cj.x * hv;
+            a.y = cj.y * hv;
+            a.z = cj.z * hv;
+            if (j == 0) {   // curvature, phi, 4096 * offset and the road bits ride on slot 0
+                const int4 c4 = __ldg(cc + 4), c5 = __ldg(cc + 5), kk = __ldg(cc + 6);
+                a.x += c4.x * rec.curv + c5.x * rec.phi + 4096 * kk.x;
+                a.y += c4.y * rec.curv + c5.y * rec.phi + 4096 * kk.y;
+                a.z += c4.z * rec.curv + c5.z * rec.phi + 4096 * kk.z;
+                a.w += (int)((pk >> 24) << 15);
+            }
+        }
+        B.A[j][k] = a;
+    }
+    // roles: the pair (a, b) that needs the fewest lane steps, then c before
+    // e with e (the unrolled inner loop) the larger
+    {
+        const unsigned n4 = sh.m(0) * sh.m(1) * sh.m(2) * sh.m(3);
+        unsigned best = ~0u, ba = 0, bb = 1;
+#pragma unroll
+        for (unsigned q = 0; q < 6; ++q) {
+            const unsigned pa = pair_a(q), pb = pair_b(q);
+            const unsigned prod = sh.m(pa) * sh.m(pb);
+            const unsigned cost = (prod + 31) / 32 * (n4 / prod);
+            if (cost < best) {
+                best = cost;
+                ba = pa;
+                bb = pb;
+            }
+        }
+        const unsigned rest = 0xFu & ~(1u << ba) & ~(1u << bb);
+        const unsigned r0 = __ffs(rest) - 1, r1 = 31 - __clz(rest);
+        const bool sw = sh.m(r0) > sh.m(r1);
+        sh.ra = ba;
+        sh.rb = bb;
+        sh.rc = sw ? r1 : r0;
+        sh.re = sw ? r0 : r1;
+        sh.ma = sh.m(sh.ra);
+        sh.mb = sh.m(sh.rb);
+        sh.mc = sh.m(sh.rc);
+        sh.me = sh.m(sh.re);
+    }
+    __syncwarp();
+
+    // the loop over the box: all six tables
+    const unsigned ma = sh.ma, mb = sh.mb, mc = sh.mc, me = sh.me;
+    const unsigned passes = (ma * mb + 31) / 32;   // 1 or 2
+    unsigned np = 0;
+    for (unsigned p = 0; p < passes; ++p) {
+        if (dup)
+            box_pass<PLAIN, true>(d, B, sh, p, np);
+        else
+            box_pass<PLAIN, false>(d, B, sh, p, np);
+    }
+    __syncwarp();
+    for (unsigned i = lane; i < 64; i += 32) {
+        const unsigned z = i >> 3, w = i & 7u;
+        if (z < mc && w < me)
+            B.T[T_CE][i] = passes > 1 ? umin64(B.TB[0][i], B.TB[1][i]) : B.TB[0][i];
+    }
+    __syncwarp();
+    if (!PLAIN)
+        npass += (unsigned long long)np * sh.ne;
+
+    // road-local survivors: the minimum of pair (x, y) survives iff it is
+    // also the minimum of its other five tables
+    unsigned long long sk[2] = {NO_KEY, NO_KEY};
+    bool sv[2] = {false, false};
+#pragma unroll
+    for (unsigned p = 0; p < 2; ++p) {
+        const unsigned t = p * 32 + lane;
+        if (p < passes && t < ma * mb) {
+            const unsigned y = divm(t, c_magic[ma]), x = t - y * ma;
+            const unsigned long long key = B.T[T_AB][x * 8 + y];
+            if (key != NO_KEY) {
+                // raw hits of the layers of slots c and e from the comb
+                unsigned rest = (unsigned)(key & 0x7FFFu), dc = 0, de = 0;
+                const unsigned Lc = sh.rc + (sh.rc >= excl), Le = sh.re + (sh.re >= excl);
+#pragma unroll
+                for (unsigned l = 0; l < N_LAYERS; ++l) {
+                    const unsigned n = max(hits_of(pk, l), 1u);
+                    const unsigned q = divm(rest, c_magic[n]);
+                    const unsigned dl = rest - q * n;
+                    rest = q;
+                    dc = l == Lc ? dl : dc;
+                    de = l == Le ? dl : de;
+                }
+                const unsigned z = B.rank[sh.rc][dc], w = B.rank[sh.re][de];
+                sv[p] = B.T[T_CE][z * 8 + w] == key && B.T[T_AC][x * 8 + z] == key &&
+                        B.T[T_BC][y * 8 + z] == key && B.T[T_AE][x * 8 + w] == key &&
+                        B.T[T_BE][y * 8 + w] == key;
+                sk[p] = key;
+            }
+        }
+    }
+    // survivors in comb order: each finds its rank among the others
+    const unsigned s0 = __ballot_sync(FULL_MASK, sv[0]), s1 = __ballot_sync(FULL_MASK, sv[1]);
+    const unsigned n_surv = __popc(s0) + __popc(s1);
+    unsigned rk[2] = {0u, 0u};
+    const unsigned my0 = (unsigned)(sk[0] & 0x7FFFu), my1 = (unsigned)(sk[1] & 0x7FFFu);
+    for (unsigned q = 0; q < 2; ++q) {
+        for (unsigned bits = q ? s1 : s0; bits; bits &= bits - 1) {
+            const unsigned src = __ffs(bits) - 1;
+            const unsigned other = __shfl_sync(FULL_MASK, q ? my1 : my0, src);
+            rk[0] += other < my0;
+            rk[1] += other < my1;
+        }
+    }
+#pragma unroll
+    for (unsigned p = 0; p < 2; ++p)
+        if (sv[p])
+            d.surv_pool[surv_at(d, g, rk[p])] = sk[p];
+    if (lane == 0) {
+        d.surv_cnt[g] = (uint8_t)n_surv;
+        if (n_surv)
+            atomicAdd(&d.rchunk_sum[g / ROAD_CHUNK], n_surv);
+    }
+
+    // cross-road candidates: the minimum key of every group (layer triple,
+    // three coordinates) whose three hits are canonical and flagged as
+    // present in another road of the event
+    if ((pk >> 23) & 1u) {
+        // canonical hits of the excluded layer (lanes 0..7)
+        unsigned xc = lane;
+        const bool xv = lane < sh.ne;
+        if (xv) {
+            const unsigned v = B.co[excl * 8 + lane];
+            for (unsigned x = lane; x-- > 0;)
+                xc = B.co[excl * 8 + x] == v ? x : xc;
+        }
+        const unsigned cmx = __ballot_sync(FULL_MASK, xv && xc == lane) & 0xFFu;
+        const unsigned long long xm = ldcg(d.xmask + g);
+        unsigned long long flp = 0;
+#pragma unroll
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned cl = l == excl ? cmx : (cm >> (8 * (l - (l > excl)))) & 0xFFu;
+            flp |= (unsigned long long)((unsigned)(xm >> (8 * l)) & cl) << (8 * l);
+        }
+        const auto fl = [flp](unsigned l) { return (unsigned)(flp >> (8 * l)) & 0xFFu; };
+        const auto groups = [&fl](unsigned t) {
+            return __popc(fl(triple_l(t, 0))) * __popc(fl(triple_l(t, 1))) * __popc(fl(triple_l(t, 2)));
+        };
+        unsigned total = 0;
+#pragma unroll
+        for (unsigned t = 0; t < 10; ++t)
+            total += groups(t);
+        unsigned Se = 1;   // comb stride of the excluded layer
+        for (unsigned l = 0; l < excl; ++l)
+            Se *= hits_of(pk, l);
+        for (unsigned gi = lane; gi < total; gi += 32) {
+            unsigned t = 0, rem = gi;
+            bool found = false;
+#pragma unroll
+            for (unsigned tt = 0; tt < 10; ++tt) {
+                const unsigned c = groups(tt);
+                if (!found) {
+                    if (rem < c) {
+                        t = tt;
+                        found = true;
+                    } else {
+                        rem -= c;
+                    }
+                }
+            }
+            const unsigned lt[3] = {triple_l(t, 0), triple_l(t, 1), triple_l(t, 2)};
+            const unsigned f0 = fl(lt[0]), f1 = fl(lt[1]), f2 = fl(lt[2]);
+            const unsigned p0 = __popc(f0), p1 = __popc(f1);
+            const unsigned dsel[3] = {nth_bit(f0, rem % p0), nth_bit(f1, (rem / p0) % p1),
+                                      nth_bit(f2, rem / (p0 * p1))};
+            unsigned long long mn = NO_KEY;
+            if (lt[0] != excl && lt[1] != excl && lt[2] != excl) {
+                // three fitted slots fixed; the fourth runs over its canonical hits
+                int4 base = make_int4(0, 0, 0, 0);
+                unsigned free_slot = 0 + 1 + 2 + 3;
+#pragma unroll
+                for (unsigned q = 0; q < 3; ++q) {
+                    const unsigned s = lt[q] - (lt[q] > excl);
+                    free_slot -= s;
+                    base = add4(base, B.A[s][B.rank[s][dsel[q]]]);
+                }
+                for (unsigned z = 0; z < sh.m(free_slot); ++z) {
+                    const int4 s = add4(base, B.A[free_slot][z]);
+                    unsigned long long key;
+                    if (PLAIN) {
+                        key = ldcg(d.fit_key + sh.cb + (unsigned)s.w);
+                    } else {
+                        bool pass;
+                        key = box_key(s, d.cut, pass);
+                    }
+                    mn = umin64(mn, key);
+                }
+            } else {
+                // the excluded layer in the triple: the pair table of the two
+                // fitted slots, then the excluded hit's comb
+                unsigned de = 0, sa = 4, sb = 4, da = 0, db = 0;
+#pragma unroll
+                for (unsigned q = 0; q < 3; ++q) {
+                    if (lt[q] == excl) {
+                        de = dsel[q];
+                    } else if (sa == 4) {
+                        sa = lt[q] - (lt[q] > excl);
+                        da = dsel[q];
+                    } else {
+                        sb = lt[q] - (lt[q] > excl);
+                        db = dsel[q];
+                    }
+                }
+                unsigned idx;
+                const unsigned tab = box_tab(sh, sa, B.rank[sa][da], sb, B.rank[sb][db], idx);
+                mn = B.T[tab][idx];
+                if (mn != NO_KEY)
+                    mn += (unsigned long long)de * Se;
+            }
+            if (mn != NO_KEY)
+                hash_min(d, group_key(rec.event, t, B.co[lt[0] * 8 + dsel[0]], B.co[lt[1] * 8 + dsel[1]],
+                                      B.co[lt[2] * 8 + dsel[2]]),
+                         mn);
+        }
+    }
+    __syncwarp();
+}
+
+static_assert(sizeof(P3Box) <= P3_WARP_BYTES, "the box path uses a warp's region of the flat path");
+
 // The roads listed in P2 (more than small_n4 distinct fits, or a cross-road
-// candidate with a repeated coordinate) are fitted by a whole CTA; then every
-// warp takes runs of WARP_ROADS consecutive roads and fits the others itself
-// (fit_run).
+// candidate with a repeated coordinate) are fitted first, one warp each
+// (box_road); then every warp takes runs of WARP_ROADS consecutive roads and
+// fits the others itself (fit_run).  Each warp works in its own region of
+// shared memory, so no stage of P3 waits for the whole CTA.
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
     const unsigned n_big = min(ldcg(&d.ctrl->n_big), d.max_roads);
     const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
     unsigned long long npass = 0;
-    {
-        P3Big &s = *reinterpret_cast<P3Big *>(smem);
-        BlockGroup grp{s.cnt};
-        RoadSmem sm{s.A, s.co, &s.cs, s.canon, s.Q, s.K, s.S};
-        uint32_t *cst = reinterpret_cast<uint32_t *>(&s.cs);
-        for (unsigned i = blockIdx.x; i < n_big; i = grab_after_first(d, qbig)) {
-            const unsigned g = min(ldcg(d.big_list + i), d.max_roads - 1);
-            if (threadIdx.x < 40)
-                s.co[threadIdx.x] = ldcg(d.coords + (size_t)g * 40 + threadIdx.x);
-            const RoadRec rec = ldcg(d.roads + g);
-            if (threadIdx.x < CONST_WORDS)
-                cst[threadIdx.x] = __ldg(const_words(d, rec.set) + threadIdx.x);
-            __syncthreads();
-            fit_road<BlockGroup, PLAIN>(d, grp, sm, g, rec, npass);
-        }
+    unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
+    // a warp's first item of each queue is its own index; the queue hands out the rest
+    const unsigned n_warps = gridDim.x * WARPS;
+    for (unsigned i = blockIdx.x * WARPS + warp_id(); i < n_big;) {
+        box_road<PLAIN>(d, region, min(ldcg(d.big_list + i), d.max_roads - 1), npass);
+        unsigned ni = 0;
+        if (lane_id() == 0)
+            ni = n_warps + atomicAdd(&d.ctrl->q[qbig], 1u);
+        i = __shfl_sync(FULL_MASK, ni, 0);
     }
-    __syncthreads();
+    __syncwarp();
     {
-        unsigned char *region = smem + warp_id() * P3_WARP_BYTES;
         const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
-        // a warp's first run is its own index; the queue hands out the rest
-        const unsigned n_warps = gridDim.x * WARPS;
         for (unsigned c = blockIdx.x * WARPS + warp_id(); c < n_runs;) {
             const unsigned g0 = c * WARP_ROADS;
             fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
@@ -2357,25 +2403,27 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_
 
 // P4 of the persistent kernel: the cross-road hit-warrior over the
 // candidate roads only (P2 sets their bits; the others keep their
-// survivors).  A road that loses survivors takes them off its chunk's total.
+// survivors).  One warp per word of candidate bits, one lane per road, so
+// every candidate road checks its survivors at once; bit word w goes to CTA
+// w % grid, so that a few candidates are spread out.  A road that loses
+// survivors takes them off its chunk's total.
 __device__ void p4_cand_phase(const Dev &d)
 {
     const unsigned n_roads = min(ldcg(&d.ctrl->n_roads), d.max_roads);
     const unsigned n_words = (n_roads + 31) / 32;
-    // bit word w goes to CTA w % grid: the few candidates are spread out
-    for (unsigned w = threadIdx.x * gridDim.x + blockIdx.x; w < n_words; w += gridDim.x * BLOCK) {
-        for (unsigned bits = ldcg(d.cand_bits + w); bits; bits &= bits - 1) {
-            const unsigned g = w * 32 + (unsigned)(__ffs(bits) - 1);
-            if (g >= n_roads)
-                continue;   // a road of the truncated tail: not fitted
-            const unsigned cnt = ldcg(d.surv_cnt + g);
-            if (!cnt)
-                continue;
-            const unsigned kept = cross_check(d, g, cnt);
-            if (kept != cnt) {
-                d.surv_cnt[g] = (uint8_t)kept;
-                atomicSub(&d.rchunk_sum[g / ROAD_CHUNK], cnt - kept);
-            }
+    const unsigned lane = lane_id();
+    for (unsigned w = warp_id() * gridDim.x + blockIdx.x; w < n_words; w += gridDim.x * WARPS) {
+        const unsigned bits = ldcg(d.cand_bits + w);
+        const unsigned g = w * 32 + lane;
+        if (!((bits >> lane) & 1u) || g >= n_roads)
+            continue;   // not a candidate, or a road of the truncated tail (not fitted)
+        const unsigned cnt = ldcg(d.surv_cnt + g);
+        if (!cnt)
+            continue;
+        const unsigned kept = cross_check(d, g, cnt);
+        if (kept != cnt) {
+            d.surv_cnt[g] = (uint8_t)kept;
+            atomicSub(&d.rchunk_sum[g / ROAD_CHUNK], cnt - kept);
         }
     }
 }
@@ -2786,11 +2834,7 @@ __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
 // ---------------------------------------------------------------------------
 
 static size_t p2_smem() { return sizeof(P2Smem); }
-static size_t p3_smem()
-{
-    size_t a = sizeof(P3Big), b = WARPS * P3_WARP_BYTES;
-    return a > b ? a : b;
-}
+static size_t p3_smem() { return WARPS * P3_WARP_BYTES; }
 
 static_assert(sizeof(P5Smem) <= WARPS * P3_WARP_BYTES, "the output stage needs no more shared memory than the fit");
 
