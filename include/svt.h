@@ -91,7 +91,9 @@ typedef struct {
     uint32_t max_events;     /* events per batch           (default 1 << 16) */
     uint32_t max_roads;      /* roads per batch            (default 1 << 20) */
     uint64_t max_tracks;     /* surviving tracks per batch (default 1 << 22) */
-    uint32_t hash_slots;     /* cross-road group table, power of 2 (default 1 << 22) */
+    uint32_t hash_slots;     /* cross-road group table, power of 2 (default 1 << 22); a batch
+                                may fill 3/4 of it, each group within 64 slots of its home
+                                slot, else SVT_E_CAPACITY */
     uint32_t pad;
     uint64_t max_combinations; /* SVT_PLAIN per-combination buffers (default 1 << 26) */
 } svt_limits;
@@ -104,7 +106,7 @@ typedef struct {
     uint64_t n_passing;       /* combinations with chi2 <= cut */
     uint64_t n_tracks;        /* survivors of the hit-warrior */
     int32_t status;           /* SVT_OK or the batch's error code */
-    uint32_t pad;
+    uint32_t n_groups;        /* distinct cross-road groups published to the group table */
     uint64_t error_word;      /* word position of the first fault (if any) */
     uint64_t phase_ns[6];     /* SVT_PERSISTENT: device time of each stage, from the
                                  first CTA's view of the grid barriers: word scan,
@@ -205,9 +207,12 @@ int svt_autotune(svt_ctx *ctx, int reps, svt_tune_point *points, uint32_t cap, u
 int svt_use_graph(svt_ctx *ctx, int enable);
 
 /* Test hook: spin limit of device-side waits in microseconds (0 = default of
- * two seconds) and, when skip_arrival is 1, block 0 of the next persistent
- * launch leaves before its first grid barrier so the others' waits run out
- * and the batch ends with SVT_E_TIMEOUT.  Never faults or hangs the device. */
+ * two seconds) and, for the next SVT_PERSISTENT launch only (a direct launch,
+ * never a graph), skip_arrival = 1: block 0 leaves before its first grid
+ * barrier; 2: block 0 leaves after the fit stage, when the cross-road group
+ * table has been filled.  The others' waits run out and the batch ends with
+ * SVT_E_TIMEOUT; the next svt_fit_events clears the group table first.
+ * 0 = no early exit.  Never faults or hangs the device. */
 int svt_debug_wait(svt_ctx *ctx, uint32_t wait_limit_us, int skip_arrival);
 
 /* Number of kernels the last svt_fit_events enqueued (for launch accounting). */
@@ -224,16 +229,22 @@ const char *svt_strerror(int code);
  * svt_run_static runs SVT_PERSISTENT on one batch over a scratch arena that
  * is a fixed-size __device__ array of the library (under 8 MB per device),
  * not a context: it allocates nothing.  Limits: 131072 words, 1024 events,
- * 8192 roads (SVT_E_CAPACITY beyond; n_words is checked before any work).
+ * 8192 roads, and a cross-road group table of 32768 slots (filled to 3/4 at
+ * most); SVT_E_CAPACITY beyond any of them (n_words is checked before any
+ * work, the others on the device).
  * d_words: the batch on the device (4-byte aligned); sets: the 360 constant
  * sets in HOST memory (same admission rule as svt_load_constants); d_tracks:
  * caller-owned DEVICE buffer of `cap` records (8-byte aligned) that receives
- * the tracks in (event, road, comb) order; *n_out (HOST) = number of tracks
- * (with SVT_E_CAPACITY, the number that did not fit `cap`).  Synchronises
- * `stream`.  The first call on a device does its setup (looks up the arena,
- * clears its group table, sets the kernel's shared-memory limit), so it must
- * come before any stream capture; there is one arena per device, so calls
- * that overlap in time (threads or streams with work in flight) race on it. */
+ * the tracks in (event, road, comb) order; *n_out (HOST) = number of tracks.
+ * With SVT_E_CAPACITY because the tracks did not fit `cap`, *n_out is their
+ * number (larger than cap) and nothing is written; with SVT_E_CAPACITY from
+ * an arena limit, *n_out = 0.
+ * The call synchronises `stream`, so it must never be called on a stream
+ * that is being captured into a graph (SVT_E_INVAL).  Every call looks up the
+ * arena on the current device; the first call on a device clears the
+ * arena's group table and sets the kernel's shared-memory limit.  There is
+ * one arena per device, so calls that overlap in time (threads or streams
+ * with work in flight) race on it. */
 int svt_run_static(const uint32_t *d_words, size_t n_words, const svt_const_set *sets,
                    uint32_t n_sets, int64_t chi2_cut, svt_track *d_tracks, size_t cap,
                    size_t *n_out, void *stream);

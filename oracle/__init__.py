@@ -15,7 +15,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "svt_oracle.c")
+_SRCS = [os.path.join(_HERE, "svt_oracle.c"), os.path.join(_HERE, "svt_oracle_mt.c")]
 _LIB = os.path.join(_HERE, "libsvt_oracle.so")
 
 OK, E_BADWORD, E_TRUNCATED, E_LIMIT, E_NOMEM = 0, -2, -3, -4, -8
@@ -36,14 +36,20 @@ assert FIT_DTYPE.itemsize == 48
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/libsvt_oracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "svt_oracle.h"))):
+    """Compile the oracle with gcc (OpenMP for the event-parallel driver)
+    into oracle/libsvt_oracle.so."""
+    deps = _SRCS + [os.path.join(_HERE, "svt_oracle.h")]
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(map(os.path.getmtime, deps)):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra",
-                               "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra", "-fopenmp",
+                               "-fPIC", "-shared", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+class _Times(C.Structure):
+    _fields_ = [("unpack", C.c_double), ("fit", C.c_double), ("warrior", C.c_double),
+                ("wall", C.c_double), ("threads", C.c_int32), ("pad", C.c_int32)]
 
 
 class _Consts(C.Structure):
@@ -67,8 +73,10 @@ def lib():
                                       C.POINTER(C.c_void_p), C.POINTER(sz)]
         _lib.orc_run.argtypes = [C.c_void_p, sz, C.POINTER(_Consts), C.c_int64, C.c_int,
                                  C.POINTER(C.c_void_p), C.POINTER(sz)]
+        _lib.orc_run_mt.argtypes = [C.c_void_p, sz, C.POINTER(_Consts), C.c_int64, C.c_int, C.c_int,
+                                    C.POINTER(C.c_void_p), C.POINTER(sz), C.POINTER(_Times)]
         _lib.orc_free.argtypes = [C.c_void_p]
-        for f in ("orc_unpack", "orc_fit_all", "orc_chi2_all", "orc_run"):
+        for f in ("orc_unpack", "orc_fit_all", "orc_chi2_all", "orc_run", "orc_run_mt"):
             getattr(_lib, f).restype = C.c_int
     return _lib
 
@@ -139,3 +147,17 @@ def run(words, consts: dict, cut: int, warrior: int = 1):
     rc = lib().orc_run(w.ctypes.data, len(w), C.byref(h.s), int(cut), int(warrior),
                        C.byref(p), C.byref(n))
     return rc, _take(p, n.value, FIT_DTYPE)
+
+
+def run_mt(words, consts: dict, cut: int, warrior: int = 1, threads: int = 0):
+    """The whole chain with the events spread over host threads (OpenMP, one
+    event per thread at a time): -> (status, survivors, times) where times =
+    {"threads", "unpack_s", "fit_s", "warrior_s", "wall_s"} (fit and warrior
+    summed over the threads).  Output identical to run()."""
+    w, h = _words(words), _Held(consts)
+    p, n, t = C.c_void_p(), C.c_size_t(), _Times()
+    rc = lib().orc_run_mt(w.ctypes.data, len(w), C.byref(h.s), int(cut), int(warrior), int(threads),
+                          C.byref(p), C.byref(n), C.byref(t))
+    times = {"threads": t.threads, "unpack_s": t.unpack, "fit_s": t.fit, "warrior_s": t.warrior,
+             "wall_s": t.wall}
+    return rc, _take(p, n.value, FIT_DTYPE), times

@@ -482,6 +482,62 @@ int orc_run(const uint32_t *words, size_t n_words, const orc_consts *c,
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* one event at a time (the event-parallel driver, svt_oracle_mt.c, calls     */
+/* these; they take the same steps as orc_run's loop over one event)          */
+/* ------------------------------------------------------------------------ */
+
+int orc_event_fits(const orc_road *roads, size_t n_roads, const orc_consts *c, int64_t cut,
+                   orc_fit **passing, size_t *n_passing)
+{
+    fit_vec all = {0, 0, 0}, pass = {0, 0, 0};
+    int rc = ORC_OK;
+    *passing = NULL;
+    *n_passing = 0;
+    for (size_t r = 0; rc == ORC_OK && r < n_roads; ++r)
+        rc = combine_and_fit(&roads[r], c, cut, &all);
+    for (size_t i = 0; rc == ORC_OK && i < all.n; ++i)
+        if (all.v[i].pass)
+            rc = fv_push(&pass, &all.v[i]);
+    free(all.v);
+    if (rc) {
+        free(pass.v);
+        return rc;
+    }
+    *passing = pass.v;
+    *n_passing = pass.n;
+    return ORC_OK;
+}
+
+int orc_event_warrior(const orc_fit *passing, size_t n, int warrior, orc_fit **out, size_t *n_out)
+{
+    fit_vec result = {0, 0, 0};
+    char *dropped = (char *)malloc(n ? n : 1);
+    int rc = ORC_OK;
+    *out = NULL;
+    *n_out = 0;
+    if (!dropped)
+        return ORC_E_NOMEM;
+    if (warrior == 0)
+        warrior_pairwise(passing, n, dropped);
+    else if (warrior == 1)
+        rc = warrior_projection(passing, n, dropped);
+    else
+        for (size_t i = 0; i < n; ++i)
+            dropped[i] = 0;
+    for (size_t i = 0; rc == ORC_OK && i < n; ++i)
+        if (!dropped[i])
+            rc = fv_push(&result, &passing[i]);
+    free(dropped);
+    if (rc) {
+        free(result.v);
+        return rc;
+    }
+    *out = result.v;
+    *n_out = result.n;
+    return ORC_OK;
+}
+
 void orc_free(void *p)
 {
     free(p);

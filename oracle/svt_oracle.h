@@ -113,6 +113,30 @@ int orc_run(const uint32_t *words, size_t n_words, const orc_consts *c,
 
 void orc_free(void *p);
 
+/* One event: every combination of its roads (roads[0..n_roads), all of one
+ * event, as orc_unpack returns them), fitted; the passing ones in canonical
+ * order -> *passing (malloc'ed). */
+int orc_event_fits(const orc_road *roads, size_t n_roads, const orc_consts *c, int64_t cut,
+                   orc_fit **passing, size_t *n_passing);
+
+/* The hit-warrior over one event's passing combinations (warrior as in
+ * orc_run); the survivors in order -> *out (malloc'ed). */
+int orc_event_warrior(const orc_fit *passing, size_t n, int warrior, orc_fit **out, size_t *n_out);
+
+/* Host time of each stage of orc_run_mt, in seconds.  fit and warrior are
+ * summed over the threads (CPU time of the stage); wall is the whole call. */
+typedef struct {
+    double unpack, fit, warrior, wall;
+    int32_t threads;          /* threads of the event loop */
+    int32_t pad;
+} orc_times;
+
+/* The chain of orc_run with the events spread over host threads (OpenMP, one
+ * event at a time per thread; svt_oracle_mt.c).  n_threads <= 0: every core
+ * OpenMP offers.  Output identical to orc_run.  times may be NULL. */
+int orc_run_mt(const uint32_t *words, size_t n_words, const orc_consts *c, int64_t cut,
+               int warrior, int n_threads, orc_fit **out, size_t *n_out, orc_times *times);
+
 #ifdef __cplusplus
 }
 #endif

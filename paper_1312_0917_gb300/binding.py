@@ -44,11 +44,11 @@ class Limits(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n_events", C.c_uint64), ("n_roads", C.c_uint64),
                 ("n_combinations", C.c_uint64), ("n_passing", C.c_uint64),
-                ("n_tracks", C.c_uint64), ("status", C.c_int32), ("pad", C.c_uint32),
+                ("n_tracks", C.c_uint64), ("status", C.c_int32), ("n_groups", C.c_uint32),
                 ("error_word", C.c_uint64), ("phase_ns", C.c_uint64 * 6)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad", "phase_ns")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ns"}
         d["phase_ns"] = list(self.phase_ns)
         return d
 
@@ -237,7 +237,9 @@ class Context:
     def use_graph(self, enable: bool = True):
         check(lib().svt_use_graph(self._h, int(enable)), "svt_use_graph")
 
-    def debug_wait(self, wait_limit_us: int = 0, skip_arrival: bool = False):
+    def debug_wait(self, wait_limit_us: int = 0, skip_arrival: int = 0):
+        """skip_arrival: 0 none, 1 block 0 leaves before the first grid
+        barrier, 2 after the fit stage (next persistent launch only)."""
         check(lib().svt_debug_wait(self._h, wait_limit_us, int(skip_arrival)), "svt_debug_wait")
 
     def last_launch_count(self) -> int:

@@ -4,6 +4,8 @@
 #pragma once
 #include "svt_internal.h"
 
+#include <cstdlib>
+
 struct svt_ctx {
     int device = 0;
     svt_limits lim{};
@@ -33,6 +35,53 @@ struct svt_ctx {
 };
 
 namespace svt {
+
+// Bound on |sum_j coef_j x_j + 4096 offset| over every admissible input: hits
+// are at most 4095, curvature and phi at most 32768 in magnitude.
+inline long long bound_row(const int16_t *coef, int32_t off)
+{
+    long long b = 0;
+    for (int j = 0; j < 6; ++j)
+        b += (long long)std::llabs(coef[j]) * (j < 4 ? 4095 : 32768);
+    return b + 4096ll * std::llabs((long long)off);
+}
+
+// The admission rule of constant sets (svt_load_constants, svt_run_static):
+// every row's bound below 2^31 (the fit's 32-bit sums are exact) and the
+// chi-square bound below 2^38 (the track key's 61 bits).
+inline bool constants_admissible(const svt_const_set *sets)
+{
+    for (int s = 0; s < N_SETS; ++s) {
+        long long chi_bound = 0;
+        for (int k = 0; k < 3; ++k) {
+            const long long bf = bound_row(sets[s].F[k], sets[s].q[k]);
+            const long long bc = bound_row(sets[s].C[k], sets[s].k[k]);
+            if (bf >= (1ll << 31) || bc >= (1ll << 31))
+                return false;
+            const long long a = bc / 4096 + 1;
+            chi_bound += a * a;
+        }
+        if (chi_bound >= (1ll << 38))
+            return false;
+    }
+    return true;
+}
+
+// Status of a batch from its control block (after the kernels).
+inline int status_of(const Ctrl &c)
+{
+    if (c.flags & FLAG_TIMEOUT)
+        return SVT_E_TIMEOUT;
+    if (c.flags & FLAG_CAPACITY)
+        return SVT_E_CAPACITY;
+    if (c.err_inv != 0ull) {
+        unsigned rank = (unsigned)(~c.err_inv & 0xFFull);
+        return rank == RANK_BAD ? SVT_E_BADWORD : rank == RANK_LIMIT ? SVT_E_LIMIT : SVT_E_TRUNCATED;
+    }
+    if (c.flags & FLAG_INTERNAL)
+        return SVT_E_CUDA;
+    return SVT_OK;
+}
 
 // Enqueue one batch of the words bound to c (control block reset, kernels)
 // on s; adds the kernel launches to *launches.

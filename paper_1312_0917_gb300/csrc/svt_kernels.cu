@@ -603,6 +603,10 @@ struct P2Smem {
     uint16_t coord[MAX_ROADS_EV][40];     // [road][layer * 8 + hit]
     uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
     uint32_t multi[N_LAYERS][128];
+    uint32_t sig[MAX_ROADS_EV][N_LAYERS]; // per road and layer: 32-bit signature of its coordinates
+                                          // that appear in another road of the event
+    uint32_t xlo[MAX_ROADS_EV];           // hits shared with a road that shares coordinates on
+    uint32_t xhi[MAX_ROADS_EV];           //   >= 3 layers: bit 8 l + d (l < 4), layer 4 in xhi
     unsigned long long err;               // smallest fault of this event (encoded)
     uint32_t n_ep, n_seg, last_ep;
     unsigned long long nx_w0, nx_w1;      // the CTA's next event: its words, first road, index
@@ -831,6 +835,45 @@ __device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, un
     }
 }
 
+// signature bit of a coordinate: a multiplicative hash into 0..31
+__device__ __forceinline__ unsigned sig_bit(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
+
+// Roads r and t of the event: the layers on which they hold a common
+// coordinate and the hits involved; with three or more such layers, the
+// shared hits of both roads are marked.
+__device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
+{
+    const uint32_t pr = s.pk[r], pt = s.pk[t];
+    unsigned lo_r = 0, lo_t = 0, hi_r = 0, hi_t = 0, layers = 0;
+#pragma unroll
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        const unsigned nr = (pr >> (4 * l)) & 15u, nt = (pt >> (4 * l)) & 15u;   // <= MAX_HITS
+        unsigned br = 0, bt = 0;
+        for (unsigned x = 0; x < nr; ++x) {
+            const unsigned v = s.coord[r][l * 8 + x];
+            for (unsigned y = 0; y < nt; ++y)
+                if (s.coord[t][l * 8 + y] == v) {
+                    br |= 1u << x;
+                    bt |= 1u << y;
+                }
+        }
+        layers += br != 0;
+        if (l < 4) {
+            lo_r |= br << (8 * l);
+            lo_t |= bt << (8 * l);
+        } else {
+            hi_r = br;
+            hi_t = bt;
+        }
+    }
+    if (layers >= 3) {
+        atomicOr(&s.xlo[r], lo_r);
+        atomicOr(&s.xhi[r], hi_r);
+        atomicOr(&s.xlo[t], lo_t);
+        atomicOr(&s.xhi[t], hi_t);
+    }
+}
+
 // Unpack event e (CTA-wide); adds the event's combinations to n_comb.
 __device__ __forceinline__ void p2_publish_next(P2Smem &s, const P2Next &nx)
 {
@@ -955,62 +998,78 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
         }
     }
     __syncthreads();
-    // the road records (four threads per road: layer sub and a share of
-    // layer 4; the first thread writes), then the coordinates (coalesced)
-    for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
-        const unsigned k = kb + threadIdx.x / ROAD_THREADS;
-        const uint32_t pk = k < nr ? s.pk[k] : 0u;
-        unsigned lo = 0, hi = 0;   // flagged hits of layers 0..3 and of layer 4
-        const bool rep = k < nr && s.rep[k] != 0;   // a coordinate repeated within a layer
-        // thread sub: layer sub, and the hits sub, sub + 4 of layer 4
-        for (unsigned pass = 0; pass < 2 && k < nr; ++pass) {
-            const unsigned l = pass ? 4u : sub;
-            const unsigned n = (pk >> (4 * l)) & 15u;
-            unsigned m = 0;
-            for (unsigned dd = pass ? sub : 0u; dd < n; dd += pass ? ROAD_THREADS : 1u) {
-                const unsigned v = s.coord[k][l * 8 + dd];
-                m |= ((s.multi[l][v >> 5] >> (v & 31u)) & 1u) << dd;
-            }
-            if (pass)
-                hi = m;
-            else
-                lo = m << (8 * l);
+
+    // Cross-road pairs.  A track can only be dropped by a track of another
+    // road that shares hits with it on three layers, so only road pairs with
+    // a coordinate in common on >= 3 layers matter.  Each road's coordinates
+    // that appear in another road (the multi bitmap) get a 32-bit signature
+    // per layer; pairs whose signatures meet on >= 3 layers take the exact
+    // test, which marks the shared hits of both roads.  A road with a marked
+    // hit is a cross-road candidate; its marked hits are the ones it
+    // publishes and looks up.
+    const unsigned nroad = min(nr, s.n_ep);   // EP-terminated segments are the roads
+    for (unsigned i = threadIdx.x; i < nroad * N_LAYERS; i += BLOCK) {
+        const unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
+        const unsigned n = (s.pk[k] >> (4 * l)) & 15u;   // <= MAX_HITS (decode clamps it)
+        unsigned sg = 0;
+        for (unsigned x = 0; x < n; ++x) {
+            const unsigned v = s.coord[k][l * 8 + x];
+            if ((s.multi[l][v >> 5] >> (v & 31u)) & 1u)
+                sg |= 1u << sig_bit(v);
         }
-        lo = group_or(lo);
-        hi = group_or(hi);
-        const unsigned long long xm = ((unsigned long long)hi << 32) | lo;
-        const unsigned layers = ((lo & 0xFFu) != 0) + ((lo & 0xFF00u) != 0) + ((lo & 0xFF0000u) != 0) +
-                                ((lo >> 24) != 0) + (hi != 0);
-        const bool cand = layers >= 3;
+        s.sig[k][l] = sg;
+    }
+    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
+        s.xlo[k] = 0;
+        s.xhi[k] = 0;
+    }
+    __syncthreads();
+    for (unsigned r = warp_id(); r < nroad; r += WARPS) {
+        const unsigned s0 = s.sig[r][0], s1 = s.sig[r][1], s2 = s.sig[r][2], s3 = s.sig[r][3], s4 = s.sig[r][4];
+        if ((s0 != 0) + (s1 != 0) + (s2 != 0) + (s3 != 0) + (s4 != 0) < 3)
+            continue;
+        for (unsigned t = r + 1 + lane_id(); t < nroad; t += 32) {
+            const unsigned c = ((s0 & s.sig[t][0]) != 0) + ((s1 & s.sig[t][1]) != 0) + ((s2 & s.sig[t][2]) != 0) +
+                               ((s3 & s.sig[t][3]) != 0) + ((s4 & s.sig[t][4]) != 0);
+            if (c >= 3)
+                pair_exact(s, r, t);
+        }
+    }
+    __syncthreads();
+
+    // the road records, one thread per road, then the coordinates (coalesced)
+    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
         const unsigned g = r0 + k;
-        if (k < nr && sub == 0 && k < s.n_ep && g < d.max_roads) {   // EP-terminated segments are the roads
-            {
-                RoadRec r;
-                r.event = e;
-                r.pk = pk | (cand ? (1u << 23) : 0u);
-                r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
-                r.phi = (int16_t)(s.cp[k] >> 16);
-                r.set = s.set[k];
-                unsigned N, N4;
-                road_sizes(pk, N, N4);
-                // fitted by a whole CTA: roads with more distinct fits than a
-                // warp's run takes, and cross-road candidates with a repeated
-                // coordinate (they publish over raw hits)
-                const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep));
-                r.cta = (big ? 1 : 0) | (rep ? 2 : 0);
-                d.roads[g] = r;
-                d.xmask[g] = xm;
-                d.surv_cnt[g] = 0;
-                if (big) {
-                    unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
-                    if (i < d.max_roads)
-                        d.big_list[i] = g;
-                }
-                if (N > 0 && cand)   // checked against the other roads' groups after the fit
-                    atomicOr(&d.cand_bits[g >> 5], 1u << (g & 31u));
-                n_comb += N;
-            }
+        if (g >= d.max_roads)
+            continue;
+        const uint32_t pk = s.pk[k];
+        const unsigned long long xm = ((unsigned long long)s.xhi[k] << 32) | s.xlo[k];
+        const bool cand = xm != 0ull;
+        const bool rep = s.rep[k] != 0;   // a coordinate repeated within a layer
+        RoadRec r;
+        r.event = e;
+        r.pk = pk | (cand ? (1u << 23) : 0u);
+        r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
+        r.phi = (int16_t)(s.cp[k] >> 16);
+        r.set = s.set[k];
+        unsigned N, N4;
+        road_sizes(pk, N, N4);
+        // fitted by one warp each (the box path): roads with more distinct
+        // fits than a warp's run takes, and cross-road candidates with a
+        // repeated coordinate (they publish over canonical hits)
+        const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep));
+        r.cta = (big ? 1 : 0) | (rep ? 2 : 0);
+        d.roads[g] = r;
+        d.xmask[g] = xm;
+        d.surv_cnt[g] = 0;
+        if (big) {
+            unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
+            if (i < d.max_roads)
+                d.big_list[i] = g;
         }
+        if (N > 0 && cand)   // checked against the other roads' groups after the fit
+            atomicOr(&d.cand_bits[g >> 5], 1u << (g & 31u));
+        n_comb += N;
     }
     {   // 16 bytes per store (a road's row is five 16-byte words)
         uint4 *dst = reinterpret_cast<uint4 *>(d.coords + (size_t)r0 * 40);
@@ -1086,14 +1145,24 @@ __device__ __forceinline__ unsigned hash_slot(unsigned long long k, unsigned mas
     return (unsigned)k & mask;
 }
 
+// The group table is probed linearly from a group's home slot, at most
+// HASH_PROBES slots, and may be filled to three quarters of its slots: a
+// batch that needs more raises FLAG_CAPACITY (SVT_E_CAPACITY, no tracks)
+// instead of probing on.
+constexpr unsigned HASH_PROBES = 64;
+
+__device__ __forceinline__ unsigned hash_probes(const Dev &d) { return min(HASH_PROBES, d.hash_mask + 1); }
+
 __device__ void hash_min(const Dev &d, unsigned long long gk, unsigned long long key)
 {
     unsigned h = hash_slot(gk, d.hash_mask);
-    for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
+    const unsigned slots = d.hash_mask + 1;
+    for (unsigned probe = 0; probe < hash_probes(d); ++probe) {
         unsigned long long prev = atomicCAS(&d.hash[h].key, 0ull, gk);
         if (prev == 0ull) {   // a new slot: marked for clearing (no value awaited)
             atomicOr(&d.hash_bits[h >> 5], 1u << (h & 31u));
-            atomicAdd(&d.ctrl->hash_used, 1u);
+            if (atomicAdd(&d.ctrl->hash_used, 1u) >= slots - slots / 4)
+                raise_flag(d, FLAG_CAPACITY);
         }
         if (prev == 0ull || prev == gk) {
             atomicMax(&d.hash[h].val_inv, ~key);
@@ -1110,7 +1179,7 @@ __device__ unsigned long long hash_get(const Dev &d, unsigned long long gk)
 {
     static_assert(sizeof(HashSlot) == 16, "one 16-byte load per slot");
     unsigned h = hash_slot(gk, d.hash_mask);
-    for (unsigned probe = 0; probe <= d.hash_mask; ++probe) {
+    for (unsigned probe = 0; probe < hash_probes(d); ++probe) {
         const ulonglong2 sl = __ldcg(reinterpret_cast<const ulonglong2 *>(d.hash + h));
         if (sl.x == gk)
             return ~sl.y;
@@ -1738,7 +1807,8 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 // (z, w) of slots c and e.  The six pair tables (minimum key over the fits
 // with the same canonical hits on two slots) come out of that one loop:
 //   T_ab[x][y]  the lane's minimum over its own fits
-//   T_ce[z][w]  the minimum over the lanes at each step (warp reduction)
+//   T_ce[z][w]  the minimum over the lanes at (z, w): taken afterwards by a
+//               warp reduction, only where a candidate or a group needs it
 //   T_ac, T_bc  the lane's minimum over w at each z, folded over the lanes
 //   T_ae, T_be  the lane's minimum over z for each w, folded at the end
 // A fit survives the road-local warrior iff its key is the minimum of all
@@ -1749,8 +1819,8 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 enum { T_AB = 0, T_CE, T_AC, T_BC, T_AE, T_BE, N_TAB };
 
 struct P3Box {
-    unsigned long long T[N_TAB][64];   // pair tables, [u * 8 + v] (u: the first role's hit)
-    unsigned long long TB[2][64];      // T_ce of each pass, [pass][z * 8 + w]
+    unsigned long long T[N_TAB][64];   // pair tables, [u * 8 + v] (u: the first role's hit); T_ce
+                                       // only where needed (box_tce)
     int4 A[4][8];                      // slot j, canonical hit k: chi-square partial sums (x, y,
                                        // z) and comb part (w); slot 0 also carries curvature, phi,
                                        // 4096 k and the road bits of the key
@@ -1798,10 +1868,25 @@ struct BoxShape {
     __device__ unsigned m(unsigned s) const { return (mpk >> (4 * s)) & 15u; }
 };
 
+// Key of the fit with summed partials s (without the comb) and comb part
+// cw, or NO_KEY when it fails the cut or `live` is false.  The comb occupies
+// bits below the chi-square's shifted bits, so it is added, not or-ed.
+__device__ __forceinline__ unsigned long long box_key2(const int4 &s, unsigned cw, long long cut, bool live,
+                                                       bool &ok)
+{
+    const long long chi2 = sq(s.x >> 12) + sq(s.y >> 12) + sq(s.z >> 12);
+    ok = live && chi2 <= cut;
+    const unsigned hi = (unsigned)((unsigned long long)chi2 >> 9);
+    const unsigned lo = ((unsigned)chi2 << 23) + cw;
+    return ok ? ((unsigned long long)hi << 32) | lo : NO_KEY;
+}
+
 // One pass over the pairs (x, y) of slots a and b: lane t = 32 p + lane.
-// DUP: the road has repeated coordinates (passing counts are weighted by the
-// raw fits each canonical fit stands for).
-template <bool PLAIN, bool DUP>
+// The inner loop over the hits of slot e has ME (4 or 8, at least me) steps,
+// unrolled and predicated, so a step has no branch.  DUP: the road has
+// repeated coordinates (passing counts are weighted by the raw fits each
+// canonical fit stands for).  T_ce is not made here (see box_tce).
+template <bool PLAIN, bool DUP, unsigned ME>
 __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p, unsigned &np)
 {
     const unsigned lane = lane_id();
@@ -1812,38 +1897,36 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
     const int4 pab = add4(B.A[sh.ra][x], B.A[sh.rb][y]);
     const unsigned wab = DUP ? (unsigned)B.mult[sh.ra][x] * B.mult[sh.rb][y] : 1u;
     const long long cut = d.cut;
-    unsigned long long qab = NO_KEY, rw[MAX_HITS];
+    const int4 *Ae = B.A[sh.re];
+    bool live[ME];
 #pragma unroll
-    for (unsigned w = 0; w < MAX_HITS; ++w)
+    for (unsigned w = 0; w < ME; ++w)
+        live[w] = act && w < me;
+    unsigned long long qab = NO_KEY, rw[ME];
+#pragma unroll
+    for (unsigned w = 0; w < ME; ++w)
         rw[w] = NO_KEY;
     for (unsigned z = 0; z < mc; ++z) {
         const int4 pz = add4(pab, B.A[sh.rc][z]);
         const unsigned wz = DUP ? wab * B.mult[sh.rc][z] : 1u;
         unsigned long long rz = NO_KEY;
 #pragma unroll
-        for (unsigned w = 0; w < MAX_HITS; ++w) {
-            if (w < me) {
-                const int4 s = add4(pz, B.A[sh.re][w]);
-                unsigned long long key;
-                if (PLAIN) {
-                    key = act ? ldcg(d.fit_key + sh.cb + (unsigned)s.w) : NO_KEY;
-                } else {
-                    bool pass;
-                    key = box_key(s, cut, pass);
-                    if (!act)
-                        key = NO_KEY;
-                    if (act && pass)
-                        np += DUP ? wz * B.mult[sh.re][w] : 1u;
-                }
-                rz = umin64(rz, key);
-                rw[w] = umin64(rw[w], key);
-                // T_ce at (z, w): the minimum over the lanes, high word first
-                const unsigned hi = (unsigned)(key >> 32);
-                const unsigned mh = __reduce_min_sync(FULL_MASK, hi);
-                const unsigned ml = __reduce_min_sync(FULL_MASK, hi == mh ? (unsigned)key : 0xFFFFFFFFu);
-                if (lane == 0)
-                    B.TB[p][z * 8 + w] = ((unsigned long long)mh << 32) | ml;
+        for (unsigned w = 0; w < ME; ++w) {
+            const int4 aw = Ae[w];
+            unsigned long long key;
+            if (PLAIN) {
+                key = live[w] ? ldcg(d.fit_key + sh.cb + (unsigned)(pz.w + aw.w)) : NO_KEY;
+            } else {
+                const int4 s = make_int4(pz.x + aw.x, pz.y + aw.y, pz.z + aw.z, 0);
+                bool ok;
+                key = box_key2(s, (unsigned)pz.w + (unsigned)aw.w, cut, live[w], ok);
+                if (DUP)
+                    np += ok ? wz * B.mult[sh.re][w] : 0u;
+                else
+                    np += ok;
             }
+            rz = umin64(rz, key);
+            rw[w] = umin64(rw[w], key);
         }
         qab = umin64(qab, rz);
         if (act) {
@@ -1854,12 +1937,39 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
     if (act) {
         B.T[T_AB][x * 8 + y] = qab;
 #pragma unroll
-        for (unsigned w = 0; w < MAX_HITS; ++w)
+        for (unsigned w = 0; w < ME; ++w)
             if (w < me) {
                 atomicMin(&B.T[T_AE][x * 8 + w], rw[w]);
                 atomicMin(&B.T[T_BE][y * 8 + w], rw[w]);
             }
     }
+}
+
+// T_ce[z][w]: the minimum key over every pair (x, y) at hits z, w of slots
+// c and e (every lane calls it with the same z, w; the result is the same in
+// every lane).
+template <bool PLAIN>
+__device__ unsigned long long box_tce(const Dev &d, const P3Box &B, const BoxShape &sh, unsigned z, unsigned w)
+{
+    const unsigned lane = lane_id();
+    const int4 pzw = add4(B.A[sh.rc][z], B.A[sh.re][w]);
+    unsigned long long mn = NO_KEY;
+    for (unsigned t = lane; t < sh.ma * sh.mb; t += 32) {
+        const unsigned y = divm(t, c_magic[sh.ma]), x = t - y * sh.ma;
+        const int4 s = add4(pzw, add4(B.A[sh.ra][x], B.A[sh.rb][y]));
+        unsigned long long key;
+        if (PLAIN) {
+            key = ldcg(d.fit_key + sh.cb + (unsigned)s.w);
+        } else {
+            bool ok;
+            key = box_key2(s, (unsigned)s.w, d.cut, true, ok);
+        }
+        mn = umin64(mn, key);
+    }
+    const unsigned hi = (unsigned)(mn >> 32);
+    const unsigned mh = __reduce_min_sync(FULL_MASK, hi);
+    const unsigned ml = __reduce_min_sync(FULL_MASK, hi == mh ? (unsigned)mn : 0xFFFFFFFFu);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
 // the table holding the minima over slots p and q (p != q) and the index of
@@ -1980,30 +2090,34 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
     }
     __syncwarp();
 
-    // the loop over the box: all six tables
-    const unsigned ma = sh.ma, mb = sh.mb, mc = sh.mc, me = sh.me;
+    // the loop over the box: every table but T_ce
+    const unsigned ma = sh.ma, mb = sh.mb, me = sh.me;
     const unsigned passes = (ma * mb + 31) / 32;   // 1 or 2
     unsigned np = 0;
     for (unsigned p = 0; p < passes; ++p) {
-        if (dup)
-            box_pass<PLAIN, true>(d, B, sh, p, np);
-        else
-            box_pass<PLAIN, false>(d, B, sh, p, np);
-    }
-    __syncwarp();
-    for (unsigned i = lane; i < 64; i += 32) {
-        const unsigned z = i >> 3, w = i & 7u;
-        if (z < mc && w < me)
-            B.T[T_CE][i] = passes > 1 ? umin64(B.TB[0][i], B.TB[1][i]) : B.TB[0][i];
+        if (me > 4) {
+            if (dup)
+                box_pass<PLAIN, true, 8>(d, B, sh, p, np);
+            else
+                box_pass<PLAIN, false, 8>(d, B, sh, p, np);
+        } else {
+            if (dup)
+                box_pass<PLAIN, true, 4>(d, B, sh, p, np);
+            else
+                box_pass<PLAIN, false, 4>(d, B, sh, p, np);
+        }
     }
     __syncwarp();
     if (!PLAIN)
         npass += (unsigned long long)np * sh.ne;
 
     // road-local survivors: the minimum of pair (x, y) survives iff it is
-    // also the minimum of its other five tables
+    // also the minimum of its other five tables; T_ce (the minimum over all
+    // pairs at its hits of slots c and e) is taken last, for the pairs that
+    // pass the other four, by the whole warp
     unsigned long long sk[2] = {NO_KEY, NO_KEY};
     bool sv[2] = {false, false};
+    unsigned zw[2] = {0u, 0u};
 #pragma unroll
     for (unsigned p = 0; p < 2; ++p) {
         const unsigned t = p * 32 + lane;
@@ -2024,11 +2138,21 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                     de = l == Le ? dl : de;
                 }
                 const unsigned z = B.rank[sh.rc][dc], w = B.rank[sh.re][de];
-                sv[p] = B.T[T_CE][z * 8 + w] == key && B.T[T_AC][x * 8 + z] == key &&
-                        B.T[T_BC][y * 8 + z] == key && B.T[T_AE][x * 8 + w] == key &&
-                        B.T[T_BE][y * 8 + w] == key;
+                sv[p] = B.T[T_AC][x * 8 + z] == key && B.T[T_BC][y * 8 + z] == key &&
+                        B.T[T_AE][x * 8 + w] == key && B.T[T_BE][y * 8 + w] == key;
                 sk[p] = key;
+                zw[p] = z * 8 + w;
             }
+        }
+    }
+#pragma unroll
+    for (unsigned p = 0; p < 2; ++p) {
+        for (unsigned bits = __ballot_sync(FULL_MASK, sv[p]); bits; bits &= bits - 1) {
+            const unsigned src = __ffs(bits) - 1;
+            const unsigned e = __shfl_sync(FULL_MASK, zw[p], src);
+            const unsigned long long m = box_tce<PLAIN>(d, B, sh, e >> 3, e & 7u);
+            if (lane == src)
+                sv[p] = m == sk[p];
         }
     }
     // survivors in comb order: each finds its rank among the others
@@ -2082,6 +2206,19 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
 #pragma unroll
         for (unsigned t = 0; t < 10; ++t)
             total += groups(t);
+        {   // the entries of T_ce that groups of (excluded layer, slot c, slot e) read
+            const unsigned Lc = sh.rc + (sh.rc >= excl), Le = sh.re + (sh.re >= excl);
+            const unsigned fc = fl(Lc), fe = fl(Le);
+            if (fl(excl))
+                for (unsigned bc = fc; bc; bc &= bc - 1)
+                    for (unsigned be = fe; be; be &= be - 1) {
+                        const unsigned z = B.rank[sh.rc][__ffs(bc) - 1], w = B.rank[sh.re][__ffs(be) - 1];
+                        const unsigned long long m = box_tce<PLAIN>(d, B, sh, z, w);
+                        if (lane == 0)
+                            B.T[T_CE][z * 8 + w] = m;
+                    }
+            __syncwarp();
+        }
         unsigned Se = 1;   // comb stride of the excluded layer
         for (unsigned l = 0; l < excl; ++l)
             Se *= hits_of(pk, l);
@@ -2594,7 +2731,7 @@ __device__ void clear_hash(const Dev &d)
 __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    if (d.skip_arrival && blockIdx.x == 0)
+    if (d.skip_arrival == 1 && blockIdx.x == 0)
         return;   // test hook: this CTA never arrives at the first barrier
     stamp(d, 0);
 
@@ -2616,6 +2753,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         return;   // a data fault: no tracks
 
     p3_phase<false>(d, smem, Q_BIG, Q_SMALL);
+    if (d.skip_arrival == 2 && blockIdx.x == 0)
+        return;   // test hook: this CTA leaves after publishing, the others' waits run out
     if (!grid_sync(d))
         return;
     stamp(d, 4);

@@ -9,13 +9,13 @@
 // file-scope __device__ array of fixed size (ARENA_BYTES), placed by the
 // module loader, and writes the tracks into the caller's buffer.
 //
-// The first call on a device looks up the arena's address with
-// cudaGetSymbolAddress and clears its group table; later calls reuse both.
-// There is one arena per device: calls that overlap in time (two host threads,
-// or two streams with work in flight) race on it.
+// Every call looks up the arena's address with cudaGetSymbolAddress on the
+// current device (cheap, and it follows a re-created primary context); the
+// first call on a device, and the first after the address changed, clears
+// its group table.  There is one arena per device: calls that overlap in time
+// (two host threads, or two streams with work in flight) race on it.
 #include "svt_ctx.h"
 
-#include <cstdlib>
 #include <vector>
 #include <mutex>
 
@@ -63,36 +63,12 @@ static __device__ __align__(256) unsigned char g_arena[ARENA_BYTES];
 namespace {
 
 struct DeviceArena {
-    unsigned char *base = nullptr;
-    bool hash_dirty = true;   // clear the group table before the next batch
+    unsigned char *base = nullptr;   // the arena's address when the table was last known empty
+    bool hash_dirty = true;          // clear the group table before the next batch
 };
 
 std::mutex g_mu;
 DeviceArena g_dev[64];
-
-// the same admission rule as svt_load_constants
-bool constants_admissible(const svt_const_set *sets)
-{
-    for (int s = 0; s < N_SETS; ++s) {
-        long long chi_bound = 0;
-        for (int k = 0; k < 3; ++k) {
-            long long bf = 4096ll * std::llabs((long long)sets[s].q[k]);
-            long long bc = 4096ll * std::llabs((long long)sets[s].k[k]);
-            for (int j = 0; j < 6; ++j) {
-                const long long mx = j < 4 ? 4095 : 32768;
-                bf += std::llabs((long long)sets[s].F[k][j]) * mx;
-                bc += std::llabs((long long)sets[s].C[k][j]) * mx;
-            }
-            if (bf >= (1ll << 31) || bc >= (1ll << 31))
-                return false;
-            const long long a = bc / 4096 + 1;
-            chi_bound += a * a;
-        }
-        if (chi_bound >= (1ll << 38))
-            return false;
-    }
-    return true;
-}
 
 }  // namespace
 
@@ -113,18 +89,26 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return SVT_E_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // the call waits for its batch, which a stream being captured cannot do
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap_st) != cudaSuccess)
+        return SVT_E_CUDA;
+    if (cap_st != cudaStreamCaptureStatusNone)
+        return SVT_E_INVAL;
 
     DeviceArena *da = &g_dev[dev];
+    unsigned char *b = nullptr;
     {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p)
+            return SVT_E_CUDA;
+        b = static_cast<unsigned char *>(p);
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!da->base) {   // first call on this device
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_arena) != cudaSuccess || !p)
-                return SVT_E_CUDA;
-            da->base = static_cast<unsigned char *>(p);
+        if (da->base != b) {   // first call on this device, or a new context: table state unknown
+            da->base = b;
+            da->hash_dirty = true;
         }
     }
-    unsigned char *b = da->base;
     Dev d{};
     d.ctrl = reinterpret_cast<Ctrl *>(b + OFF_CTRL);
     d.consts = reinterpret_cast<const svt_const_set *>(b + OFF_CONSTS);
@@ -182,17 +166,10 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     if (cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))
         return SVT_E_CUDA;
     da->hash_dirty = (h.flags & FLAG_TIMEOUT) != 0;
-    int st = SVT_OK;
-    if (h.flags & FLAG_TIMEOUT)
-        st = SVT_E_TIMEOUT;
-    else if (h.flags & FLAG_CAPACITY)
-        st = SVT_E_CAPACITY;
-    else if (h.err_inv) {
-        const unsigned rank = (unsigned)(~h.err_inv & 0xFFull);
-        st = rank == RANK_BAD ? SVT_E_BADWORD : rank == RANK_LIMIT ? SVT_E_LIMIT : SVT_E_TRUNCATED;
-    } else if (h.flags & FLAG_INTERNAL)
-        st = SVT_E_CUDA;
-    if (st == SVT_OK || st == SVT_E_CAPACITY)
+    const int st = status_of(h);
+    // with SVT_E_CAPACITY, the survivors when they did not fit `cap`; 0 when
+    // an arena limit (events, roads, group table) was exceeded
+    if (st == SVT_OK || (st == SVT_E_CAPACITY && h.n_out > cap))
         *n_out = (size_t)h.n_out;
     return st;
 }

@@ -64,3 +64,42 @@ def test_limits_and_errors(consts, cuts):
     assert st == B.E_BADWORD and n == 0
     st, n, got = run_static(words, consts, cuts["small"], 4096)      # and it still works
     assert st == B.OK and n == len(got) > 0
+
+
+def _at_limit_configs():
+    # 1025 events (one road each), 8199 roads (911 events of 9): both below
+    # the arena's 131072 words; 1024 events x 8 roads: exactly at both limits
+    return {"events": synth.Config("ev1025", 1025, ("fixed", 1), ("uniform", 1, 1)),
+            "roads": synth.Config("rd8199", 911, ("fixed", 9), ("uniform", 1, 1)),
+            "at_limit": synth.Config("ev1024", 1024, ("fixed", 8), ("uniform", 1, 1))}
+
+
+@pytest.mark.parametrize("what", ["events", "roads"])
+def test_arena_event_and_road_limits(ctx, consts, cuts, what):
+    """More events or roads than the arena holds: SVT_E_CAPACITY with no
+    tracks (checked on the device); the next call still equals the context
+    path."""
+    b = synth.make_batch(_at_limit_configs()[what], seed=6)
+    assert len(b.words) < (1 << 17)
+    st, n, _ = run_static(b.words, consts, cuts["small"], 1 << 14)
+    assert st == B.E_CAPACITY and n == 0
+    good = synth.make_batch("small", seed=2).words
+    ctx.load_constants(consts, cuts["small"])
+    st0, want, _ = run_gpu(ctx, good, B.PERSISTENT)
+    st, n, got = run_static(good, consts, cuts["small"], len(want) + 16)
+    assert st0 == st == B.OK and n == len(want)
+    assert got.tobytes() == want.tobytes()
+
+
+def test_batch_at_the_event_and_road_limits_equals_the_context_path(ctx, consts, cuts):
+    """1024 events and 8192 roads, exactly the arena's limits: byte for byte
+    the context path's tracks, twice in a row."""
+    b = synth.make_batch(_at_limit_configs()["at_limit"], seed=7)
+    assert b.n_events == 1024 and len(b.roads) == 8192
+    ctx.load_constants(consts, cuts["small"])
+    st0, want, _ = run_gpu(ctx, b.words, B.PERSISTENT)
+    assert st0 == B.OK and len(want) > 0
+    for _ in range(2):
+        st, n, got = run_static(b.words, consts, cuts["small"], len(want) + 16)
+        assert st == B.OK and n == len(want)
+        assert got.tobytes() == want.tobytes()
