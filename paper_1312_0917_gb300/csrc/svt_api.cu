@@ -158,9 +158,6 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     }
     c->lim = L;
     Dev &d = c->d;
-    unsigned n_chunks_w = (unsigned)((L.max_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
-    // chunk slots: the plain kernels' word chunks, the persistent kernel's CTAs
-    const unsigned n_slots_w = n_chunks_w > (unsigned)MAX_GRID ? n_chunks_w : (unsigned)MAX_GRID;
     d.max_events = L.max_events;
     d.max_roads = L.max_roads;
     d.max_chunks_r = (L.max_roads + ROAD_CHUNK - 1) / ROAD_CHUNK;
@@ -170,9 +167,8 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     d.small_n4 = N4_SMALL_MAX;
     bool ok =
         !dalloc(c, &d.ctrl, 1) && !dalloc(c, const_cast<svt_const_set **>(&d.consts), N_SETS) &&
-        !dalloc(c, &d.chunk_ee, n_slots_w) && !dalloc(c, &d.chunk_ep, n_slots_w) &&
-        !dalloc(c, &d.chunk_ee_off, n_slots_w) && !dalloc(c, &d.chunk_ep_off, n_slots_w) &&
-        !dalloc(c, &d.ev_word_end, L.max_events) && !dalloc(c, &d.ev_road_end, L.max_events) &&
+        !dalloc(c, &d.span_ee, MAX_SPANS + MAX_GRID) && !dalloc(c, &d.span_ep, MAX_SPANS + MAX_GRID) &&
+        !dalloc(c, &d.span_seg, MAX_SPANS + MAX_GRID) && !dalloc(c, &d.ev_road_end, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
         !dalloc(c, &d.cand_bits, L.max_roads / 32 + 1) && !dalloc(c, &d.fitc, N_SETS * SET_INT4) &&
@@ -234,7 +230,6 @@ int svt_unpack(svt_ctx *c, const uint32_t *d_words, size_t n_words, void *stream
         return SVT_E_CAPACITY;
     c->d.words = d_words;
     c->d.n_words = n_words;
-    c->d.n_chunks_w = (unsigned)((n_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
     c->bound = true;
     c->roads_valid = false;
     c->ran = false;

@@ -10,9 +10,8 @@ namespace svt {
 
 constexpr int BLOCK = 256;                 // threads per CTA, every kernel
 constexpr int WARPS = BLOCK / 32;
-constexpr int CHUNK_WORDS = 4096;          // words per unpack work item (16 per thread)
-constexpr int MAX_GRID = 4096;             // CTAs of the persistent kernel at most (its word-scan
-                                           // totals use the first MAX_GRID chunk slots)
+constexpr int MAX_GRID = 4096;             // CTAs of any kernel over the word spans at most
+constexpr int MAX_SPANS = MAX_GRID * WARPS; // word spans (one per warp of the grid)
 constexpr int MAX_ROADS_EV = 256;          // format limit: roads per event
 constexpr int MAX_HITS = 8;                // format limit: hits per layer per road
 constexpr int N_LAYERS = 5;
@@ -99,11 +98,12 @@ struct Dev {
     const svt_const_set *consts;
     const uint32_t *words;
     unsigned long long n_words;
-    unsigned int n_chunks_w;        // ceil(n_words / CHUNK_WORDS)
     unsigned int max_events, max_roads, max_chunks_r;
     unsigned long long max_tracks, max_combs;
-    uint32_t *chunk_ee, *chunk_ep, *chunk_ee_off, *chunk_ep_off;   // [n_chunks_w]
-    uint32_t *ev_word_end, *ev_road_end;                          // [max_events]
+    uint32_t *span_ee, *span_ep, *span_seg;   // [MAX_SPANS + MAX_GRID] per word span (one per warp),
+                                              // then per CTA (its spans together): EE and EP words,
+                                              // EP words since its last EE (SEG_EE set when it holds one)
+    uint32_t *ev_road_end;                    // [max_events] roads up to the end of each event
     RoadRec *roads;                                               // [max_roads]
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]

@@ -3,14 +3,14 @@
 // Stages (arXiv:1312.0917, Sec. II-A: unpack, combine, fit), followed by the
 // chi-square cut and the hit-warrior:
 //
-//   P0  word chunks: count EE / EP words, check every word's fields
-//   P1  word chunks: scatter the end word and the road count of every event
-//   P2  events: decode each road (header, XFT track, hits ranked per layer),
-//       enforce the grammar and limits, flag hits whose coordinate appears in
-//       another road of the same event on the same layer
+//   P0  word spans (one per warp): count EE / EP words, check every word's fields
+//   P1  word spans: decode the roads whose header lies in the span (header,
+//       XFT track, hits ranked per layer), enforce the grammar and limits
+//   P2  events: flag the hits a road shares with another road of the event
+//       that holds its coordinates on >= 3 layers (the cross-road candidates)
 //   P3  roads: combinations, fit, chi-square, cut and the road-local part of
 //       the hit-warrior; publish cross-road group minima for flagged groups
-//   P4  road chunks: finish the hit-warrior across roads, count survivors
+//   P4  candidate roads: finish the hit-warrior across roads, count survivors
 //   P5  road chunks: write the surviving tracks in (event, road, comb) order
 //
 // SVT_PLAIN runs P0, P1, P2, a combination scan, a fit kernel with one thread
@@ -349,183 +349,343 @@ __device__ __forceinline__ void stamp(const Dev &d, unsigned k)
 enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
 
 // ---------------------------------------------------------------------------
-// P0 / P1: word chunks
+// P0 / P1: the word stream, one warp per span.  The stream is cut into
+// gridDim.x * WARPS spans of whole 32-word windows; warp w of CTA b owns span
+// b * WARPS + w.  P0 counts each span's EE and EP words and the EP words after
+// its last EE, and checks every word's fields.  P1 gives each warp the counts
+// of the spans before its own (every CTA sums them itself, no CTA scans for
+// the others) and decodes the roads whose header lies in the warp's span, a
+// window at a time: lane i holds word i of the window, and ballots over the
+// EP, EE and type bits give each word its road, its position in the road,
+// its event, its road's place in the event and its hit's rank in its layer.
+// A warp follows its last road past the end of its span.
 // ---------------------------------------------------------------------------
 
-__device__ void p0_item(const Dev &d, unsigned c)
+constexpr unsigned WIN = 32;               // words per window: one per lane
+constexpr unsigned SEG_EE = 0x80000000u;   // segment word: an EE was seen (low bits: EP words since)
+
+// span i of the stream (0 <= i < gridDim.x * WARPS): words [a, e)
+__device__ __forceinline__ void span_of(const Dev &d, unsigned i, unsigned long long &a, unsigned long long &e)
 {
-    unsigned long long base = (unsigned long long)c * CHUNK_WORDS;
-    unsigned long long end = min(base + CHUNK_WORDS, d.n_words);
-    unsigned ee = 0, ep = 0;
-    unsigned long long bad = ~0ull;
-    // all loads of a thread are issued before the first is used
-    static_assert(CHUNK_WORDS % BLOCK == 0, "a word chunk is a whole number of words per thread");
-    uint32_t w[CHUNK_WORDS / BLOCK];
-#pragma unroll
-    for (unsigned k = 0; k < CHUNK_WORDS / BLOCK; ++k) {
-        const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
-        w[k] = i < end ? __ldg(d.words + i) : 0u;
-    }
-#pragma unroll
-    for (unsigned k = 0; k < CHUNK_WORDS / BLOCK; ++k) {
-        const unsigned long long i = base + threadIdx.x + (unsigned long long)k * BLOCK;
-        ee += w[k] >> 31;
-        ep += (w[k] >> 30) & 1u;
-        if (i < end && !word_ok(w[k]) && bad == ~0ull)
-            bad = i;
-    }
-    if (bad != ~0ull)
-        report(d, bad, RANK_BAD);
-    unsigned long long tot_ee = block_sum(ee), tot_ep = block_sum(ep);
-    if (threadIdx.x == 0) {
-        d.chunk_ee[c] = (uint32_t)tot_ee;
-        d.chunk_ep[c] = (uint32_t)tot_ep;
-    }
+    const unsigned long long n = (unsigned long long)gridDim.x * WARPS;
+    const unsigned long long per = ((d.n_words + n - 1) / n + WIN - 1) / WIN * WIN;
+    a = min((unsigned long long)i * per, d.n_words);
+    e = min(a + per, d.n_words);
 }
 
-// run by the CTA that finishes P0 last
-__device__ void p0_finish(const Dev &d)
+// Join of the segment words of two stretches of words, x before y: the EP
+// words since the last EE of both (SEG_EE when either holds an EE).  0 is the
+// identity.  Counts stay below 2^31 (a batch holds fewer words).
+__device__ __forceinline__ unsigned seg_join(unsigned x, unsigned y)
 {
-    unsigned long long n_ee = block_scan_array(d.chunk_ee, d.chunk_ee_off, d.n_chunks_w);
-    unsigned long long n_ep = block_scan_array(d.chunk_ep, d.chunk_ep_off, d.n_chunks_w);
-    if (threadIdx.x == 0) {
-        Ctrl *c = d.ctrl;
-        c->n_events = (unsigned)n_ee;
-        c->n_ep = (unsigned)n_ep;
-        unsigned tail = 0;
-        if (d.n_words > 0 && !(__ldg(d.words + d.n_words - 1) >> 31)) {
-            tail = 1;
-            report(d, d.n_words, RANK_TRUNC);
-        }
-        c->has_tail = tail;
-        if (n_ee > d.max_events || n_ep > d.max_roads)
-            raise_flag(d, FLAG_CAPACITY);
-        if (n_ee == 0)
-            c->n_roads = 0;
-        __threadfence();
-    }
+    return (y & SEG_EE) ? y : (x & SEG_EE) | ((x & ~SEG_EE) + y);
 }
 
-__device__ void p1_item(const Dev &d, unsigned c)
+// segment word of one window from its EE and EP lane masks
+__device__ __forceinline__ unsigned seg_window(unsigned em, unsigned pm)
 {
-    unsigned long long base = (unsigned long long)c * CHUNK_WORDS + (unsigned long long)threadIdx.x * 16;
-    uint32_t w[16];
-    unsigned ee = 0, ep = 0;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        unsigned long long i = base + k;
-        w[k] = i < d.n_words ? __ldg(d.words + i) : 0u;
-        ee += w[k] >> 31;
-        ep += (w[k] >> 30) & 1u;
-    }
-    unsigned long long ee_ex = block_excl_scan(ee, nullptr);
-    unsigned long long ep_ex = block_excl_scan(ep, nullptr);
-    unsigned ev = ldcg(d.chunk_ee_off + c) + (unsigned)ee_ex;
-    unsigned rd = ldcg(d.chunk_ep_off + c) + (unsigned)ep_ex;
-    const unsigned n_events = ldcg(&d.ctrl->n_events);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        rd += (w[k] >> 30) & 1u;
-        if (w[k] >> 31) {
-            if (ev < d.max_events) {
-                d.ev_word_end[ev] = (uint32_t)(base + k);
-                d.ev_road_end[ev] = rd;
-            }
-            if (ev + 1 == n_events)
-                d.ctrl->n_roads = rd;
-            ++ev;
-        }
-    }
+    return em ? SEG_EE | (unsigned)__popc((pm >> (31 - __clz(em))) >> 1) : (unsigned)__popc(pm);
 }
 
-// ---------------------------------------------------------------------------
-// P0 / P1 of the persistent kernel: CTA b owns one contiguous slice of the
-// words (equal slices, a multiple of 32 words).  P0 counts the slice's EE
-// and EP words; after the grid barrier every CTA sums the CTA totals below
-// its own (its offsets) and over all CTAs (the stream's counts), so no CTA
-// scans for the others, and P1 scatters the slice's event boundaries.
-// ---------------------------------------------------------------------------
-
-constexpr unsigned SCAN_PT = 32;                     // words per thread per tile
-constexpr unsigned SCAN_TILE = BLOCK * SCAN_PT;
-
-// a tile staged in shared memory, one pad word per 32 so that thread t can
-// read its 32 consecutive words without bank conflicts
-struct ScanSmem {
-    uint32_t w[SCAN_TILE + SCAN_TILE / 32];
-};
-__device__ __forceinline__ unsigned scan_pad(unsigned i) { return i + (i >> 5); }
-
-__device__ __forceinline__ void scan_slice(const Dev &d, unsigned long long &w0, unsigned long long &w1)
+// In-order fold of one segment word per lane (lane i's stretch before lane
+// i + 1's); the result in every lane.
+__device__ __forceinline__ unsigned warp_seg_fold(unsigned v)
 {
-    const unsigned long long per = ((d.n_words + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
-    w0 = min((unsigned long long)blockIdx.x * per, d.n_words);
-    w1 = min(w0 + per, d.n_words);
+    for (unsigned o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_down_sync(FULL_MASK, v, o);
+        if (lane_id() + o < 32)
+            v = seg_join(v, u);
+    }
+    return __shfl_sync(FULL_MASK, v, 0);
 }
 
-// One tile of a slice into registers, word threadIdx.x + k * BLOCK of the
-// tile in w[k] (0 past the slice: neither EE nor EP).  The loads take a
-// clamped index, so that all of them issue before the first value is used.
-__device__ __forceinline__ void scan_load(const uint32_t *slice, unsigned n, unsigned off, uint32_t (&w)[SCAN_PT])
+// the same over the CTA (thread t's stretch before thread t + 1's)
+__device__ unsigned block_seg_fold(unsigned v)
 {
+    __shared__ unsigned s_seg[WARPS];
+    v = warp_seg_fold(v);
+    if (lane_id() == 0)
+        s_seg[warp_id()] = v;
+    __syncthreads();
+    unsigned r = 0;
 #pragma unroll
-    for (unsigned k = 0; k < SCAN_PT; ++k) {
-        const unsigned i = off + threadIdx.x + k * BLOCK;
-        const uint32_t x = __ldg(slice + min(i, n - 1u));
-        w[k] = i < n ? x : 0u;
-    }
+    for (unsigned w = 0; w < WARPS; ++w)
+        r = seg_join(r, s_seg[w]);
+    __syncthreads();
+    return r;
 }
 
 __device__ void scan_count(const Dev &d)
 {
-    unsigned long long w0, w1;
-    scan_slice(d, w0, w1);
-    const unsigned n = (unsigned)(w1 - w0);   // a slice holds < 2^32 words
-    const uint32_t *slice = d.words + w0;
-    unsigned ee = 0, ep = 0;
-    unsigned bad = ~0u;
-    for (unsigned off = 0; off < n; off += SCAN_TILE) {
-        uint32_t w[SCAN_PT];
-        scan_load(slice, n, off, w);
+    const unsigned lane = lane_id(), sp = blockIdx.x * WARPS + warp_id();
+    unsigned long long a, e;
+    span_of(d, sp, a, e);
+    unsigned ee = 0, ep = 0, seg = 0;
+    unsigned long long bad = ~0ull;
+    constexpr unsigned UNROLL = 8;   // windows whose loads are in flight together
+    for (unsigned long long base = a; base < e; base += UNROLL * WIN) {
+        uint32_t w[UNROLL];
 #pragma unroll
-        for (unsigned k = 0; k < SCAN_PT; ++k) {
-            const unsigned i = off + threadIdx.x + k * BLOCK;
-            ee += w[k] >> 31;
-            ep += (w[k] >> 30) & 1u;
-            if (i < n && !word_ok(w[k]) && bad == ~0u)
+        for (unsigned k = 0; k < UNROLL; ++k) {
+            const unsigned long long i = base + k * WIN + lane;
+            w[k] = i < e ? __ldg(d.words + i) : 0u;
+        }
+#pragma unroll
+        for (unsigned k = 0; k < UNROLL; ++k) {
+            const unsigned long long i = base + k * WIN + lane;
+            const unsigned em = __ballot_sync(FULL_MASK, w[k] >> 31);
+            const unsigned pm = __ballot_sync(FULL_MASK, (w[k] >> 30) & 1u);
+            ee += __popc(em);
+            ep += __popc(pm);
+            seg = seg_join(seg, seg_window(em, pm));
+            if (i < e && bad == ~0ull && !word_ok(w[k]))
                 bad = i;
         }
     }
-    if (bad != ~0u)
-        report(d, w0 + bad, RANK_BAD);
-    // EE count in the high half, EP count in the low half (each < 2^32)
-    const unsigned long long tot = block_sum(((unsigned long long)ee << 32) | ep);
-    if (threadIdx.x == 0) {
-        d.chunk_ee[blockIdx.x] = (uint32_t)(tot >> 32);
-        d.chunk_ep[blockIdx.x] = (uint32_t)tot;
+    bad = warp_min_u64(bad);
+    __shared__ unsigned s_cnt[3][WARPS];
+    if (lane == 0) {
+        if (bad != ~0ull)
+            report(d, bad, RANK_BAD);
+        d.span_ee[sp] = ee;
+        d.span_ep[sp] = ep;
+        d.span_seg[sp] = seg;
+        s_cnt[0][warp_id()] = ee;
+        s_cnt[1][warp_id()] = ep;
+        s_cnt[2][warp_id()] = seg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // the CTA's spans together, after the per-warp entries
+        unsigned tee = 0, tep = 0, tseg = 0;
+#pragma unroll
+        for (unsigned w = 0; w < WARPS; ++w) {
+            tee += s_cnt[0][w];
+            tep += s_cnt[1][w];
+            tseg = seg_join(tseg, s_cnt[2][w]);
+        }
+        d.span_ee[MAX_SPANS + blockIdx.x] = tee;
+        d.span_ep[MAX_SPANS + blockIdx.x] = tep;
+        d.span_seg[MAX_SPANS + blockIdx.x] = tseg;
     }
 }
 
-// P1; false when the stream does not fit the context (every CTA sees the
-// same totals and stops)
-__device__ bool scan_scatter(const Dev &d, unsigned char *smem)
+// P1 of one warp.  A ballot scan of the span finds the roads that start in
+// it (the word after an EP word) with their road index, event and place in
+// the event, and queues them in shared memory; each batch of 32 queued roads
+// is decoded one road per lane, the lane walking its road's words from the
+// header to the EP word (past the span's end if need be).  Each lane builds
+// its road's coordinate row in shared memory; the batch's rows (consecutive
+// roads) are then copied out with 16-byte stores.
+constexpr unsigned P1_AHEAD = 4;                  // windows scanned per step (loads in flight together)
+constexpr unsigned P1_Q = (P1_AHEAD + 1) * WIN;  // queued road starts per warp
+struct P1Warp {
+    uint16_t row[WIN][40];           // coordinate rows of the batch's roads
+    uint32_t pos[P1_Q], g[P1_Q], ev[P1_Q], rie[P1_Q];   // queued roads: first word, index, event,
+                                                         // roads of the event before it
+};
+static_assert(sizeof(P1Warp) % 16 == 0, "warp regions of 16-byte multiples");
+
+// the longest road a lane walks: a road of more words breaks a rule within
+// its first MAX_ROAD_WORDS words (a ninth hit on some layer at the latest)
+constexpr unsigned MAX_ROAD_WORDS = 3 + N_LAYERS * MAX_HITS + 1;
+
+// Decode queued roads [off, off + cnt) (cnt <= 32) one per lane; returns the
+// batch's first fault (encoded as in Ctrl::err_inv, ~0 when none).
+__device__ __forceinline__ unsigned long long decode_batch(const Dev &d, P1Warp &q, unsigned off, unsigned cnt,
+                                                           unsigned n_events)
 {
-    ScanSmem &s = *reinterpret_cast<ScanSmem *>(smem);
-    unsigned long long w0, w1;
-    scan_slice(d, w0, w1);
-    const unsigned n = (unsigned)(w1 - w0);
-    const uint32_t *slice = d.words + w0;
-    // the first tile's loads go out before the sums over the CTA totals
-    uint32_t w[SCAN_PT];
-    if (n)
-        scan_load(slice, n, 0, w);
-    unsigned long long below = 0, all = 0;   // EE << 32 | EP
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += BLOCK) {
-        const unsigned long long v = ((unsigned long long)ldcg(d.chunk_ee + i) << 32) | ldcg(d.chunk_ep + i);
+    const unsigned lane = lane_id();
+    unsigned long long err = ~0ull;
+    bool done = false;   // a complete road (its EP word seen)
+    unsigned g = 0;
+    if (lane < cnt) {
+        const unsigned start = q.pos[off + lane], ev = q.ev[off + lane], rie = q.rie[off + lane];
+        g = q.g[off + lane];
+        uint16_t *row = q.row[lane];
+        unsigned long long cnt8 = 0;   // hits so far, layer l in bits 8 l .. 8 l + 7
+        uint32_t hdr = 0, cw = 0, pw = 0;
+        bool ee = false;
+        for (unsigned k0 = 0; k0 < MAX_ROAD_WORDS && !done && err == ~0ull; k0 += 8) {
+            uint32_t w4[8];
+#pragma unroll
+            for (unsigned u = 0; u < 8; ++u) {   // eight loads in flight
+                const unsigned long long p = (unsigned long long)start + k0 + u;
+                w4[u] = p < d.n_words ? __ldg(d.words + p) : 0u;
+            }
+#pragma unroll
+            for (unsigned u = 0; u < 8; ++u) {
+                const unsigned k = k0 + u;
+                const unsigned long long p = (unsigned long long)start + k;
+                if (done || err != ~0ull || k >= MAX_ROAD_WORDS || p >= d.n_words)
+                    break;
+                const uint32_t w = w4[u];
+                const unsigned type = (w >> 27) & 7u;
+                const bool ep = (w >> 30) & 1u;
+                bool bad;
+                if (k == 0) {
+                    bad = type != 7 || ep;
+                    hdr = w;
+                    if (!bad && rie >= (unsigned)MAX_ROADS_EV)
+                        err = (p << 8) | RANK_LIMIT;
+                } else if (k == 1) {
+                    bad = type != 5 || ep;
+                    cw = w;
+                } else if (k == 2) {
+                    bad = type != 6;
+                    pw = w;
+                } else {
+                    bad = type > 4;
+                    if (!bad) {
+                        const unsigned r = (unsigned)(cnt8 >> (8 * type)) & 0xFFu;
+                        if (r >= (unsigned)MAX_HITS)
+                            err = (p << 8) | RANK_LIMIT;
+                        else
+                            row[type * 8 + r] = (uint16_t)(w & 0xFFFu);
+                        cnt8 += 1ull << (8 * type);
+                    }
+                }
+                if (bad)
+                    err = (p << 8) | RANK_BAD;
+                else if (ep && err == ~0ull) {
+                    done = true;
+                    ee = (w >> 31) != 0;
+                }
+            }
+        }
+        if (done && g < d.max_roads) {   // a complete road: its record
+            unsigned pk = 0;
+#pragma unroll
+            for (unsigned l = 0; l < N_LAYERS; ++l)
+                pk |= min((unsigned)(cnt8 >> (8 * l)) & 0xFFu, (unsigned)MAX_HITS) << (4 * l);
+            const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
+            const unsigned excl = min((hdr >> 7) & 7u, 4u);
+            RoadRec r;
+            r.event = ev;
+            r.pk = pk | (excl << 20) | (min(rie, 255u) << 24);
+            r.curv = (int16_t)(cw & 0xFFFFu);
+            r.phi = (int16_t)(pw & 0xFFFFu);
+            r.set = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
+            r.cta = 0;
+            d.roads[g] = r;
+            if (ee && ev < d.max_events) {   // the event's last road
+                d.ev_road_end[ev] = g + 1;
+                if (ev + 1 == n_events)
+                    d.ctrl->n_roads = g + 1;
+            }
+        }
+    }
+    __syncwarp();
+    // the rows of the batch's complete roads (consecutive road indices from
+    // the first lane's), five 16-byte words each
+    const unsigned g0 = __shfl_sync(FULL_MASK, g, 0), dm = __ballot_sync(FULL_MASK, done);
+    const uint4 *src = reinterpret_cast<const uint4 *>(&q.row[0][0]);
+    uint4 *dst = reinterpret_cast<uint4 *>(d.coords + (size_t)g0 * 40);
+    for (unsigned i = lane; i < cnt * N_LAYERS; i += WIN) {
+        const unsigned j = i / N_LAYERS;
+        if (((dm >> j) & 1u) && g0 + j < d.max_roads)
+            dst[i] = src[i];
+    }
+    __syncwarp();
+    return warp_min_u64(err);
+}
+
+// P1 for one warp: the roads whose header lies in [a, e).  g, ev: EP and EE
+// words before a; rie: EP words since the last EE before a (roads of the open
+// event).
+__device__ void decode_span(const Dev &d, P1Warp &q, unsigned long long a, unsigned long long e, unsigned g,
+                            unsigned ev, unsigned rie, unsigned n_events)
+{
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    bool prev_ep = a == 0 || ((__ldg(d.words + a - 1) >> 30) & 1u);   // word a starts a road
+    unsigned qn = 0;
+    unsigned long long err = ~0ull;
+    for (unsigned long long W0 = a;; W0 += P1_AHEAD * WIN) {
+        const bool more = W0 < e && err == ~0ull;
+        if (more) {   // P1_AHEAD windows: their road starts join the queue
+            uint32_t wds[P1_AHEAD];
+#pragma unroll
+            for (unsigned k = 0; k < P1_AHEAD; ++k) {
+                const unsigned long long i = W0 + k * WIN + lane;
+                wds[k] = i < e ? __ldg(d.words + i) : 0u;
+            }
+#pragma unroll
+            for (unsigned k = 0; k < P1_AHEAD; ++k) {
+                const unsigned long long i = W0 + k * WIN + lane;
+                const bool in = i < e;
+                const uint32_t wd = wds[k];
+                const unsigned pm = __ballot_sync(FULL_MASK, in && ((wd >> 30) & 1u));
+                const unsigned em = __ballot_sync(FULL_MASK, in && (wd >> 31));
+                const unsigned sm = ((pm << 1) | (prev_ep ? 1u : 0u)) & __ballot_sync(FULL_MASK, in);
+                if ((sm >> lane) & 1u) {   // a road starts at this word
+                    const unsigned j = qn + __popc(sm & lt), em_lt = em & lt;
+                    q.pos[j] = (uint32_t)i;
+                    q.g[j] = g + __popc(pm & lt);
+                    q.ev[j] = ev + __popc(em & lt);
+                    q.rie[j] = em_lt ? __popc(pm & lt & ~((2u << (31 - __clz(em_lt))) - 1u)) : rie + __popc(pm & lt);
+                }
+                qn += __popc(sm);
+                g += __popc(pm);
+                ev += __popc(em);
+                rie = em ? (unsigned)__popc((pm >> (31 - __clz(em))) >> 1) : rie + __popc(pm);
+                prev_ep = (pm >> 31) & 1u;
+            }
+            __syncwarp();
+        }
+        // full batches of 32 roads, and at the end the rest
+        unsigned off = 0;
+        while (err == ~0ull && (qn - off >= WIN || (!more && qn > off))) {
+            const unsigned c = min(qn - off, WIN);
+            err = decode_batch(d, q, off, c, n_events);
+            off += c;
+        }
+        if (!more || err != ~0ull)
+            break;
+        if (off) {   // fewer than 32 left: to the front of the queue
+            const unsigned rest = qn - off;
+            uint32_t p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+            if (lane < rest) {
+                p0 = q.pos[off + lane];
+                p1 = q.g[off + lane];
+                p2 = q.ev[off + lane];
+                p3 = q.rie[off + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                q.pos[lane] = p0;
+                q.g[lane] = p1;
+                q.ev[lane] = p2;
+                q.rie[lane] = p3;
+            }
+            qn = rest;
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && err != ~0ull)
+        atomicMax(&d.ctrl->err_inv, ~err);   // the first fault of the batch is its status
+}
+
+// P1; false when the stream does not fit the context (every CTA sees the
+// same totals and stops).  smem: the CTA's shared memory (a P1Warp per warp).
+__device__ bool scan_decode(const Dev &d, unsigned char *smem)
+{
+    const unsigned mine0 = blockIdx.x * WARPS;
+    // the CTAs below this one (their aggregates follow the per-warp entries),
+    // and all CTAs (the stream's counts)
+    const unsigned per = (gridDim.x + BLOCK - 1) / BLOCK;
+    const unsigned c0 = min(threadIdx.x * per, gridDim.x), c1 = min(c0 + per, gridDim.x);
+    unsigned long long all = 0, below = 0;   // EE << 32 | EP
+    unsigned seg = 0;
+    for (unsigned c = c0; c < c1; ++c) {
+        const unsigned long long v = ((unsigned long long)ldcg(d.span_ee + MAX_SPANS + c) << 32) |
+                                     ldcg(d.span_ep + MAX_SPANS + c);
         all += v;
-        below += i < blockIdx.x ? v : 0ull;
+        if (c < blockIdx.x) {
+            below += v;
+            seg = seg_join(seg, ldcg(d.span_seg + MAX_SPANS + c));
+        }
     }
     block_sum2(all, below);
+    seg = block_seg_fold(seg);
     const unsigned n_ee = (unsigned)(all >> 32), n_ep = (unsigned)all;
     const bool fits = n_ee <= d.max_events && n_ep <= d.max_roads;
     // the candidate bits of this batch's roads start at zero (P2 sets them)
@@ -549,301 +709,66 @@ __device__ bool scan_scatter(const Dev &d, unsigned char *smem)
     }
     if (!fits)
         return false;
-    unsigned ev = (unsigned)(below >> 32), rd = (unsigned)below;
-    for (unsigned off = 0; off < n; off += SCAN_TILE) {
-        if (off)
-            scan_load(slice, n, off, w);
-#pragma unroll
-        for (unsigned k = 0; k < SCAN_PT; ++k)
-            s.w[scan_pad(threadIdx.x + k * BLOCK)] = w[k];
-        __syncthreads();
-        // thread t: words 32t .. 32t + 31 of the tile (zero past the slice)
-        const unsigned t0 = threadIdx.x * SCAN_PT;
-        unsigned cnt = 0;   // EE count in the high half, EP count in the low half (a tile: < 2^16)
-#pragma unroll
-        for (unsigned k = 0; k < SCAN_PT; ++k) {
-            const uint32_t x = s.w[scan_pad(t0 + k)];
-            cnt += ((x >> 31) << 16) | ((x >> 30) & 1u);
-        }
-        static_assert(SCAN_TILE < 65536, "tile counts fit 16 bits");
-        unsigned tot;
-        const unsigned ex = block_excl_scan32(cnt, &tot);
-        unsigned my_ev = ev + (ex >> 16), my_rd = rd + (ex & 0xFFFFu);
-#pragma unroll
-        for (unsigned k = 0; k < SCAN_PT; ++k) {
-            const uint32_t x = s.w[scan_pad(t0 + k)];
-            my_rd += (x >> 30) & 1u;
-            if (x >> 31) {
-                if (my_ev < d.max_events) {
-                    d.ev_word_end[my_ev] = (uint32_t)(w0 + off + t0 + k);
-                    d.ev_road_end[my_ev] = my_rd;
-                }
-                if (my_ev + 1 == n_ee)
-                    d.ctrl->n_roads = my_rd;
-                ++my_ev;
-            }
-        }
-        ev += tot >> 16;
-        rd += tot & 0xFFFFu;
-        __syncthreads();   // the tile buffer is refilled next
+    // the spans of this CTA below this warp
+    unsigned g = (unsigned)below, ev = (unsigned)(below >> 32);
+    {
+        const unsigned j = lane_id(), sp = mine0 + j;
+        const bool b4 = j < warp_id();
+        g += warp_sum(b4 ? ldcg(d.span_ep + sp) : 0u);
+        ev += warp_sum(b4 ? ldcg(d.span_ee + sp) : 0u);
+        seg = seg_join(seg, warp_seg_fold(b4 ? ldcg(d.span_seg + sp) : 0u));
     }
+    unsigned long long a, e;
+    span_of(d, mine0 + warp_id(), a, e);
+    P1Warp &q = reinterpret_cast<P1Warp *>(smem)[warp_id()];
+    decode_span(d, q, a, e, g, ev, seg & ~SEG_EE, n_ee);
     return true;
 }
 
 // ---------------------------------------------------------------------------
-// P2: one event per CTA
+// P2: the cross-road flags of each event (one CTA per event).  A track can
+// only be dropped by a track of another road that shares hits with it on
+// three layers, so only road pairs with a coordinate in common on >= 3
+// layers matter.  The coordinates of the event that appear in two or more
+// roads (per-layer bitmaps) get, per road and layer, a 64-bit signature;
+// pairs of roads whose signatures meet on >= 3 layers take the exact test,
+// which marks the shared hits of both roads.  A road with a marked hit is a
+// cross-road candidate; its marked hits are the ones it publishes and looks
+// up.  The road records get the candidate bit and their fit path.
 // ---------------------------------------------------------------------------
 
+constexpr unsigned P2_PAIRS = 1024;   // road pairs queued for the exact test (more: tested in place)
+
 struct P2Smem {
-    uint32_t end[MAX_ROADS_EV];           // word position of each road's EP
-    uint32_t pk[MAX_ROADS_EV];            // RoadRec::pk without the candidate bit
-    uint32_t cp[MAX_ROADS_EV];            // curv | phi << 16
-    uint16_t set[MAX_ROADS_EV];
-    uint8_t rep[MAX_ROADS_EV];            // a coordinate repeated within a layer of the road
+    RoadRec rec[MAX_ROADS_EV];
     uint16_t coord[MAX_ROADS_EV][40];     // [road][layer * 8 + hit]
+    unsigned long long sig[MAX_ROADS_EV][N_LAYERS];   // signatures of a road's shared coordinates
     uint32_t seen[N_LAYERS][128];         // coordinate bitmaps of the event
     uint32_t multi[N_LAYERS][128];
-    uint32_t sig[MAX_ROADS_EV][N_LAYERS]; // per road and layer: 32-bit signature of its coordinates
-                                          // that appear in another road of the event
     uint32_t xlo[MAX_ROADS_EV];           // hits shared with a road that shares coordinates on
     uint32_t xhi[MAX_ROADS_EV];           //   >= 3 layers: bit 8 l + d (l < 4), layer 4 in xhi
-    unsigned long long err;               // smallest fault of this event (encoded)
-    uint32_t n_ep, n_seg, last_ep;
-    unsigned long long nx_w0, nx_w1;      // the CTA's next event: its words, first road, index
-    uint32_t nx_r0, nx_e;
+    uint16_t elig[MAX_ROADS_EV];          // roads with shared coordinates on >= 3 layers
+    uint32_t cp[P2_PAIRS];                // road pairs whose signatures meet on >= 3 layers (r | t << 16)
+    uint8_t rep[MAX_ROADS_EV];            // a coordinate repeated within a layer of the road
+    unsigned n_elig, n_cp;
 };
+static_assert(offsetof(P2Smem, coord) % 16 == 0 && offsetof(P2Smem, rec) % 16 == 0, "16-byte rows");
 
-// The CTA's next event, claimed by thread 0 while the current one is
-// unpacked: the claim goes out at the start, the event's word and road
-// offsets are loaded midway, and they are published at the end.
-struct P2Next {
-    unsigned claim, e, r0;
-    unsigned long long w0, w1;
-};
+// signature bit of a coordinate: a multiplicative hash into 0..63
+__device__ __forceinline__ unsigned sig_bit(unsigned v) { return (v * 0x9E3779B1u) >> 26; }
 
-// words [w0, w1] and first road r0 of item e (the item after the last event
-// is the truncated tail)
-__device__ __forceinline__ void event_span(const Dev &d, unsigned e, unsigned n_events, unsigned long long &w0,
-                                           unsigned long long &w1, unsigned &r0)
+__device__ __forceinline__ bool is_multi(const P2Smem &s, unsigned l, unsigned v)
 {
-    w0 = e == 0 ? 0ull : (unsigned long long)ldcg(d.ev_word_end + e - 1) + 1;
-    w1 = e >= n_events ? d.n_words - 1 : (unsigned long long)ldcg(d.ev_word_end + e);
-    r0 = e == 0 ? 0u : ldcg(d.ev_road_end + e - 1);
+    return (s.multi[l][v >> 5] >> (v & 31u)) & 1u;
 }
-
-constexpr unsigned ROAD_THREADS = 4;                      // threads per road in P2
-constexpr unsigned ROADS_PER_PASS = BLOCK / ROAD_THREADS;
-
-// OR over the four threads of a road (lanes 4i .. 4i+3 of a warp)
-__device__ __forceinline__ unsigned group_or(unsigned x)
-{
-    x |= __shfl_xor_sync(FULL_MASK, x, 1, ROAD_THREADS);
-    x |= __shfl_xor_sync(FULL_MASK, x, 2, ROAD_THREADS);
-    return x;
-}
-
-// decode_road for a warp with a road of 256 words or more (malformed input
-// only): per-layer counters, eight loads in flight, words reloaded (L1) in
-// pass 2.  The whole warp takes this path (its shuffles span the warp).
-__device__ void decode_road_long(const Dev &d, P2Smem &s, unsigned k, unsigned sub, unsigned start,
-                                 unsigned len, unsigned qa, unsigned qb, uint32_t &hdr, uint32_t &cw,
-                                 uint32_t &pw, unsigned (&total)[N_LAYERS], unsigned long long &err)
-{
-    const uint32_t *rw = d.words + start;
-    unsigned c[N_LAYERS] = {0, 0, 0, 0, 0};
-    // pass 1: grammar, the road's first three words, hits per layer
-    for (unsigned base = qa; base < qb; base += 8) {
-        uint32_t wb[8];
-#pragma unroll
-        for (unsigned u = 0; u < 8; ++u)
-            wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
-#pragma unroll
-        for (unsigned u = 0; u < 8; ++u) {
-            const unsigned q = base + u;
-            if (q >= qb)
-                break;
-            const uint32_t w = wb[u];
-            const unsigned type = (w >> 27) & 7u, ep = (w >> 30) & 1u;
-            if ((q == 0 && type != 7) || (q == 1 && type != 5) || (q == 2 && type != 6) || (q >= 3 && type > 4) ||
-                (ep && q < 2))
-                err = min(err, ((unsigned long long)(start + q) << 8) | RANK_BAD);
-            if (q == 0)
-                hdr = w;
-            else if (q == 1)
-                cw = w;
-            else if (q == 2)
-                pw = w;
-            else if (type <= 4)
-#pragma unroll
-                for (unsigned l = 0; l < N_LAYERS; ++l)
-                    c[l] += type == l;
-        }
-    }
-    // ranks: exclusive scan of the per-layer counts over the group
-    unsigned rank[N_LAYERS];
-#pragma unroll
-    for (unsigned l = 0; l < N_LAYERS; ++l) {
-        unsigned inc = c[l];
-#pragma unroll
-        for (unsigned o = 1; o < ROAD_THREADS; o <<= 1) {
-            const unsigned v = __shfl_up_sync(FULL_MASK, inc, o, ROAD_THREADS);
-            if (sub >= o)
-                inc += v;
-        }
-        rank[l] = inc - c[l];
-        total[l] = __shfl_sync(FULL_MASK, inc, ROAD_THREADS - 1, ROAD_THREADS);
-    }
-    (void)len;
-    // pass 2: place the hits (the words are in L1)
-    for (unsigned base = max(qa, 3u); base < qb; base += 8) {
-        uint32_t wb[8];
-#pragma unroll
-        for (unsigned u = 0; u < 8; ++u)
-            wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
-#pragma unroll
-        for (unsigned u = 0; u < 8; ++u) {
-            const unsigned q = base + u;
-            if (q >= qb)
-                break;
-            const uint32_t w = wb[u];
-            const unsigned type = (w >> 27) & 7u;
-            if (type > 4)
-                continue;
-            unsigned r = 0;
-#pragma unroll
-            for (unsigned l = 0; l < N_LAYERS; ++l)
-                if (type == l)
-                    r = rank[l]++;
-            if (r >= MAX_HITS)
-                err = min(err, ((unsigned long long)(start + q) << 8) | RANK_LIMIT);
-            else
-                s.coord[k][type * 8 + r] = (uint16_t)(w & 0xFFFu);
-        }
-    }
-}
-
-// Decode road k of the event: words [start, end] (absolute positions, below
-// 2^31), four threads per road, thread `sub` taking a quarter of the words.
-// Every lane of the warp calls it (`active` false for lanes without a road).
-// Pass 1 checks the grammar and counts the hits per layer; a scan over the
-// four threads gives each hit its rank in its layer; pass 2 places the hits
-// (unused hit slots stay 0).  When every road of the warp is shorter than
-// 256 words, the counts and ranks of layers 0..3 are packed in 8-bit fields
-// of one word (no field can overflow) and a thread's words stay in
-// registers between the passes when it has at most four; otherwise
-// (malformed long roads) per-layer counters are used.
-__device__ void decode_road(const Dev &d, P2Smem &s, bool active, unsigned k, unsigned sub,
-                            unsigned start, unsigned end, unsigned long long &err)
-{
-    const unsigned len = active && end >= start ? end - start + 1 : 0u;
-    const unsigned per = (len + ROAD_THREADS - 1) / ROAD_THREADS;
-    const unsigned qa = min(sub * per, len), qb = min(qa + per, len);
-    const uint32_t *rw = d.words + start;
-    uint32_t hdr = 0, cw = 0, pw = 0;
-    unsigned total[N_LAYERS];
-    if (__all_sync(FULL_MASK, len < 256)) {
-        unsigned cnt = 0, c4 = 0;   // hits of layers 0..3 (8 bits each) and of layer 4
-        uint32_t wb[4];
-        for (unsigned base = qa; base < qb; base += 4) {
-#pragma unroll
-            for (unsigned u = 0; u < 4; ++u)   // four loads in flight
-                wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
-#pragma unroll
-            for (unsigned u = 0; u < 4; ++u) {
-                const unsigned q = base + u;
-                if (q >= qb)
-                    break;
-                const uint32_t w = wb[u];
-                const unsigned type = (w >> 27) & 7u;
-                bool bad;
-                if (q < 3) {   // header (type 7), curvature (5), phi (6); no EP in the first two
-                    bad = type != ((0x657u >> (4 * q)) & 15u) || (q < 2 && ((w >> 30) & 1u));
-                    hdr = q == 0 ? w : hdr;
-                    cw = q == 1 ? w : cw;
-                    pw = q == 2 ? w : pw;
-                } else {
-                    bad = type > 4;
-                    cnt += type < 4 ? 1u << (8 * type) : 0u;
-                    c4 += type == 4;
-                }
-                if (bad)
-                    err = min(err, ((unsigned long long)(start + q) << 8) | RANK_BAD);
-            }
-        }
-        // ranks: exclusive scan of the counts over the four threads
-        unsigned ic = cnt, i4 = c4;
-#pragma unroll
-        for (unsigned o = 1; o < ROAD_THREADS; o <<= 1) {
-            const unsigned vc = __shfl_up_sync(FULL_MASK, ic, o, ROAD_THREADS);
-            const unsigned v4 = __shfl_up_sync(FULL_MASK, i4, o, ROAD_THREADS);
-            if (sub >= o) {
-                ic += vc;
-                i4 += v4;
-            }
-        }
-        const unsigned tc = __shfl_sync(FULL_MASK, ic, ROAD_THREADS - 1, ROAD_THREADS);
-        total[4] = __shfl_sync(FULL_MASK, i4, ROAD_THREADS - 1, ROAD_THREADS);
-#pragma unroll
-        for (unsigned l = 0; l < 4; ++l)
-            total[l] = (tc >> (8 * l)) & 0xFFu;
-        unsigned rk = ic - cnt, r4 = i4 - c4;
-        // pass 2: place the hits
-        const bool held = per <= 4;
-        for (unsigned base = qa; base < qb; base += 4) {
-            if (!held) {
-#pragma unroll
-                for (unsigned u = 0; u < 4; ++u)
-                    wb[u] = base + u < qb ? __ldg(rw + base + u) : 0u;
-            }
-#pragma unroll
-            for (unsigned u = 0; u < 4; ++u) {
-                const unsigned q = base + u;
-                if (q >= qb)
-                    break;
-                const uint32_t w = wb[u];
-                const unsigned type = (w >> 27) & 7u;
-                if (q < 3 || type > 4)
-                    continue;
-                unsigned r;
-                if (type < 4) {
-                    r = (rk >> (8 * type)) & 0xFFu;
-                    rk += 1u << (8 * type);
-                } else {
-                    r = r4++;
-                }
-                if (r >= MAX_HITS)
-                    err = min(err, ((unsigned long long)(start + q) << 8) | RANK_LIMIT);
-                else
-                    s.coord[k][type * 8 + r] = (uint16_t)(w & 0xFFFu);
-            }
-        }
-    } else {
-        decode_road_long(d, s, k, sub, start, len, qa, qb, hdr, cw, pw, total, err);
-    }
-    hdr = group_or(hdr);
-    cw = group_or(cw);
-    pw = group_or(pw);
-    if (active && sub == 0) {
-        const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
-        const unsigned excl = min((hdr >> 7) & 7u, 4u);
-        const unsigned mh = MAX_HITS;
-        s.pk[k] = min(total[0], mh) | (min(total[1], mh) << 4) | (min(total[2], mh) << 8) |
-                  (min(total[3], mh) << 12) | (min(total[4], mh) << 16) | (excl << 20) | ((k & 255u) << 24);
-        s.cp[k] = (cw & 0xFFFFu) | (pw << 16);
-        s.set[k] = (uint16_t)((wedge * 6 + barrel) * 5 + excl);
-        s.rep[k] = 0;   // set by the bitmap step
-    }
-}
-
-// signature bit of a coordinate: a multiplicative hash into 0..31
-__device__ __forceinline__ unsigned sig_bit(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
 
 // Roads r and t of the event: the layers on which they hold a common
 // coordinate and the hits involved; with three or more such layers, the
-// shared hits of both roads are marked.
+// shared hits of both roads are marked.  Only coordinates present in two
+// roads can be common.
 __device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
 {
-    const uint32_t pr = s.pk[r], pt = s.pk[t];
+    const uint32_t pr = s.rec[r].pk, pt = s.rec[t].pk;
     unsigned lo_r = 0, lo_t = 0, hi_r = 0, hi_t = 0, layers = 0;
 #pragma unroll
     for (unsigned l = 0; l < N_LAYERS; ++l) {
@@ -851,6 +776,8 @@ __device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
         unsigned br = 0, bt = 0;
         for (unsigned x = 0; x < nr; ++x) {
             const unsigned v = s.coord[r][l * 8 + x];
+            if (!is_multi(s, l, v))
+                continue;
             for (unsigned y = 0; y < nt; ++y)
                 if (s.coord[t][l * 8 + y] == v) {
                     br |= 1u << x;
@@ -874,190 +801,146 @@ __device__ void pair_exact(P2Smem &s, unsigned r, unsigned t)
     }
 }
 
-// Unpack event e (CTA-wide); adds the event's combinations to n_comb.
-__device__ __forceinline__ void p2_publish_next(P2Smem &s, const P2Next &nx)
+// The exact test of pair_exact by a whole warp: lane 8 l + x (then lane x
+// for layer 4) takes hit x of road r on layer l and compares it with road t's
+// hits on that layer.
+__device__ void pair_exact_warp(P2Smem &s, unsigned r, unsigned t)
 {
-    if (threadIdx.x == 0) {
-        s.nx_e = nx.e;
-        s.nx_w0 = nx.w0;
-        s.nx_w1 = nx.w1;
-        s.nx_r0 = nx.r0;
+    const unsigned lane = lane_id();
+    const uint32_t pr = s.rec[r].pk, pt = s.rec[t].pk;
+    unsigned m_r[2], m_t[2];   // marked hits of r and t: layers 0..3, then layer 4
+#pragma unroll
+    for (unsigned pass = 0; pass < 2; ++pass) {
+        const unsigned l = pass ? 4u : lane >> 3, x = pass ? lane : lane & 7u;
+        const unsigned nr = (pr >> (4 * l)) & 15u, nt = (pt >> (4 * l)) & 15u;   // <= MAX_HITS
+        unsigned br = 0, bt = 0;
+        if (x < nr && (!pass || lane < 8)) {
+            const unsigned v = s.coord[r][l * 8 + x];
+            if (is_multi(s, l, v))
+                for (unsigned y = 0; y < nt; ++y)
+                    if (s.coord[t][l * 8 + y] == v) {
+                        br = 1u << x;
+                        bt |= 1u << y;
+                    }
+        }
+        const unsigned sh = pass ? 0u : 8 * l;
+        m_r[pass] = __reduce_or_sync(FULL_MASK, br << sh);
+        m_t[pass] = __reduce_or_sync(FULL_MASK, bt << sh);
+    }
+    const unsigned layers = ((m_r[0] & 0xFFu) != 0) + ((m_r[0] & 0xFF00u) != 0) + ((m_r[0] & 0xFF0000u) != 0) +
+                            ((m_r[0] >> 24) != 0) + (m_r[1] != 0);
+    if (layers >= 3 && lane == 0) {
+        atomicOr(&s.xlo[r], m_r[0]);
+        atomicOr(&s.xhi[r], m_r[1]);
+        atomicOr(&s.xlo[t], m_t[0]);
+        atomicOr(&s.xhi[t], m_t[1]);
     }
 }
 
-__device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsigned long long w1, unsigned r0,
-                         unsigned n_events, unsigned n_items, unsigned char *smem, unsigned long long &n_comb,
-                         P2Next &nx)
+// Flags of event e (roads r0 .. r0 + nr - 1); adds its combinations to n_comb.
+__device__ void p2_event(const Dev &d, unsigned e, unsigned r0, unsigned nr, unsigned char *smem,
+                         unsigned long long &n_comb)
 {
     P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
-    const bool tail = e >= n_events;
-    if (threadIdx.x == 0) {
-        nx.claim = atomicAdd(&d.ctrl->q[Q_P2], 1u);   // used midway
-        s.err = ~0ull;
-        s.n_ep = 0;
+    // the event's roads: records and coordinate rows (16-byte loads)
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
+        s.rec[k] = ldcg(d.roads + r0 + k);
+        s.rep[k] = 0;
+        s.xlo[k] = 0;
+        s.xhi[k] = 0;
     }
-    // the hit slots and the coordinate bitmaps start at zero (the scan's
-    // barriers order these stores before their first use)
     {
-        uint4 *z = reinterpret_cast<uint4 *>(&s.coord[0][0]);
-        static_assert(sizeof(s.coord) % 16 == 0 && offsetof(P2Smem, coord) % 16 == 0, "16-byte stores");
-        for (unsigned i = threadIdx.x; i < sizeof(s.coord) / 16; i += BLOCK)
-            z[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
-            (&s.seen[0][0])[i] = 0;
-            (&s.multi[0][0])[i] = 0;
-        }
+        const uint4 *src = reinterpret_cast<const uint4 *>(d.coords + (size_t)r0 * 40);
+        uint4 *dst = reinterpret_cast<uint4 *>(&s.coord[0][0]);
+        for (unsigned i = threadIdx.x; i < nr * N_LAYERS; i += BLOCK)
+            dst[i] = ldcg(src + i);
     }
-    // road boundaries: ranks of the EP words of [w0, w1] (positions below
-    // 2^31).  Each thread takes a run of up to 64 consecutive words per round
-    // (one block scan).
-    unsigned running = 0;
-    const unsigned e0 = (unsigned)w0, e1 = (unsigned)w1;
-    for (unsigned rw = e0; rw <= e1; rw += BLOCK * 64) {
-        const unsigned len = min(e1 + 1 - rw, (unsigned)(BLOCK * 64));
-        const unsigned per = (len + BLOCK - 1) / BLOCK;
-        const unsigned a = rw + threadIdx.x * per, lim = min(per, len - min(threadIdx.x * per, len));
-        unsigned long long bits = 0;
-        for (unsigned j0 = 0; j0 < lim; j0 += 4) {   // four loads in flight
-            uint32_t w[4];
-#pragma unroll
-            for (unsigned u = 0; u < 4; ++u)
-                w[u] = j0 + u < lim ? __ldg(d.words + a + j0 + u) : 0u;
-#pragma unroll
-            for (unsigned u = 0; u < 4; ++u)
-                bits |= (unsigned long long)((w[u] >> 30) & 1u) << (j0 + u);
-        }
-        if (e1 >= a && e1 - a < lim)   // the event's last word: an EP word or not
-            s.last_ep = (unsigned)(bits >> (e1 - a)) & 1u;
-        unsigned tot;
-        unsigned k = running + block_excl_scan32((unsigned)__popcll(bits), &tot);
-        for (; bits; bits &= bits - 1, ++k)
-            if (k < MAX_ROADS_EV)
-                s.end[k] = a + (unsigned)(__ffsll((long long)bits) - 1);
-        running += tot;
+    for (unsigned i = threadIdx.x; i < N_LAYERS * 128; i += BLOCK) {
+        (&s.seen[0][0])[i] = 0;
+        (&s.multi[0][0])[i] = 0;
     }
-    const bool last_ep = s.last_ep != 0;   // written before the last scan's barriers
-    unsigned n_seg = running + (last_ep ? 0u : 1u);
-    if (threadIdx.x == 0)
-        s.n_ep = running;
-    __syncthreads();
-    if (n_seg > MAX_ROADS_EV && threadIdx.x == 0)
-        s.err = min(s.err, ((unsigned long long)(s.end[MAX_ROADS_EV - 1] + 1ull) << 8) | RANK_LIMIT);
-    unsigned nr = min(n_seg, (unsigned)MAX_ROADS_EV);
-
-    // decode: four threads per road; unused hit slots stay 0
-    unsigned long long err = ~0ull;
-    const unsigned sub = threadIdx.x % ROAD_THREADS;
-    for (unsigned kb = 0; kb < nr; kb += ROADS_PER_PASS) {
-        const unsigned k = kb + threadIdx.x / ROAD_THREADS;
-        const bool active = k < nr;
-        decode_road(d, s, active, k, sub, !active || k == 0 ? (unsigned)w0 : s.end[k - 1] + 1u,
-                    !active ? (unsigned)w0 : k < running ? s.end[k] : (unsigned)w1, err);
-    }
-    err = warp_min_u64(err);
-    if (lane_id() == 0 && err != ~0ull)
-        atomicMin(&s.err, err);
-    __syncthreads();
     if (threadIdx.x == 0) {
-        if (s.err != ~0ull)
-            atomicMax(&d.ctrl->err_inv, ~s.err);
-        // the next event: its offsets are loaded now, published at the end
-        nx.e = gridDim.x + nx.claim;
-        if (nx.e < n_items)
-            event_span(d, nx.e, n_events, nx.w0, nx.w1, nx.r0);
+        s.n_elig = 0;
+        s.n_cp = 0;
     }
-    if (tail) {
-        p2_publish_next(s, nx);
-        return;
+    __syncthreads();
+    // coordinates present in >= 2 roads on a layer: each distinct coordinate
+    // of a road's layer marks the bitmap, a second road with it the multi bit
+    for (unsigned i = threadIdx.x; i < nr * N_LAYERS; i += BLOCK) {
+        const unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
+        const unsigned n = (s.rec[k].pk >> (4 * l)) & 15u;
+        bool rep = false;
+        for (unsigned x = 0; x < n; ++x) {
+            const unsigned v = s.coord[k][l * 8 + x];
+            bool first = true;
+            for (unsigned y = 0; y < x; ++y)
+                first = first && s.coord[k][l * 8 + y] != v;
+            if (first) {
+                const unsigned bit = 1u << (v & 31u);
+                if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
+                    atomicOr(&s.multi[l][v >> 5], bit);
+            }
+            rep = rep || !first;
+        }
+        if (rep)
+            s.rep[k] = 1;
     }
-
-    // cross-road flags: coordinates present in >= 2 roads on the same layer.
-    // Each distinct coordinate of a road's layer marks the event's bitmap; a
-    // second road with it sets the multi bit.  Thread q of a road takes
-    // layer q and the hits q, q + 4 of layer 4.
-    static_assert(ROAD_THREADS == 4 && N_LAYERS == 5, "four threads per road: layers 0..3, then layer 4 shared");
-    for (unsigned i = threadIdx.x; i < nr * ROAD_THREADS; i += BLOCK) {
-        const unsigned k = i / ROAD_THREADS, q = i % ROAD_THREADS;
-        const uint32_t pk = s.pk[k];
-        for (unsigned pass = 0; pass < 2; ++pass) {
-            const unsigned l = pass ? 4u : q;
-            const unsigned n = (pk >> (4 * l)) & 15u;
-            for (unsigned dd = pass ? q : 0u; dd < n; dd += pass ? ROAD_THREADS : 1u) {
-                const unsigned v = s.coord[k][l * 8 + dd];
-                bool first = true;
-                for (unsigned x = 0; x < dd; ++x)
-                    first = first && s.coord[k][l * 8 + x] != v;
-                if (first) {
-                    const unsigned bit = 1u << (v & 31u);
-                    if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
-                        atomicOr(&s.multi[l][v >> 5], bit);
-                } else {
-                    s.rep[k] = 1;
-                }
+    __syncthreads();
+    // signatures of the shared coordinates; roads with >= 3 such layers
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
+        unsigned layers = 0;
+#pragma unroll
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned n = (s.rec[k].pk >> (4 * l)) & 15u;
+            unsigned long long sg = 0;
+            for (unsigned x = 0; x < n; ++x) {
+                const unsigned v = s.coord[k][l * 8 + x];
+                if (is_multi(s, l, v))
+                    sg |= 1ull << sig_bit(v);
+            }
+            s.sig[k][l] = sg;
+            layers += sg != 0;
+        }
+        if (layers >= 3)
+            s.elig[atomicAdd(&s.n_elig, 1u)] = (uint16_t)k;
+    }
+    __syncthreads();
+    // pairs of eligible roads whose signatures meet on >= 3 layers
+    const unsigned ne = s.n_elig;
+    for (unsigned a = warp_id(); a < ne; a += WARPS) {
+        const unsigned r = s.elig[a];
+        const unsigned long long s0 = s.sig[r][0], s1 = s.sig[r][1], s2 = s.sig[r][2], s3 = s.sig[r][3],
+                                 s4 = s.sig[r][4];
+        for (unsigned b = a + 1 + lane_id(); b < ne; b += 32) {
+            const unsigned t = s.elig[b];
+            const unsigned c = ((s0 & s.sig[t][0]) != 0) + ((s1 & s.sig[t][1]) != 0) + ((s2 & s.sig[t][2]) != 0) +
+                               ((s3 & s.sig[t][3]) != 0) + ((s4 & s.sig[t][4]) != 0);
+            if (c >= 3) {   // queued for a warp's exact test (in place when the queue is full)
+                const unsigned k = atomicAdd(&s.n_cp, 1u);
+                if (k < P2_PAIRS)
+                    s.cp[k] = r | (t << 16);
+                else
+                    pair_exact(s, r, t);
             }
         }
     }
     __syncthreads();
-
-    // Cross-road pairs.  A track can only be dropped by a track of another
-    // road that shares hits with it on three layers, so only road pairs with
-    // a coordinate in common on >= 3 layers matter.  Each road's coordinates
-    // that appear in another road (the multi bitmap) get a 32-bit signature
-    // per layer; pairs whose signatures meet on >= 3 layers take the exact
-    // test, which marks the shared hits of both roads.  A road with a marked
-    // hit is a cross-road candidate; its marked hits are the ones it
-    // publishes and looks up.
-    const unsigned nroad = min(nr, s.n_ep);   // EP-terminated segments are the roads
-    for (unsigned i = threadIdx.x; i < nroad * N_LAYERS; i += BLOCK) {
-        const unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
-        const unsigned n = (s.pk[k] >> (4 * l)) & 15u;   // <= MAX_HITS (decode clamps it)
-        unsigned sg = 0;
-        for (unsigned x = 0; x < n; ++x) {
-            const unsigned v = s.coord[k][l * 8 + x];
-            if ((s.multi[l][v >> 5] >> (v & 31u)) & 1u)
-                sg |= 1u << sig_bit(v);
-        }
-        s.sig[k][l] = sg;
-    }
-    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
-        s.xlo[k] = 0;
-        s.xhi[k] = 0;
-    }
+    for (unsigned k = warp_id(); k < min(s.n_cp, P2_PAIRS); k += WARPS)
+        pair_exact_warp(s, s.cp[k] & 0xFFFFu, s.cp[k] >> 16);
     __syncthreads();
-    for (unsigned r = warp_id(); r < nroad; r += WARPS) {
-        const unsigned s0 = s.sig[r][0], s1 = s.sig[r][1], s2 = s.sig[r][2], s3 = s.sig[r][3], s4 = s.sig[r][4];
-        if ((s0 != 0) + (s1 != 0) + (s2 != 0) + (s3 != 0) + (s4 != 0) < 3)
-            continue;
-        for (unsigned t = r + 1 + lane_id(); t < nroad; t += 32) {
-            const unsigned c = ((s0 & s.sig[t][0]) != 0) + ((s1 & s.sig[t][1]) != 0) + ((s2 & s.sig[t][2]) != 0) +
-                               ((s3 & s.sig[t][3]) != 0) + ((s4 & s.sig[t][4]) != 0);
-            if (c >= 3)
-                pair_exact(s, r, t);
-        }
-    }
-    __syncthreads();
-
-    // the road records, one thread per road, then the coordinates (coalesced)
-    for (unsigned k = threadIdx.x; k < nroad; k += BLOCK) {
+    // the road records: candidate bit and fit path
+    for (unsigned k = threadIdx.x; k < nr; k += BLOCK) {
         const unsigned g = r0 + k;
-        if (g >= d.max_roads)
-            continue;
-        const uint32_t pk = s.pk[k];
+        RoadRec r = s.rec[k];
         const unsigned long long xm = ((unsigned long long)s.xhi[k] << 32) | s.xlo[k];
-        const bool cand = xm != 0ull;
-        const bool rep = s.rep[k] != 0;   // a coordinate repeated within a layer
-        RoadRec r;
-        r.event = e;
-        r.pk = pk | (cand ? (1u << 23) : 0u);
-        r.curv = (int16_t)(s.cp[k] & 0xFFFFu);
-        r.phi = (int16_t)(s.cp[k] >> 16);
-        r.set = s.set[k];
+        const bool cand = xm != 0ull, rep = s.rep[k] != 0;
         unsigned N, N4;
-        road_sizes(pk, N, N4);
+        road_sizes(r.pk, N, N4);
         // fitted by one warp each (the box path): roads with more distinct
         // fits than a warp's run takes, and cross-road candidates with a
         // repeated coordinate (they publish over canonical hits)
         const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep));
+        r.pk |= cand ? (1u << 23) : 0u;
         r.cta = (big ? 1 : 0) | (rep ? 2 : 0);
         d.roads[g] = r;
         d.xmask[g] = xm;
@@ -1071,44 +954,26 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned long long w0, unsign
             atomicOr(&d.cand_bits[g >> 5], 1u << (g & 31u));
         n_comb += N;
     }
-    {   // 16 bytes per store (a road's row is five 16-byte words)
-        uint4 *dst = reinterpret_cast<uint4 *>(d.coords + (size_t)r0 * 40);
-        const uint4 *src = reinterpret_cast<const uint4 *>(&s.coord[0][0]);
-        for (unsigned i = threadIdx.x; i < nr * N_LAYERS; i += BLOCK) {
-            const unsigned k = i / N_LAYERS, g = r0 + k;
-            if (k < s.n_ep && g < d.max_roads)
-                dst[i] = src[i];
-        }
-    }
-    p2_publish_next(s, nx);
+    __syncthreads();   // the shared arrays are refilled for the next event
 }
 
 // P2 over the event queue; one combination-count atomic per CTA
 __device__ void p2_phase(const Dev &d, unsigned char *smem)
 {
-    P2Smem &s = *reinterpret_cast<P2Smem *>(smem);
-    const unsigned n_events = ldcg(&d.ctrl->n_events);
-    const unsigned n_items = n_events + ldcg(&d.ctrl->has_tail);
+    if (ldcg(&d.ctrl->err_inv) != 0ull)
+        return;   // a data fault (every CTA reads the same word after the barrier): no tracks
+    const unsigned n_events = min(ldcg(&d.ctrl->n_events), d.max_events);
     // survivor totals of the road chunks start at zero (the fit adds to them)
     const unsigned n_chunks = min((ldcg(&d.ctrl->n_roads) + ROAD_CHUNK - 1) / ROAD_CHUNK, d.max_chunks_r);
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_chunks; i += gridDim.x * BLOCK)
         d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
-    // the CTA's first event is its own index; each event claims the next
-    if (threadIdx.x == 0) {
-        s.nx_e = blockIdx.x;
-        if (blockIdx.x < n_items)
-            event_span(d, blockIdx.x, n_events, s.nx_w0, s.nx_w1, s.nx_r0);
-    }
-    __syncthreads();
-    P2Next nx{0u, 0u, 0u, 0ull, 0ull};
-    for (;;) {
-        const unsigned e = s.nx_e, r0 = s.nx_r0;
-        const unsigned long long w0 = s.nx_w0, w1 = s.nx_w1;
-        if (e >= n_items)
-            break;
-        p2_event(d, e, w0, w1, r0, n_events, n_items, smem, n_comb, nx);
-        __syncthreads();   // the next event is published
+    // the CTA's first event is its own index, the queue hands out the rest
+    for (unsigned e = blockIdx.x; e < n_events; e = grab_after_first(d, Q_P2)) {
+        const unsigned r0 = e == 0 ? 0u : min(ldcg(d.ev_road_end + e - 1), d.max_roads);
+        const unsigned r1 = min(ldcg(d.ev_road_end + e), d.max_roads);
+        // an event of more than MAX_ROADS_EV roads is a fault (reported in P1)
+        p2_event(d, e, r0, min(r1 - min(r0, r1), (unsigned)MAX_ROADS_EV), smem, n_comb);
     }
     n_comb = block_sum(n_comb);
     if (threadIdx.x == 0 && n_comb)
@@ -1811,6 +1676,8 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 //               warp reduction, only where a candidate or a group needs it
 //   T_ac, T_bc  the lane's minimum over w at each z, folded over the lanes
 //   T_ae, T_be  the lane's minimum over z for each w, folded at the end
+// (the lane minima are folded by shared-memory atomics; folding them through
+// scratch rows or warp shuffles measured slower)
 // A fit survives the road-local warrior iff its key is the minimum of all
 // six (see the flat path); it is then the minimum of its pair (x, y), so a
 // pair has at most one candidate and a road at most 64 survivors.
@@ -1886,7 +1753,7 @@ __device__ __forceinline__ unsigned long long box_key2(const int4 &s, unsigned c
 // unrolled and predicated, so a step has no branch.  DUP: the road has
 // repeated coordinates (passing counts are weighted by the raw fits each
 // canonical fit stands for).  T_ce is not made here (see box_tce).
-template <bool PLAIN, bool DUP, unsigned ME>
+template <bool PLAIN, bool DUP, unsigned ME, bool FULLW>
 __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p, unsigned &np)
 {
     const unsigned lane = lane_id();
@@ -1901,7 +1768,7 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
     bool live[ME];
 #pragma unroll
     for (unsigned w = 0; w < ME; ++w)
-        live[w] = act && w < me;
+        live[w] = FULLW || (act && w < me);   // full passes of 8-hit slots e: every lane, every w
     unsigned long long qab = NO_KEY, rw[ME];
 #pragma unroll
     for (unsigned w = 0; w < ME; ++w)
@@ -1934,8 +1801,9 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
             atomicMin(&B.T[T_BC][y * 8 + z], rz);
         }
     }
-    if (act) {
+    if (act)
         B.T[T_AB][x * 8 + y] = qab;
+    if (act) {
 #pragma unroll
         for (unsigned w = 0; w < ME; ++w)
             if (w < me) {
@@ -1943,6 +1811,7 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
                 atomicMin(&B.T[T_BE][y * 8 + w], rw[w]);
             }
     }
+    __syncwarp();
 }
 
 // T_ce[z][w]: the minimum key over every pair (x, y) at hits z, w of slots
@@ -2094,17 +1963,21 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
     const unsigned ma = sh.ma, mb = sh.mb, me = sh.me;
     const unsigned passes = (ma * mb + 31) / 32;   // 1 or 2
     unsigned np = 0;
+    // full passes and all eight hits of slot e (every 8^4 road): no per-step predicate
+    const bool fullw = (ma * mb) % 32 == 0 && me == 8 && !dup;
     for (unsigned p = 0; p < passes; ++p) {
-        if (me > 4) {
+        if (fullw)
+            box_pass<PLAIN, false, 8, true>(d, B, sh, p, np);
+        else if (me > 4) {
             if (dup)
-                box_pass<PLAIN, true, 8>(d, B, sh, p, np);
+                box_pass<PLAIN, true, 8, false>(d, B, sh, p, np);
             else
-                box_pass<PLAIN, false, 8>(d, B, sh, p, np);
+                box_pass<PLAIN, false, 8, false>(d, B, sh, p, np);
         } else {
             if (dup)
-                box_pass<PLAIN, true, 4>(d, B, sh, p, np);
+                box_pass<PLAIN, true, 4, false>(d, B, sh, p, np);
             else
-                box_pass<PLAIN, false, 4>(d, B, sh, p, np);
+                box_pass<PLAIN, false, 4, false>(d, B, sh, p, np);
         }
     }
     __syncwarp();
@@ -2739,7 +2612,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
     if (!grid_sync(d))
         return;
     stamp(d, 1);
-    if (!scan_scatter(d, smem))
+    if (!scan_decode(d, smem))
         return;
     if (!grid_sync(d))
         return;
@@ -2774,20 +2647,12 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
 // plain per-stage kernels
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(BLOCK) k_p0(Dev d)
-{
-    for (unsigned c = grab(d, Q_P0); c < d.n_chunks_w; c = grab(d, Q_P0))
-        p0_item(d, c);
-    if (last_block(&d.ctrl->done[0], gridDim.x))
-        p0_finish(d);
-}
+__global__ void __launch_bounds__(BLOCK) k_p0(Dev d) { scan_count(d); }
 
 __global__ void __launch_bounds__(BLOCK) k_p1(Dev d)
 {
-    if (ldcg(&d.ctrl->flags) & FLAG_CAPACITY)
-        return;
-    for (unsigned c = grab(d, Q_P1); c < d.n_chunks_w; c = grab(d, Q_P1))
-        p1_item(d, c);
+    extern __shared__ __align__(16) unsigned char smem[];
+    scan_decode(d, smem);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_p2(Dev d)
@@ -2962,8 +2827,8 @@ __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
         o.pad[0] = o.pad[1] = 0;
         o.curv = rec.curv;
         o.phi = rec.phi;
-        for (unsigned j = 0; j < 40; ++j)
-            o.coord[j >> 3][j & 7] = ldcg(d.coords + (size_t)g * 40 + j);
+        for (unsigned j = 0; j < 40; ++j)   // slots beyond a layer's hits hold no coordinate
+            o.coord[j >> 3][j & 7] = (j & 7u) < o.n[j >> 3] ? ldcg(d.coords + (size_t)g * 40 + j) : (uint16_t)0;
         d.road_out[g] = o;
     }
 }
@@ -2972,6 +2837,7 @@ __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
 // launchers
 // ---------------------------------------------------------------------------
 
+static size_t p1_smem() { return WARPS * sizeof(P1Warp); }
 static size_t p2_smem() { return sizeof(P2Smem); }
 static size_t p3_smem() { return WARPS * P3_WARP_BYTES; }
 
@@ -2979,7 +2845,7 @@ static_assert(sizeof(P5Smem) <= WARPS * P3_WARP_BYTES, "the output stage needs n
 
 size_t persistent_smem_bytes()
 {
-    size_t a = p2_smem(), b = p3_smem(), c = sizeof(ScanSmem), e = sizeof(P5Smem);
+    size_t a = p2_smem(), b = p3_smem(), c = p1_smem(), e = sizeof(P5Smem);
     a = a > b ? a : b;
     a = a > c ? a : c;
     return a > e ? a : e;
@@ -3003,6 +2869,8 @@ static cudaError_t set_smem_attrs()
                                   (int)persistent_smem_bytes())))
         return e;
     if ((e = cudaFuncSetAttribute(k_p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())))
         return e;
     if ((e = cudaFuncSetAttribute(k_warrior_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)p3_smem())))
@@ -3028,10 +2896,9 @@ cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches)
     cudaError_t e = set_smem_attrs();
     if (e)
         return e;
-    int g = plain_grid();
-    unsigned gw = d.n_chunks_w ? d.n_chunks_w : 1;
-    k_p0<<<gw, BLOCK, 0, s>>>(d);
-    k_p1<<<gw, BLOCK, 0, s>>>(d);
+    const int g = plain_grid();   // the same grid for P0 and P1: the word spans follow it
+    k_p0<<<g, BLOCK, 0, s>>>(d);
+    k_p1<<<g, BLOCK, p1_smem(), s>>>(d);
     k_p2<<<g, BLOCK, p2_smem(), s>>>(d);
     *n_launches += 3;
     return cudaGetLastError();

@@ -28,8 +28,6 @@ constexpr unsigned long long S_WORDS = 1ull << 17;
 constexpr unsigned S_EVENTS = 1u << 10;
 constexpr unsigned S_ROADS = 1u << 13;
 constexpr unsigned S_HASH = 1u << 15;
-constexpr unsigned S_CHUNKS_W0 = (unsigned)((S_WORDS + CHUNK_WORDS - 1) / CHUNK_WORDS);
-constexpr unsigned S_CHUNKS_W = S_CHUNKS_W0 > (unsigned)MAX_GRID ? S_CHUNKS_W0 : (unsigned)MAX_GRID;
 constexpr unsigned S_CHUNKS_R = (S_ROADS + ROAD_CHUNK - 1) / ROAD_CHUNK;
 
 constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
@@ -37,9 +35,10 @@ constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 // byte offsets of the arena's regions
 constexpr size_t OFF_CTRL = 0;
 constexpr size_t OFF_CONSTS = OFF_CTRL + up256(sizeof(Ctrl));
-constexpr size_t OFF_CHUNK = OFF_CONSTS + up256(sizeof(svt_const_set) * N_SETS);   // 4 x [S_CHUNKS_W] u32
-constexpr size_t OFF_EV = OFF_CHUNK + up256(4 * sizeof(uint32_t) * S_CHUNKS_W);     // 2 x [S_EVENTS] u32
-constexpr size_t OFF_ROADS = OFF_EV + up256(2 * sizeof(uint32_t) * S_EVENTS);
+constexpr unsigned S_SPANS = MAX_SPANS + MAX_GRID;   // per-warp word spans, then per-CTA totals
+constexpr size_t OFF_SPAN = OFF_CONSTS + up256(sizeof(svt_const_set) * N_SETS);    // 3 x [S_SPANS] u32
+constexpr size_t OFF_EV = OFF_SPAN + up256(3 * sizeof(uint32_t) * S_SPANS);         // [S_EVENTS] u32
+constexpr size_t OFF_ROADS = OFF_EV + up256(sizeof(uint32_t) * S_EVENTS);
 constexpr size_t OFF_COORDS = OFF_ROADS + up256(sizeof(RoadRec) * S_ROADS);
 constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS);
 constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
@@ -114,20 +113,16 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.consts = reinterpret_cast<const svt_const_set *>(b + OFF_CONSTS);
     d.words = d_words;
     d.n_words = n_words;
-    d.n_chunks_w = (unsigned)((n_words + CHUNK_WORDS - 1) / CHUNK_WORDS);
     d.max_events = S_EVENTS;
     d.max_roads = S_ROADS;
     d.max_chunks_r = S_CHUNKS_R;
     d.max_tracks = cap;
     d.max_combs = 0;
-    uint32_t *chunk = reinterpret_cast<uint32_t *>(b + OFF_CHUNK);
-    d.chunk_ee = chunk;
-    d.chunk_ep = chunk + S_CHUNKS_W;
-    d.chunk_ee_off = chunk + 2 * S_CHUNKS_W;
-    d.chunk_ep_off = chunk + 3 * S_CHUNKS_W;
-    uint32_t *ev = reinterpret_cast<uint32_t *>(b + OFF_EV);
-    d.ev_word_end = ev;
-    d.ev_road_end = ev + S_EVENTS;
+    uint32_t *span = reinterpret_cast<uint32_t *>(b + OFF_SPAN);
+    d.span_ee = span;
+    d.span_ep = span + S_SPANS;
+    d.span_seg = span + 2 * S_SPANS;
+    d.ev_road_end = reinterpret_cast<uint32_t *>(b + OFF_EV);
     d.roads = reinterpret_cast<RoadRec *>(b + OFF_ROADS);
     d.coords = reinterpret_cast<uint16_t *>(b + OFF_COORDS);
     d.xmask = reinterpret_cast<unsigned long long *>(b + OFF_XMASK);
