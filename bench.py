@@ -1,23 +1,36 @@
 """Benchmark of the SVT track-fitting chain on one GB300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload scaled] [--mode persistent|plain] [--no-cpu]
+                    [--workload stress] [--no-cpu] [--no-plain] [--no-serve]
+                    [--no-tune] [--no-subs]
 
-One step = one batch of the workload (default: 3000 events x 64 roads, 1-4
-hits per layer, 18.77M combinations) through the whole chain: unpack,
-combine, fit, chi-square cut, hit-warrior, ordered output.
+One step = one batch of the headline workload through the whole chain:
+unpack, combine, fit, chi-square cut, hit-warrior, ordered output.  The
+headline workload is the largest single-GPU configuration: 200 events x 128
+roads x 8 hits on each of 5 layers (838,860,800 combinations).
 
   value  track fits (combinations) per second with the words resident in
-         HBM; each step is timed with CUDA events on its stream, and a 256 MB
-         buffer is written between steps to flush L2 (the input is 11.9 MB).
+         HBM: the persistent kernel, replayed from a CUDA graph, autotuned;
+         each step timed with CUDA events on its stream, a 256 MB buffer
+         written between steps to flush L2.
   e2e    the same metric through the public C ABI from pinned host memory:
-         per step H2D of the words, svt_unpack, svt_fit_events, svt_get_tracks
-         (D2H of the status block and the surviving tracks), host wall clock.
-         The value is the throughput of two contexts taking batches in turn
-         (one batch's copies overlap the other's kernel); p50 / p99 are the
-         latency of one batch at a time, and serial_value its throughput.
-  --impl reference  the CPU oracle (test infrastructure) timed on the host
-         cores on a bounded sample of the same workload.
+         per batch H2D of the words, svt_unpack, svt_fit_events,
+         svt_get_tracks (D2H of the status block and the tracks), host wall
+         clock; two contexts take batches in turn (one batch's copies overlap
+         the other's kernel).  p50 / p99 are one batch at a time.
+  roofline  integer multiply-adds: 36 per distinct fit (the fit of one input
+         vector x, Sec. II: 18 for p = F x + q, 18 for the chi-square rows;
+         combinations that differ only in the excluded layer's hit share x),
+         against the device's multiply-add rate (SMs x 64 lanes x clock; the
+         in-tree measurement beside it).
+  scaled / uneven  the 3000 x 64 and 10,000-event uneven batches: the
+         persistent form against the plain per-stage launch (fits/s, p50,
+         p99 per batch, device and end to end).
+  serving  the serving runtime under Poisson arrivals at five offered event
+         rates, p50 / p99 from arrival to tracks in host memory.
+  cpu_baseline  the oracle (test infrastructure) on the machine's host cores:
+         its event-parallel driver on a bounded sample, per-stage times.
+  --impl reference  the oracle as it stands, timed on the host cores.
 
 Multi-GPU: the chain shards by events with no exchange, so N ranks run
 independent replicas (weak scaling); value = all ranks' fits / max time.
@@ -38,8 +51,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Integer pipe of one GB300 SM: 4 sub-partitions x 16 INT32 lanes
-INT32_LANES_PER_SM = 64
+# multiply-add lanes of one GB300 SM (the IMAD rate: half the FP32 lanes)
+IMAD_LANES_PER_SM = 64
+MACS_PER_FIT = 36   # 6 inputs x (3 track parameters + 3 chi-square components)
+HEADLINE = "stress"
 
 
 def parse_args(argv=None):
@@ -48,14 +63,14 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="svt", choices=["svt", "reference"])
-    ap.add_argument("--workload", default="scaled")
-    ap.add_argument("--mode", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparisons")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-subs", action="store_true", help="skip the scaled and uneven sub-workloads")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch settings; for profiler runs)")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help="offered-load time per rate")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per offered rate")
     return ap.parse_args(argv)
 
 
@@ -67,6 +82,16 @@ def dist_env():
 def load_cut(workload):
     with open(os.path.join(ROOT, "tests", "golden", "chi2_cuts.json")) as f:
         return int(json.load(f)[workload]["cut"])
+
+
+def distinct_fits(batch) -> int:
+    """Combinations of the four fitted layers summed over roads: the fits
+    with distinct inputs (the excluded layer's hit is not an input)."""
+    n = batch.roads["n"].astype(np.int64)
+    ex = batch.roads["excl"].astype(np.int64)
+    per = np.prod(n, axis=1)
+    ne = n[np.arange(len(n)), ex]
+    return int(np.sum(np.where(ne > 0, per // np.maximum(ne, 1), 0)))
 
 
 def workload_desc(cfg, n_fits, n_words):
@@ -146,13 +171,14 @@ def run_device_steps(ctx, B, torch, d_words, n_words, mode, steps, warmup, strea
             if i >= warmup:
                 ends[i - warmup].record(stream)
     stream.synchronize()
-    st, n = ctx.get_tracks(out=None, stream=stream)[0], None
+    st, _ = ctx.get_tracks(out=None, stream=stream)
     B.check(st, "svt_get_tracks")
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
 def run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, steps, warmup, stream):
-    """Per-step host wall time (s) through the public API, pinned host I/O."""
+    """Per-batch host wall time (s) through the public API, pinned host I/O,
+    one batch at a time."""
     n_words = h_words.numel()
     lat, d2h = [], []
     for i in range(warmup + steps):
@@ -206,59 +232,57 @@ def run_e2e_pipelined(ctxs, B, torch, h_words, d_words, h_outs, mode, steps, war
     return t1 - t0, d2h
 
 
-def cpu_baseline(batch, consts, cut, target_s=20.0):
-    """The oracle as it stands, single thread, on the first events of the
-    batch (grown until one run takes about target_s / 2 seconds; when the
-    whole batch takes less, it is run again until target_s / 2 seconds have
-    passed)."""
+def cpu_baseline(batch, consts, cut, target_s=12.0):
+    """The oracle as it stands on the host cores: its event-parallel driver
+    (one event per core at a time) on the first events of the batch, grown
+    until a run takes about target_s / 2 seconds; per-stage host times."""
     import oracle
     oracle.build()
-    n_ev = 25
+    cores = os.cpu_count() or 1
+    n_ev = min(batch.n_events, cores)
     while True:
         words = batch.event_slice(0, n_ev)
         t0 = time.perf_counter()
-        rc, out = oracle.run(words, consts, cut)
+        rc, out, times = oracle.run_mt(words, consts, cut)
         dt = time.perf_counter() - t0
+        assert rc == 0
         if dt > target_s / 2 or n_ev >= batch.n_events:
             break
-        n_ev = min(batch.n_events, int(n_ev * max(2.0, 1.1 * target_s / 2 / max(dt, 1e-3))))
-    runs = 1
-    while dt < target_s / 2:
-        t0 = time.perf_counter()
-        oracle.run(words, consts, cut)
-        dt += time.perf_counter() - t0
-        runs += 1
-    fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
-    return {"value": fits * runs / dt, "unit": "fits/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d events of the batch (%d combinations), %d run(s), %.1f s"
-                      % (n_ev, fits, runs, dt)}
+        n_ev = min(batch.n_events, max(n_ev + cores, int(n_ev * 1.1 * target_s / 2 / max(dt, 1e-3))))
+    sel = batch.roads["event"] < n_ev
+    fits = int(np.prod(batch.roads["n"][sel], axis=1).sum())
+    return {"value": fits / dt, "unit": "fits/s", "cores": times["threads"], "kind": "oracle",
+            "sample": "first %d events of the batch (%d combinations), one run, %.1f s wall"
+                      % (n_ev, fits, dt),
+            "stage_s": {"unpack": round(times["unpack_s"], 3), "combine_fit_cut": round(times["fit_s"], 3),
+                        "hit_warrior": round(times["warrior_s"], 3),
+                        "note": "unpack serial; the others summed over threads"}}
 
 
-def run_serving(B, synth, consts, cut, rates, seconds, n_slots=4, seed=0):
+def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=4, seed=0):
     """Serving loop (svt_server) under Poisson arrivals of requests whose
-    event counts are log-uniform in [1, 512) (workload-shaped events), at each
+    event counts are log-uniform in [1, 512) (scaled-shaped events), at each
     offered event rate.  Latency of a request: from its scheduled arrival to
     its tracks in host memory (admission wait, copies and kernel included)."""
-    import threading
     sizes = synth.request_sizes(seed, 64)
     pool = [synth.make_batch("scaled", seed=500 + i, n_events=int(k)).words for i, k in enumerate(sizes)]
     srv = B.Server(consts, cut, n_slots=n_slots)
     try:
-        for w in pool[:8]:                       # warm-up
-            rid = srv.submit(w)
+        for w in pool[:16]:                      # warm-up
+            srv.submit(w)
             r = srv.wait(10_000_000)
             srv.take(r["request_id"], r["n_tracks"])
         rng = np.random.default_rng(seed)
         out = []
         for rate in rates:
             req_rate = rate / float(np.mean(sizes))
-            n_req = int(min(20000, max(50, req_rate * seconds)))
+            n_req = int(n_requests)
             arrivals = np.cumsum(rng.exponential(1.0 / req_rate, n_req))
             done, sched = {}, {}
 
             def collect():
                 while len(done) < n_req:
-                    r = srv.wait(2_000_000)
+                    r = srv.wait(5_000_000)
                     if r is None:
                         break
                     srv.take(r["request_id"], r["n_tracks"])
@@ -281,30 +305,29 @@ def run_serving(B, synth, consts, cut, rates, seconds, n_slots=4, seed=0):
                 sched[srv.submit(w)] = (target, t_sub)
                 n_ev += int(sizes[i % len(pool)])
             th.join()
-            lat, bad, t_end = [], 0, t0
+            lat, wait, bad, t_end = [], [], 0, t0
             for rid, (r, t_done) in done.items():
                 target, t_sub = sched[rid]
                 lat.append((t_sub - target) + r["latency_ns"] * 1e-9)
+                wait.append(t_sub - target)
                 bad += r["status"] != B.OK
                 t_end = max(t_end, t_done)
             lat = np.array(lat) * 1e6
             out.append({"offered_events_per_s": rate, "requests": n_req, "completed": len(done),
                         "errors": bad, "sustained_events_per_s": n_ev / (t_end - t0),
-                        "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99))})
+                        "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                        "p99_submit_wait_us": float(np.percentile(np.array(wait) * 1e6, 99))})
         return {"slots": srv.config()["n_slots"], "request_events": "log-uniform in [1, 512)",
                 "arrivals": "Poisson", "rates": out}
     finally:
         srv.close()
 
 
-# DRAM bytes (read + write) of one persistent-kernel launch on the scaled
-# workload, from the ncu capture summarised in
-# profiles/k_persistent_scaled_3000x64.md, with the SHA-256 of the kernel
-# sources (kernels and their header) it was taken on: the bench line reports
-# it only while they are unchanged.
-NCU_TRAFFIC = {"workload": "scaled",
-               "kernels_sha256": "53b361275c95dffd66983c02f8b7bad8be483502d0c5ea06d4bfb405093c05b9",
-               "bytes": 13421312}
+# DRAM bytes (read + write) of one persistent-kernel launch per workload, from
+# the ncu captures in profiles/, with the SHA-256 of the kernel sources
+# (kernels and their header) they were taken on: the bench line reports a
+# figure only while the sources are unchanged.
+NCU_TRAFFIC = {}
 
 
 def measured_traffic(workload: str):
@@ -313,9 +336,9 @@ def measured_traffic(workload: str):
     for name in ("svt_kernels.cu", "svt_internal.h"):
         with open(os.path.join(ROOT, "paper_1312_0917_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
-    sha = h.hexdigest()
-    if workload == NCU_TRAFFIC["workload"] and sha == NCU_TRAFFIC["kernels_sha256"]:
-        return NCU_TRAFFIC["bytes"]
+    rec = NCU_TRAFFIC.get(workload)
+    if rec and rec["kernels_sha256"] == h.hexdigest():
+        return rec["bytes"]
     return None
 
 
@@ -336,6 +359,55 @@ def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
+def tune(ctx, B, d_words, n_words, stream):
+    assert ctx.unpack(d_words, n_words, stream) == B.OK
+    pts = ctx.autotune(reps=5, stream=stream)
+    best = min(pts, key=lambda p: p[2])
+    return {"blocks_per_sm": best[0], "small_n4": best[1],
+            "points": [[p[0], p[1], round(p[2] * 1e3, 1)] for p in pts]}
+
+
+def sub_workload(B, torch, synth, name, consts, local, args):
+    """One sub-workload: the persistent form (autotuned, graph) against the
+    plain per-stage launch, device time per batch and end to end (one batch
+    at a time, pinned host I/O)."""
+    cfg = synth.CONFIGS[name]
+    batch = synth.make_batch(cfg, seed=0)
+    cut = load_cut(name)
+    n_fits, n_words = batch.n_fits, len(batch.words)
+    ctx = B.Context(local, max_combinations=n_fits if not args.no_plain else 1 << 10)
+    ctx.load_constants(consts, cut)
+    stream = torch.cuda.Stream()
+    h_words = torch.from_numpy(batch.words.view(np.int32)).pin_memory()
+    d_words = torch.empty_like(h_words, device="cuda")
+    d_words.copy_(h_words)
+    torch.cuda.synchronize()
+    out = {"workload": workload_desc(cfg, n_fits, n_words)}
+    if not args.no_tune:
+        out["autotuned"] = tune(ctx, B, d_words, n_words, stream)
+    steps = max(10, args.steps)
+    modes = [("persistent", B.PERSISTENT)] + ([] if args.no_plain else [("plain", B.PLAIN)])
+    for label, mode in modes:
+        ctx.use_graph(mode == B.PERSISTENT)
+        t = run_device_steps(ctx, B, torch, d_words, n_words, mode, steps, args.warmup, stream)
+        stats = ctx.get_stats(stream)
+        h_out = torch.empty(max(1, stats["n_tracks"]) * 40, dtype=torch.uint8).pin_memory()
+        lat, _ = run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, steps, args.warmup, stream)
+        out[label] = {"fits_per_s": n_fits / (statistics.mean(t) / 1e3),
+                      "ms_per_batch": statistics.mean(t),
+                      "p50_us": 1e3 * float(np.percentile(t, 50)), "p99_us": 1e3 * float(np.percentile(t, 99)),
+                      "e2e_p50_us": 1e6 * float(np.percentile(lat, 50)),
+                      "e2e_p99_us": 1e6 * float(np.percentile(lat, 99)),
+                      "gpu_launches_per_batch": ctx.last_launch_count(),
+                      "tracks": stats["n_tracks"]}
+        if mode == B.PERSISTENT:
+            out[label]["phase_us"] = dict(zip(
+                ["word_scan", "road_decode", "cross_road_flags", "fit_cut_local_warrior",
+                 "cross_road_warrior", "output"], [round(x / 1e3, 1) for x in stats["phase_ns"]]))
+    ctx.close()
+    return out
+
+
 def gpu_arm(args):
     import torch
     from paper_1312_0917_gb300 import binding as B, synth, build as nvbuild
@@ -346,15 +418,16 @@ def gpu_arm(args):
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     nvbuild.build()
+    peak = B.measure_int_peak(local)
     cfg = synth.CONFIGS[args.workload]
     batch = synth.make_batch(cfg, seed=0)
     consts = synth.make_constants(0)
     cut = load_cut(args.workload)
     n_fits, n_words, n_events = batch.n_fits, len(batch.words), batch.n_events
-    mode = B.PERSISTENT if args.mode == "persistent" else B.PLAIN
+    n_fit4 = distinct_fits(batch)
+    mode = B.PERSISTENT
 
-    ctx = B.Context(local, max_combinations=(n_fits if not args.no_plain or mode == B.PLAIN
-                                             else 1 << 10))
+    ctx = B.Context(local, max_combinations=n_fits if not args.no_plain else 1 << 10)
     ctx.load_constants(consts, cut)
     stream = torch.cuda.Stream()
     h_words = torch.from_numpy(batch.words.view(np.int32)).pin_memory()
@@ -362,24 +435,15 @@ def gpu_arm(args):
     d_words.copy_(h_words)
     torch.cuda.synchronize()
 
-    # correctness of the timed configuration is checked by the tests; here the
-    # track count is recorded beside the numbers
-    tuned = None
-    if mode == B.PERSISTENT and not args.no_tune:
-        assert ctx.unpack(d_words, n_words, stream) == B.OK
-        pts = ctx.autotune(reps=5, stream=stream)
-        best = min(pts, key=lambda p: p[2])
-        tuned = {"blocks_per_sm": best[0], "small_n4": best[1],
-                 "points": [[p[0], p[1], round(p[2] * 1e3, 1)] for p in pts]}
-    if mode == B.PERSISTENT:
-        ctx.use_graph(True)
-    times = None
+    # correctness of the timed configuration is checked by the tests (every
+    # workload against the oracle); here the track count is recorded
+    tuned = None if args.no_tune else tune(ctx, B, d_words, n_words, stream)
+    ctx.use_graph(True)
     with ClockSampler(local) as clocks:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        times = run_device_steps(ctx, B, torch, d_words, n_words, mode, args.steps,
-                                 args.warmup, stream)
+        times = run_device_steps(ctx, B, torch, d_words, n_words, mode, args.steps, args.warmup, stream)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -389,30 +453,25 @@ def gpu_arm(args):
     step_ms = total_ms / len(times)
     value = whole_job_rate(n_fits, world, step_ms / 1e3)
 
-    # plain per-stage path on the same batch, for comparison
+    # the plain per-stage pipeline on the same batch, for comparison
     plain = None
-    if mode == B.PERSISTENT and not args.no_plain:
+    if not args.no_plain:
         ctx.use_graph(False)
-        pt = run_device_steps(ctx, B, torch, d_words, n_words, B.PLAIN, max(5, args.steps // 3),
-                              3, stream)
+        pt = run_device_steps(ctx, B, torch, d_words, n_words, B.PLAIN, max(5, args.steps // 3), 3, stream)
         plain = {"ms_per_step": statistics.mean(pt), "fits_per_s": n_fits / (statistics.mean(pt) / 1e3),
-                 "p50_us": 1e3 * float(np.percentile(pt, 50)),
-                 "p99_us": 1e3 * float(np.percentile(pt, 99)),
+                 "p50_us": 1e3 * float(np.percentile(pt, 50)), "p99_us": 1e3 * float(np.percentile(pt, 99)),
                  "gpu_launches_per_step": ctx.last_launch_count()}
-        if mode == B.PERSISTENT:
-            ctx.use_graph(True)
+        ctx.use_graph(True)
 
     # end to end through the public API: the latency of one batch at a time,
     # then the throughput of two contexts taking batches in turn (the value)
     h_out = torch.empty(max(1, stats["n_tracks"]) * 40, dtype=torch.uint8).pin_memory()
-    lat, d2h = run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, args.steps, args.warmup,
-                       stream)
-    ctx2 = B.Context(local, max_combinations=(n_fits if mode == B.PLAIN else 1 << 10))
+    lat, d2h = run_e2e(ctx, B, torch, h_words, d_words, h_out, mode, args.steps, args.warmup, stream)
+    ctx2 = B.Context(local, max_combinations=1 << 10)
     ctx2.load_constants(consts, cut)
     if tuned:
         ctx2.set_launch(tuned["blocks_per_sm"], tuned["small_n4"])
-    if mode == B.PERSISTENT:
-        ctx2.use_graph(True)
+    ctx2.use_graph(True)
     stream2 = torch.cuda.Stream()
     d_words2 = torch.empty_like(d_words)
     h_out2 = torch.empty_like(h_out).pin_memory()
@@ -423,12 +482,13 @@ def gpu_arm(args):
     ctx2.close()
     e2e_s = max_over_ranks(pipe_s, world)
     e2e = {"value": whole_job_rate(n_fits * args.steps, world, e2e_s), "unit": "fits/s",
-           "h2d_bytes_per_step": n_words * 4, "d2h_bytes_per_step": int(statistics.mean(pipe_d2h)) + 160,
+           "h2d_bytes_per_step": n_words * 4, "d2h_bytes_per_step": int(statistics.mean(pipe_d2h)) + 200,
            "pipelined": "two contexts taking batches in turn (copies of one overlap the other's kernel)",
            "p50_us": 1e6 * float(np.percentile(lat, 50)), "p99_us": 1e6 * float(np.percentile(lat, 99)),
            "latency": "one batch at a time: H2D, kernel, D2H",
            "serial_value": whole_job_rate(n_fits * len(lat), world, max_over_ranks(sum(lat), world)),
            "events_per_s": n_events * world * args.steps / e2e_s}
+    ctx.close()
 
     if rank != 0:
         dist.barrier()
@@ -436,38 +496,45 @@ def gpu_arm(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     clk = clocks.summary()
     mhz = clk["sm_max_mhz"] or 2070.0
-    # ALU roofline: 36 int32 multiply-adds per combination (6 inputs x 6 output
-    # rows: 3 parameters, 3 chi-square components), against the INT32 lanes
-    peak_tops = sms * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
-    achieved = 36.0 * n_fits / (step_ms / 1e3) / 1e12
+    peak_macs = sms * IMAD_LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = MACS_PER_FIT * n_fit4 / (step_ms / 1e3) / 1e12
     line = {
         "metric": "track fits/s", "value": value, "unit": "fits/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32/int64", "data": "synthetic (seeded generator, workload shape of the config)",
-        "config": {"workload": workload_desc(cfg, n_fits, n_words), "mode": args.mode,
-                   "graph": mode == B.PERSISTENT, "autotuned": tuned,
-                   "l2": "256 MB flush written between steps",
+        "config": {"workload": workload_desc(cfg, n_fits, n_words), "mode": "persistent",
+                   "graph": True, "autotuned": tuned, "l2": "256 MB flush written between steps",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "events_per_s": n_events * world / (step_ms / 1e3),
         "latency_us": {"p50": 1e3 * float(np.percentile(times, 50)),
                        "p99": 1e3 * float(np.percentile(times, 99))},
         "tracks_per_step": stats["n_tracks"], "status": stats["status"],
-        "phase_us": dict(zip(["word_scan", "event_scatter", "unpack", "fit_cut_local_warrior",
+        "phase_us": dict(zip(["word_scan", "road_decode", "cross_road_flags", "fit_cut_local_warrior",
                               "cross_road_warrior", "output"],
                              [round(x / 1e3, 1) for x in stats["phase_ns"]])),
         "e2e": e2e,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops,
-                     "traffic": measured_traffic(args.workload) if mode == B.PERSISTENT else None,
-                     "note": "36 int32 MACs per combination / INT32 lanes x SMs x max clock"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_macs, "unit": "T int32 MAC/s",
+                     "frac": achieved / peak_macs, "traffic": measured_traffic(args.workload),
+                     "peak_measured": peak["imad"] / 1e12,
+                     "units": "%d distinct fits x %d multiply-adds per launch" % (n_fit4, MACS_PER_FIT),
+                     "note": "peak = SMs x 64 multiply-add lanes x max clock; peak_measured: "
+                             "svt_measure_int_peak (mad.lo.u32 chains on every SM); "
+                             "per combination the same time is %.2f T MAC/s"
+                             % (MACS_PER_FIT * n_fits / (step_ms / 1e3) / 1e12)},
+        "int_peak_tops": {k: round(v / 1e12, 2) for k, v in peak.items()},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
     if plain:
         line["plain"] = plain
-    if not args.no_serve and rank == 0 and world == 1 and args.workload == "scaled":
-        line["serving"] = run_serving(B, synth, consts, cut, (1e4, 1e5, 1e6), args.serve_seconds)
+    if world == 1 and not args.no_subs:
+        for name in ("scaled", "uneven"):
+            if name != args.workload:
+                line[name] = sub_workload(B, torch, synth, name, consts, local, args)
+    if not args.no_serve and world == 1:
+        line["serving"] = run_serving(B, synth, consts, load_cut("serving"),
+                                      (1e4, 3e4, 1e5, 3e5, 1e6), args.serve_requests)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(batch, consts, cut)
     print(json.dumps(line), flush=True)
@@ -490,27 +557,32 @@ def reference_arm(args):
     batch = synth.make_batch(cfg, seed=0)
     consts = synth.make_constants(0)
     cut = load_cut(args.workload)
-    # bounded sample per step: ~1.5 s of oracle work
-    n_ev = max(1, min(batch.n_events, 150 if args.workload == "scaled" else 20))
+    # bounded sample per step: one event per host core (the oracle's
+    # event-parallel driver), at least enough events for about a second
+    cores = os.cpu_count() or 1
+    per_ev = batch.n_fits / batch.n_events
+    n_ev = max(1, min(batch.n_events, max(cores, int(cores * 2e6 / per_ev))))
     words = batch.event_slice(0, n_ev)
     fits = int(np.prod(batch.roads["n"][batch.roads["event"] < n_ev], axis=1).sum())
     for _ in range(args.warmup):
-        oracle.run(words, consts, cut)
-    t = []
+        oracle.run_mt(words, consts, cut)
+    t, threads = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        rc, out = oracle.run(words, consts, cut)
+        rc, out, times = oracle.run_mt(words, consts, cut)
         t.append(time.perf_counter() - t0)
+        threads = times["threads"]
         assert rc == 0
     value = fits * len(t) / sum(t)
-    sample = "first %d events of the %s batch (%d combinations) per step" % (n_ev, cfg.name, fits)
+    sample = ("first %d events of the %s batch (%d combinations) per step, the oracle's "
+              "event-parallel driver" % (n_ev, cfg.name, fits))
     line = {"impl": "reference", "metric": "track fits/s", "value": value, "unit": "fits/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/int64", "data": "synthetic",
             "config": {"workload": workload_desc(cfg, batch.n_fits, len(batch.words)),
-                       "mode": "cpu oracle, serial"},
-            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                       "mode": "cpu oracle, events over host cores"},
+            "cpu_baseline": {"value": value, "unit": "fits/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "fits/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

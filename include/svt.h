@@ -162,8 +162,11 @@ int svt_fit_events(svt_ctx *ctx, int mode, void *stream);
 /* Synchronise `stream`, then copy the batch's surviving tracks, in
  * (event, road, comb) order, to `out` (host or device memory, capacity `cap`
  * records).  *n_out = number of survivors (also when they do not fit, in
- * which case SVT_E_CAPACITY is returned and nothing is copied).  Returns the
- * batch status (a device-detected error is returned here with *n_out = 0). */
+ * which case SVT_E_CAPACITY is returned).  Returns the batch status (a
+ * device-detected error is returned here with *n_out = 0).  The status block
+ * and as many records as the context's previous batch had are copied in one
+ * go (one synchronisation when the count does not grow); when the call
+ * returns anything but SVT_OK, the contents of `out` are unspecified. */
 int svt_get_tracks(svt_ctx *ctx, svt_track *out, size_t cap, size_t *n_out,
                    void *stream);
 
@@ -219,6 +222,16 @@ int svt_debug_wait(svt_ctx *ctx, uint32_t wait_limit_us, int skip_arrival);
 int svt_last_launch_count(svt_ctx *ctx);
 
 const char *svt_strerror(int code);
+
+/* Integer throughput of `device`, the denominator of the fit's roofline (not
+ * a step of the chain): every thread of a grid that fills the device runs
+ * eight independent chains of one operation, timed with CUDA events (best of
+ * five launches after a warm-up).  *imad_per_s: 32-bit multiply-adds
+ * (mad.lo.u32) per second; *iadd_per_s: 32-bit adds; *mixed_per_s:
+ * multiply-adds and xors alternating (two pipes at once).  HOST pointers.
+ * Allocates one word of device memory for the duration of the call;
+ * synchronises the device. */
+int svt_measure_int_peak(int device, double *imad_per_s, double *iadd_per_s, double *mixed_per_s);
 
 /* ---- the chain without allocation ----------------------------------------
  * The paper has no counterpart: this entry point exists for callers that

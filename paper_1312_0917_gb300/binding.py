@@ -87,6 +87,8 @@ SIGNATURES = {
     "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
     "svt_last_launch_count": (C.c_int, [C.c_void_p]),
     "svt_strerror": (C.c_char_p, [C.c_int]),
+    "svt_measure_int_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
     "svt_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32),
                                 C.c_void_p]),
     "svt_run_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint32, C.c_int64, C.c_void_p,
@@ -294,3 +296,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_int_peak(device: int = 0) -> dict:
+    """svt_measure_int_peak: integer operations per second of the device
+    -> {"imad": ..., "iadd": ..., "mixed": ...}."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    check(lib().svt_measure_int_peak(device, C.byref(a), C.byref(b), C.byref(c)), "svt_measure_int_peak")
+    return {"imad": a.value, "iadd": b.value, "mixed": c.value}

@@ -306,17 +306,29 @@ int svt_get_tracks(svt_ctx *c, svt_track *out, size_t cap, size_t *n_out, void *
     if (!c->ran)
         return SVT_E_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaSetDevice(c->device) || read_ctrl(c, s))
+    if (cudaSetDevice(c->device))
         return SVT_E_CUDA;
+    // The status block and, speculatively, as many tracks as the previous
+    // batch had go out together, so a batch like the one before takes one
+    // synchronisation; the rest (if any) follows once the count is known.
+    const size_t spec = out ? std::min(cap, (size_t)c->last_n_out) : 0;
+    if (cudaMemcpyAsync(c->h_ctrl, c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) ||
+        (spec && cudaMemcpyAsync(out, c->d.tracks, spec * sizeof(svt_track), cudaMemcpyDefault, s)) ||
+        cudaStreamSynchronize(s))
+        return SVT_E_CUDA;
+    if (c->h_ctrl->flags & FLAG_TIMEOUT)
+        c->hash_dirty = true;   // the batch may have stopped before clearing the table
     int st = status_of(*c->h_ctrl);
     if (st)
         return st;
     size_t n = (size_t)c->h_ctrl->n_out;
     *n_out = n;
+    c->last_n_out = n;
     if (n > cap)
         return SVT_E_CAPACITY;
-    if (n && (!out || cudaMemcpyAsync(out, c->d.tracks, n * sizeof(svt_track), cudaMemcpyDefault, s) ||
-              cudaStreamSynchronize(s)))
+    if (n > spec && (!out || cudaMemcpyAsync(out + spec, c->d.tracks + spec, (n - spec) * sizeof(svt_track),
+                                             cudaMemcpyDefault, s) ||
+                     cudaStreamSynchronize(s)))
         return out ? SVT_E_CUDA : SVT_E_INVAL;
     return SVT_OK;
 }

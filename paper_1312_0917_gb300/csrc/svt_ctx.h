@@ -21,6 +21,7 @@ struct svt_ctx {
     unsigned long long wait_ns = 2000000000ull;
     int skip_arrival = 0;
     bool hash_dirty = false;         // a batch stopped before clearing its group table
+    unsigned long long last_n_out = 0;   // tracks of the last batch read (svt_get_tracks' first copy)
     // CUDA graph of one svt_fit_events enqueue
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;

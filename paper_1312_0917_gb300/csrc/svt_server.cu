@@ -1,15 +1,17 @@
 // svt_server.cu -- serving runtime: continuous batching of independent event
 // batches (requests) over a fixed set of device slots.
 //
-// Each slot owns a context (device buffers sized for one request), a CUDA
-// stream and pinned host staging for the request's words and tracks.  A
-// request is admitted when a slot is free; its host->device copy, persistent
-// kernel and control-block read are enqueued on the slot's stream at once,
-// so requests admitted while others run overlap on the device (each kernel
-// takes a share of the SMs).  A progress thread watches the slots' events,
-// fetches each result's tracks once their count is known and releases the
-// slot.  Latency runs from svt_server_submit to the moment the tracks are in
-// host memory.
+// Each slot owns a context (device buffers sized for one request), a copy
+// stream and a compute stream, pinned host staging for the request's words,
+// and a track buffer in mapped pinned host memory that the kernel's output
+// stage writes directly (over the CPU-GPU link, no device-to-host copy).  A
+// request is admitted when a slot is free; its host->device copy (copy
+// stream), then its persistent kernel and control-block read (compute
+// stream, after the copy's event) are enqueued at once, so requests admitted
+// while others run overlap on the device (each kernel takes a share of the
+// SMs).  A progress thread watches the slots' events; when a slot's control
+// block has arrived its tracks are already in host memory, and the result is
+// published.  Latency runs from svt_server_submit to that moment.
 #include "svt_ctx.h"
 
 #include <algorithm>
@@ -33,16 +35,17 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum SlotState { SLOT_FREE = 0, SLOT_RESERVED, SLOT_RUNNING, SLOT_FETCHING };
+enum SlotState { SLOT_FREE = 0, SLOT_RESERVED, SLOT_RUNNING };
 
 struct Slot {
     svt_ctx *ctx = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // compute: kernel and control-block read
+    cudaStream_t copy = nullptr;     // host->device copy of the words
     uint32_t *h_words = nullptr;     // pinned staging of the request's words
     uint32_t *d_words = nullptr;     // device copy of the words
-    svt_track *h_tracks = nullptr;   // pinned staging of the result
-    cudaEvent_t ev_ctrl = nullptr;   // control block in host memory
-    cudaEvent_t ev_done = nullptr;   // tracks in host memory
+    svt_track *h_tracks = nullptr;   // mapped pinned host memory: the kernel writes the tracks here
+    cudaEvent_t ev_h2d = nullptr;    // the words are on the device
+    cudaEvent_t ev_ctrl = nullptr;   // control block (and so the tracks) in host memory
     int state = SLOT_FREE;
     uint64_t id = 0;
     size_t n_tracks = 0;
@@ -109,39 +112,22 @@ bool progress_once(svt_server *s)
             std::lock_guard<std::mutex> lk(s->mu);
             state = sl.state;
         }
-        if (state == SLOT_RUNNING) {
-            const cudaError_t q = cudaEventQuery(sl.ev_ctrl);
-            if (q == cudaErrorNotReady)
-                continue;
-            moved = true;
-            if (q != cudaSuccess) {
-                finish(s, sl, SVT_E_CUDA, 0);
-                continue;
-            }
-            int st = ctx_status(sl.ctx);
-            const size_t n = (size_t)sl.ctx->h_ctrl->n_out;
-            if (st == SVT_OK && n > s->cfg.max_tracks)
-                st = SVT_E_CAPACITY;
-            if (st != SVT_OK || n == 0) {
-                finish(s, sl, st, 0);
-                continue;
-            }
-            sl.n_tracks = n;
-            if (cudaMemcpyAsync(sl.h_tracks, sl.ctx->d.tracks, n * sizeof(svt_track), cudaMemcpyDeviceToHost,
-                                sl.stream) != cudaSuccess ||
-                cudaEventRecord(sl.ev_done, sl.stream) != cudaSuccess) {
-                finish(s, sl, SVT_E_CUDA, 0);
-                continue;
-            }
-            std::lock_guard<std::mutex> lk(s->mu);
-            sl.state = SLOT_FETCHING;
-        } else if (state == SLOT_FETCHING) {
-            const cudaError_t q = cudaEventQuery(sl.ev_done);
-            if (q == cudaErrorNotReady)
-                continue;
-            moved = true;
-            finish(s, sl, q == cudaSuccess ? SVT_OK : SVT_E_CUDA, sl.n_tracks);
+        if (state != SLOT_RUNNING)
+            continue;
+        const cudaError_t q = cudaEventQuery(sl.ev_ctrl);
+        if (q == cudaErrorNotReady)
+            continue;
+        moved = true;
+        if (q != cudaSuccess) {
+            finish(s, sl, SVT_E_CUDA, 0);
+            continue;
         }
+        // the kernel wrote the tracks into the slot's mapped host buffer
+        int st = ctx_status(sl.ctx);
+        const size_t n = (size_t)sl.ctx->h_ctrl->n_out;
+        if (st == SVT_OK && n > s->cfg.max_tracks)
+            st = SVT_E_CAPACITY;
+        finish(s, sl, st, st == SVT_OK ? n : 0);
     }
     return moved;
 }
@@ -167,10 +153,12 @@ void destroy_slots(svt_server *s)
     for (Slot &sl : s->slots) {
         if (sl.stream)
             cudaStreamSynchronize(sl.stream);
+        if (sl.copy)
+            cudaStreamSynchronize(sl.copy);
         if (sl.ev_ctrl)
             cudaEventDestroy(sl.ev_ctrl);
-        if (sl.ev_done)
-            cudaEventDestroy(sl.ev_done);
+        if (sl.ev_h2d)
+            cudaEventDestroy(sl.ev_h2d);
         if (sl.h_words)
             cudaFreeHost(sl.h_words);
         if (sl.h_tracks)
@@ -179,6 +167,8 @@ void destroy_slots(svt_server *s)
             cudaFree(sl.d_words);
         if (sl.stream)
             cudaStreamDestroy(sl.stream);
+        if (sl.copy)
+            cudaStreamDestroy(sl.copy);
         if (sl.ctx)
             svt_destroy(sl.ctx);
         sl = Slot{};
@@ -244,15 +234,19 @@ int svt_server_create(svt_server **out, int device, const svt_server_config *con
             break;
         sl.ctx->blocks_per_sm = (int)cfg.ctas_per_sm;
         sl.ctx->max_ctas = (int)cfg.max_ctas;
+        void *d_tracks_host = nullptr;   // the device's address of the mapped track buffer
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&sl.copy, cudaStreamNonBlocking) != cudaSuccess ||
             cudaMallocHost(&sl.h_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
-            cudaMallocHost(&sl.h_tracks, sizeof(svt_track) * cfg.max_tracks) != cudaSuccess ||
+            cudaHostAlloc(&sl.h_tracks, sizeof(svt_track) * cfg.max_tracks, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&d_tracks_host, sl.h_tracks, 0) != cudaSuccess ||
             cudaMalloc(&sl.d_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev_ctrl, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev_ctrl, cudaEventDisableTiming) != cudaSuccess) {
             st = SVT_E_CUDA;
             break;
         }
+        sl.ctx->d.tracks = static_cast<svt_track *>(d_tracks_host);   // the output stage writes host memory
         cudaMemGetInfo(&after, &tot);
         if (!n_slots && i == 0) {   // size the slot count from the first slot's footprint
             const size_t per = before > after ? before - after : 1;
@@ -329,7 +323,9 @@ int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint
     int launches = 0;
     bool ok = cudaSetDevice(s->device) == cudaSuccess &&
               (!n_words || cudaMemcpyAsync(sl->d_words, sl->h_words, n_words * sizeof(uint32_t),
-                                           cudaMemcpyHostToDevice, sl->stream) == cudaSuccess) &&
+                                           cudaMemcpyHostToDevice, sl->copy) == cudaSuccess) &&
+              cudaEventRecord(sl->ev_h2d, sl->copy) == cudaSuccess &&
+              cudaStreamWaitEvent(sl->stream, sl->ev_h2d, 0) == cudaSuccess &&
               svt_unpack(sl->ctx, sl->d_words, n_words, sl->stream) == SVT_OK &&
               ctx_enqueue(sl->ctx, s->cfg.mode, sl->stream, &launches) == cudaSuccess &&
               cudaMemcpyAsync(sl->ctx->h_ctrl, sl->ctx->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,

@@ -432,3 +432,13 @@ def test_two_contexts_taking_batches_in_turn(ctx, consts, cuts):
     finally:
         ctx.use_graph(False)
         ctxs[1].close()
+
+
+def test_integer_peak_is_measured():
+    """svt_measure_int_peak: positive rates of the order of the device's
+    multiply-add lanes x clock (152 SMs x 64 lanes x ~2 GHz ~ 2e13)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    peak = B.measure_int_peak(0)
+    assert 1e12 < peak["imad"] < 1e14 and 1e12 < peak["iadd"] < 1e14
+    assert peak["mixed"] >= 0.9 * peak["imad"]
