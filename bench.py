@@ -324,10 +324,13 @@ def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=4, seed=0):
 
 
 # DRAM bytes (read + write) of one persistent-kernel launch per workload, from
-# the ncu captures in profiles/, with the SHA-256 of the kernel sources
+# the ncu captures summarised under profiles/, with the SHA-256 of the kernel sources
 # (kernels and their header) they were taken on: the bench line reports a
 # figure only while the sources are unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "stress": {"kernels_sha256": "804da36d3a865235ba716effa494abb2e315d3bb934243f68b0ff5e79c44b8ee", "bytes": 5260544},   # 5.260 MB read + 256 B written
+    "scaled": {"kernels_sha256": "804da36d3a865235ba716effa494abb2e315d3bb934243f68b0ff5e79c44b8ee", "bytes": 12684288},  # 12.621 MB read + 63.7 KB written
+}
 
 
 def measured_traffic(workload: str):
