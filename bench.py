@@ -38,6 +38,7 @@ independent replicas (weak scaling); value = all ranks' fits / max time.
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import os
 import statistics
@@ -116,7 +117,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -126,20 +127,25 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.monotonic(), [x.strip() for x in line.split(",")]))
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
+        proc, self.proc = self.proc, None
+        if proc:
+            proc.terminate()
             try:
-                self.proc.wait(timeout=5)
+                proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
-                self.proc.kill()
+                proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        taken between monotonic times t0 and t1 (all samples by default)."""
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for t, r in self.rows:
+            if (t0 is not None and t < t0) or (t1 is not None and t > t1):
+                continue
             try:
                 mhz.append(float(r[1]))
                 mx = float(r[2])
@@ -365,9 +371,10 @@ def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
 def tune(ctx, B, d_words, n_words, stream):
     assert ctx.unpack(d_words, n_words, stream) == B.OK
     pts = ctx.autotune(reps=5, stream=stream)
-    best = min(pts, key=lambda p: p[2])
-    return {"blocks_per_sm": best[0], "small_n4": best[1],
-            "points": [[p[0], p[1], round(p[2] * 1e3, 1)] for p in pts]}
+    best = ctx.get_launch()
+    keys = ("block", "blocks_per_sm", "small_n4", "run_roads")
+    return dict(best, axes=list(keys) + ["us"],
+                points=[[p[0][k] for k in keys] + [round(p[1] * 1e3, 1)] for p in pts])
 
 
 def sub_workload(B, torch, synth, name, consts, local, args):
@@ -442,14 +449,17 @@ def gpu_arm(args):
     # workload against the oracle); here the track count is recorded
     tuned = None if args.no_tune else tune(ctx, B, d_words, n_words, stream)
     ctx.use_graph(True)
-    with ClockSampler(local) as clocks:
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        times = run_device_steps(ctx, B, torch, d_words, n_words, mode, args.steps, args.warmup, stream)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+    clocks = ClockSampler(local).__enter__()
+    atexit.register(clocks.__exit__)   # the sampler stops on an early exit too
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_timed0 = time.monotonic()
+    times = run_device_steps(ctx, B, torch, d_words, n_words, mode, args.steps, args.warmup, stream)
+    torch.cuda.synchronize()
+    t_timed1 = time.monotonic()
+    if world > 1:
+        dist.barrier()
     launches = ctx.last_launch_count()
     stats = ctx.get_stats(stream)
     total_ms = max_over_ranks(sum(times), world)
@@ -473,7 +483,7 @@ def gpu_arm(args):
     ctx2 = B.Context(local, max_combinations=1 << 10)
     ctx2.load_constants(consts, cut)
     if tuned:
-        ctx2.set_launch(tuned["blocks_per_sm"], tuned["small_n4"])
+        ctx2.set_launch(**{k: tuned[k] for k in ("block", "blocks_per_sm", "small_n4", "run_roads")})
     ctx2.use_graph(True)
     stream2 = torch.cuda.Stream()
     d_words2 = torch.empty_like(d_words)
@@ -492,12 +502,16 @@ def gpu_arm(args):
            "serial_value": whole_job_rate(n_fits * len(lat), world, max_over_ranks(sum(lat), world)),
            "events_per_s": n_events * world * args.steps / e2e_s}
     ctx.close()
+    clocks.__exit__()
 
     if rank != 0:
         dist.barrier()
         return
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    clk = clocks.summary()
+    # the timed region is short (tens of ms): its samples, and those of the
+    # whole GPU section (timed steps, plain, end-to-end runs) beside them
+    clk = clocks.summary(t_timed0 - 0.02, t_timed1 + 0.02)
+    clk["gpu_section"] = clocks.summary()
     mhz = clk["sm_max_mhz"] or 2070.0
     peak_macs = sms * IMAD_LANES_PER_SM * mhz * 1e6 / 1e12
     achieved = MACS_PER_FIT * n_fit4 / (step_ms / 1e3) / 1e12

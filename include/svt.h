@@ -178,29 +178,40 @@ int svt_get_roads(svt_ctx *ctx, svt_road *out, size_t cap, size_t *n_out, void *
 /* Synchronise `stream` and return the counters and status of the last batch. */
 int svt_get_stats(svt_ctx *ctx, svt_stats *out, void *stream);
 
-/* Launch settings of the persistent kernel (autotuning).  blocks_per_sm:
- * resident CTAs per SM (0 = occupancy maximum); small_n4: roads with at most
- * this many distinct fits (combinations of the four fitted layers) are
- * processed by one warp, larger ones by a whole CTA (<= 256, 0 = 256).  Takes
- * effect from the next svt_fit_events. */
-int svt_set_launch(svt_ctx *ctx, int blocks_per_sm, int small_n4);
+/* Launch settings of the persistent kernel (autotuning); the tracks do not
+ * depend on them (every combination of values below gives the same bytes). */
+typedef struct {
+    int32_t block;           /* threads per CTA: 128, 256 or 512 (0 = 256) */
+    int32_t blocks_per_sm;   /* resident CTAs per SM (0 = the occupancy maximum of that block size) */
+    int32_t small_n4;        /* roads with more than this many distinct fits (combinations of the
+                              * four fitted layers) take a warp of their own (the box path); the
+                              * others are fitted in runs of roads (1 .. 256, 0 = 256) */
+    int32_t run_roads;       /* roads per queue claim of those runs: 4, 8 or 16 (0 = 8) */
+} svt_launch;
+
+/* Set the launch settings; they take effect from the next svt_fit_events
+ * (a captured graph is dropped).  SVT_E_INVAL on a value outside the ranges
+ * above. */
+int svt_set_launch(svt_ctx *ctx, const svt_launch *cfg);
+
+/* The launch settings in use, with the zeros resolved (*out, HOST). */
+int svt_get_launch(svt_ctx *ctx, svt_launch *out);
 
 /* One configuration measured by svt_autotune. */
 typedef struct {
-    int32_t blocks_per_sm;
-    int32_t small_n4;
+    svt_launch cfg;
     float ms;                  /* median device time of one SVT_PERSISTENT batch */
 } svt_tune_point;
 
-/* Autotuner of the persistent kernel: for every resident-CTA count per SM
- * (1 .. occupancy maximum) and every split between warp and CTA roads
- * (small_n4 = 64, 128, 256), run the bound batch once to warm up and `reps`
- * times timed with CUDA events on `stream`, then keep the configuration with
- * the smallest median time (as svt_set_launch would).  The tracks do not
- * depend on these settings.  Writes up to `cap` measured points to `points`
- * (HOST memory) and their number to *n_points.  Requires constants and a
- * bound batch; synchronises `stream`; SVT_E_CAPACITY if cap > 0 is too small
- * (the best configuration is still applied). */
+/* Autotuner of the persistent kernel over the grid of svt_launch values:
+ * block size 128 / 256 / 512, resident CTAs per SM from 1 to that size's
+ * occupancy maximum, small_n4 = 64 / 128 / 256 and run_roads = 4 / 8 / 16.
+ * Each configuration runs the bound batch once to warm up and `reps` times
+ * timed with CUDA events on `stream`; the one with the smallest median time
+ * is kept (as svt_set_launch would).  Writes up to `cap` measured points to
+ * `points` (HOST memory) and their number to *n_points.  Requires constants
+ * and a bound batch; synchronises `stream`; SVT_E_CAPACITY if cap > 0 is too
+ * small (the best configuration is still applied). */
 int svt_autotune(svt_ctx *ctx, int reps, svt_tune_point *points, uint32_t cap, uint32_t *n_points,
                  void *stream);
 

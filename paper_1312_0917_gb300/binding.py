@@ -53,8 +53,16 @@ class Stats(C.Structure):
         return d
 
 
+class Launch(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("small_n4", C.c_int32),
+                ("run_roads", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class TunePoint(C.Structure):
-    _fields_ = [("blocks_per_sm", C.c_int32), ("small_n4", C.c_int32), ("ms", C.c_float)]
+    _fields_ = [("cfg", Launch), ("ms", C.c_float)]
 
 
 class ServerConfig(C.Structure):
@@ -82,7 +90,8 @@ SIGNATURES = {
     "svt_get_roads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
                                 C.c_void_p]),
     "svt_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_void_p]),
-    "svt_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "svt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(Launch)]),
+    "svt_get_launch": (C.c_int, [C.c_void_p, C.POINTER(Launch)]),
     "svt_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
     "svt_last_launch_count": (C.c_int, [C.c_void_p]),
@@ -225,16 +234,22 @@ class Context:
         check(lib().svt_get_stats(self._h, C.byref(s), stream_ptr(stream)), "svt_get_stats")
         return s.as_dict()
 
-    def set_launch(self, blocks_per_sm: int = 0, small_n4: int = 0):
-        check(lib().svt_set_launch(self._h, blocks_per_sm, small_n4), "svt_set_launch")
+    def set_launch(self, block: int = 0, blocks_per_sm: int = 0, small_n4: int = 0, run_roads: int = 0):
+        cfg = Launch(block, blocks_per_sm, small_n4, run_roads)
+        check(lib().svt_set_launch(self._h, C.byref(cfg)), "svt_set_launch")
+
+    def get_launch(self) -> dict:
+        cfg = Launch()
+        check(lib().svt_get_launch(self._h, C.byref(cfg)), "svt_get_launch")
+        return cfg.as_dict()
 
     def autotune(self, reps: int = 5, stream=None) -> list:
         """Measure every launch configuration on the bound batch and keep the
-        fastest; returns [(blocks_per_sm, small_n4, ms), ...]."""
-        pts = (TunePoint * 64)()
+        fastest; returns [({block, blocks_per_sm, small_n4, run_roads}, ms), ...]."""
+        pts = (TunePoint * 512)()
         n = C.c_uint32()
-        check(lib().svt_autotune(self._h, reps, pts, 64, C.byref(n), stream_ptr(stream)), "svt_autotune")
-        return [(p.blocks_per_sm, p.small_n4, p.ms) for p in pts[:n.value]]
+        check(lib().svt_autotune(self._h, reps, pts, 512, C.byref(n), stream_ptr(stream)), "svt_autotune")
+        return [(p.cfg.as_dict(), p.ms) for p in pts[:n.value]]
 
     def use_graph(self, enable: bool = True):
         check(lib().svt_use_graph(self._h, int(enable)), "svt_use_graph")

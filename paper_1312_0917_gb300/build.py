@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsvt.so")
-SOURCES = ["svt_kernels.cu", "svt_api.cu", "svt_server.cu", "svt_static.cu", "svt_peak.cu"]
+SOURCES = ["svt_kernels.cu", "svt_kernels_b128.cu", "svt_kernels_b512.cu", "svt_api.cu", "svt_server.cu", "svt_static.cu", "svt_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -101,7 +101,7 @@ cudaError_t enqueue(svt_ctx *c, int mode, cudaStream_t s, int *launches)
         return launch_fit_plain(d, s, launches);
     }
     c->skip_arrival = 0;   // the test hook holds for one persistent launch
-    return launch_persistent(d, s, c->blocks_per_sm, c->max_ctas, launches);
+    return launch_persistent(c->block, d, s, c->blocks_per_sm, c->max_ctas, launches);
 }
 
 }  // namespace
@@ -165,10 +165,11 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
     d.max_combs = L.max_combinations;
     d.hash_mask = L.hash_slots - 1;
     d.small_n4 = N4_SMALL_MAX;
+    d.run_roads = WARP_ROADS;
     bool ok =
         !dalloc(c, &d.ctrl, 1) && !dalloc(c, const_cast<svt_const_set **>(&d.consts), N_SETS) &&
         !dalloc(c, &d.span_ee, MAX_SPANS + MAX_GRID) && !dalloc(c, &d.span_ep, MAX_SPANS + MAX_GRID) &&
-        !dalloc(c, &d.span_seg, MAX_SPANS + MAX_GRID) && !dalloc(c, &d.ev_road_end, L.max_events) &&
+        !dalloc(c, &d.span_seg, MAX_SPANS + MAX_GRID) && !dalloc(c, &d.ev_road_end, L.max_events) && !dalloc(c, &d.ev_big, L.max_events) &&
         !dalloc(c, &d.roads, L.max_roads) && !dalloc(c, &d.coords, (size_t)L.max_roads * 40) &&
         !dalloc(c, &d.xmask, L.max_roads) && !dalloc(c, &d.big_list, L.max_roads) &&
         !dalloc(c, &d.cand_bits, L.max_roads / 32 + 1) && !dalloc(c, &d.fitc, N_SETS * SET_INT4) &&
@@ -391,13 +392,45 @@ int svt_get_stats(svt_ctx *c, svt_stats *out, void *stream)
     return SVT_OK;
 }
 
-int svt_set_launch(svt_ctx *c, int blocks_per_sm, int small_n4)
+static bool launch_ok(const svt_launch &L)
 {
-    if (!c || blocks_per_sm < 0 || small_n4 < 0 || small_n4 > N4_SMALL_MAX)
+    return (L.block == 0 || persistent_block_ok(L.block)) && L.blocks_per_sm >= 0 && L.small_n4 >= 0 &&
+           L.small_n4 <= N4_SMALL_MAX && (L.run_roads == 0 || L.run_roads == 4 || L.run_roads == 8 ||
+                                          L.run_roads == RUN_ROADS_MAX);
+}
+
+static void apply_launch(svt_ctx *c, const svt_launch &L)
+{
+    c->block = L.block ? L.block : 256;
+    c->blocks_per_sm = L.blocks_per_sm;
+    c->d.small_n4 = L.small_n4 ? L.small_n4 : N4_SMALL_MAX;
+    c->d.run_roads = L.run_roads ? L.run_roads : WARP_ROADS;
+}
+
+static svt_launch current_launch(const svt_ctx *c)
+{
+    return svt_launch{c->block, c->blocks_per_sm, c->d.small_n4, c->d.run_roads};
+}
+
+int svt_set_launch(svt_ctx *c, const svt_launch *cfg)
+{
+    if (!c || !cfg || !launch_ok(*cfg))
         return SVT_E_INVAL;
-    c->blocks_per_sm = blocks_per_sm;
-    c->d.small_n4 = small_n4 ? small_n4 : N4_SMALL_MAX;
+    apply_launch(c, *cfg);
     drop_graph(c);
+    return SVT_OK;
+}
+
+int svt_get_launch(svt_ctx *c, svt_launch *out)
+{
+    if (!c || !out)
+        return SVT_E_INVAL;
+    *out = current_launch(c);
+    if (out->blocks_per_sm == 0) {
+        if (cudaSetDevice(c->device))
+            return SVT_E_CUDA;
+        out->blocks_per_sm = persistent_max_blocks_per_sm(c->block, c->device);
+    }
     return SVT_OK;
 }
 
@@ -413,52 +446,62 @@ int svt_autotune(svt_ctx *c, int reps, svt_tune_point *points, uint32_t cap, uin
     if (cudaSetDevice(c->device))
         return SVT_E_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const int maxb = persistent_max_blocks_per_sm(c->device);
-    if (maxb <= 0)
-        return SVT_E_CUDA;
     static const int kSmall[] = {64, 128, N4_SMALL_MAX};
+    static const int kRun[] = {4, WARP_ROADS, RUN_ROADS_MAX};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) || cudaEventCreate(&e1))
         return SVT_E_CUDA;
-    const int old_bps = c->blocks_per_sm, old_small = c->d.small_n4;
-    int best_bps = old_bps, best_small = old_small, st = SVT_OK;
+    const svt_launch old = current_launch(c);
+    svt_launch best_cfg = old;
+    int st = SVT_OK;
     float best = 0.f;
     uint32_t n = 0;
     std::vector<float> t(reps);
-    for (int bps = 1; bps <= maxb && st == SVT_OK; ++bps)
-        for (int small : kSmall) {
-            c->blocks_per_sm = bps;
-            c->d.small_n4 = small;
-            int nl = 0;
-            if (enqueue(c, SVT_PERSISTENT, s, &nl) || read_ctrl(c, s)) {   // warm-up
-                st = SVT_E_CUDA;
-                break;
-            }
-            if ((st = status_of(*c->h_ctrl)) != SVT_OK)
-                break;
-            for (int r = 0; r < reps && st == SVT_OK; ++r) {
-                if (cudaEventRecord(e0, s) || enqueue(c, SVT_PERSISTENT, s, &nl) || cudaEventRecord(e1, s) ||
-                    cudaEventSynchronize(e1) || cudaEventElapsedTime(&t[r], e0, e1))
-                    st = SVT_E_CUDA;
-            }
-            if (st != SVT_OK)
-                break;
-            std::sort(t.begin(), t.end());
-            const float med = t[reps / 2];
-            if (n < cap)
-                points[n] = svt_tune_point{bps, small, med};
-            ++n;
-            if (best == 0.f || med < best) {
-                best = med;
-                best_bps = bps;
-                best_small = small;
-            }
+    for (int block : PERSISTENT_BLOCKS) {
+        const int maxb = persistent_max_blocks_per_sm(block, c->device);
+        if (maxb <= 0) {
+            st = SVT_E_CUDA;
+            break;
         }
+        for (int bps = 1; bps <= maxb && st == SVT_OK; ++bps)
+            for (int small : kSmall)
+                for (int run : kRun) {
+                    if (st != SVT_OK)
+                        break;
+                    const svt_launch L{block, bps, small, run};
+                    apply_launch(c, L);
+                    int nl = 0;
+                    if (enqueue(c, SVT_PERSISTENT, s, &nl) || read_ctrl(c, s)) {   // warm-up
+                        st = SVT_E_CUDA;
+                        break;
+                    }
+                    if ((st = status_of(*c->h_ctrl)) != SVT_OK)
+                        break;
+                    for (int r = 0; r < reps && st == SVT_OK; ++r) {
+                        if (cudaEventRecord(e0, s) || enqueue(c, SVT_PERSISTENT, s, &nl) ||
+                            cudaEventRecord(e1, s) || cudaEventSynchronize(e1) ||
+                            cudaEventElapsedTime(&t[r], e0, e1))
+                            st = SVT_E_CUDA;
+                    }
+                    if (st != SVT_OK)
+                        break;
+                    std::sort(t.begin(), t.end());
+                    const float med = t[reps / 2];
+                    if (n < cap)
+                        points[n] = svt_tune_point{L, med};
+                    ++n;
+                    if (best == 0.f || med < best) {
+                        best = med;
+                        best_cfg = L;
+                    }
+                }
+        if (st != SVT_OK)
+            break;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
-    c->blocks_per_sm = st == SVT_OK ? best_bps : old_bps;
-    c->d.small_n4 = st == SVT_OK ? best_small : old_small;
+    apply_launch(c, st == SVT_OK ? best_cfg : old);
     drop_graph(c);
     if (n_points)
         *n_points = n;

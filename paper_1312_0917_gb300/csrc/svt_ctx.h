@@ -15,6 +15,7 @@ struct svt_ctx {
     bool bound = false;              // a batch is bound by svt_unpack
     bool roads_valid = false;        // the road table holds the bound batch
     bool ran = false;                // svt_fit_events ran on the bound batch
+    int block = 256;                 // threads per CTA of the persistent kernel (128, 256, 512)
     int blocks_per_sm = 0;
     int max_ctas = 0;                // persistent grid cap (0 = all SMs x blocks_per_sm)
     int last_launches = 0;

@@ -8,17 +8,18 @@
 
 namespace svt {
 
-constexpr int BLOCK = 256;                 // threads per CTA, every kernel
-constexpr int WARPS = BLOCK / 32;
 constexpr int MAX_GRID = 4096;             // CTAs of any kernel over the word spans at most
-constexpr int MAX_SPANS = MAX_GRID * WARPS; // word spans (one per warp of the grid)
+constexpr int MAX_SPANS = MAX_GRID * 8;    // word spans (one per warp of the grid): a grid of
+                                           // b threads per CTA has at most MAX_SPANS * 32 / b CTAs
 constexpr int MAX_ROADS_EV = 256;          // format limit: roads per event
 constexpr int MAX_HITS = 8;                // format limit: hits per layer per road
 constexpr int N_LAYERS = 5;
 constexpr int N_SETS = 360;                // 12 wedges x 6 barrels x 5 excluded layers
 constexpr int SURV_SLOTS = 64;             // survivors per road are <= 64 (see box_road)
 constexpr int ROAD_CHUNK = 256;            // roads per output work item
-constexpr int WARP_ROADS = 8;              // roads per work item of a fitting warp
+constexpr int WARP_ROADS = 8;              // roads a fitting warp takes into its tables at once
+constexpr int P2W_ROADS = 64;              // events of at most this many roads: one warp each in P2
+constexpr int RUN_ROADS_MAX = 16;          // roads per queue claim of a fitting warp (run_roads)
 constexpr int N4_SMALL_MAX = 256;          // largest road a single warp takes
 constexpr int QTAB_SMALL = 160;            // the same sum for any road with N4 <= 256
 constexpr unsigned long long NO_KEY = ~0ull;
@@ -63,7 +64,7 @@ struct Ctrl {
     unsigned int has_tail;        // words after the last EE
     unsigned int n_roads;         // roads of complete events
     unsigned int n_big;           // roads fitted by a whole CTA (list length)
-    unsigned int pad_c;
+    unsigned int n_big_ev;        // events of more than P2W_ROADS roads (list length)
     unsigned int hash_used;       // claimed slots of the group table
     unsigned int q[12];           // work-queue heads
     unsigned int bar;             // grid barrier arrivals
@@ -104,6 +105,7 @@ struct Dev {
                                               // then per CTA (its spans together): EE and EP words,
                                               // EP words since its last EE (SEG_EE set when it holds one)
     uint32_t *ev_road_end;                    // [max_events] roads up to the end of each event
+    uint32_t *ev_big;                         // [max_events] events of more than P2W_ROADS roads
     RoadRec *roads;                                               // [max_roads]
     uint16_t *coords;                                             // [max_roads][5][8]
     unsigned long long *xmask;                                    // [max_roads]
@@ -127,16 +129,49 @@ struct Dev {
     svt_road *road_out;                                           // [max_roads] (svt_get_roads)
     long long cut;
     int small_n4;
+    int run_roads;         // roads per queue claim of the fit stage's runs: 4, 8 or 16
     int skip_arrival;
     unsigned long long wait_ns;
 };
 
-// launchers (svt_kernels.cu)
+// Launchers.  svt_kernels.cu is compiled once per block size of the
+// persistent kernel, each build in its own namespace: b256 (svt_kernels.cu,
+// also the plain pipeline), b128 (svt_kernels_b128.cu), b512
+// (svt_kernels_b512.cu).
+#define SVT_PERSISTENT_DECLS                                                                          \
+    cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas,      \
+                                  int *n_launches);                                                   \
+    int persistent_max_blocks_per_sm(int device);                                                     \
+    size_t persistent_smem_bytes();
+namespace b128 { SVT_PERSISTENT_DECLS }
+namespace b512 { SVT_PERSISTENT_DECLS }
+namespace b256 {
+SVT_PERSISTENT_DECLS
 cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches);
 cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches);
-cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas, int *n_launches);
 cudaError_t launch_export_roads(const Dev &d, cudaStream_t s);
-int persistent_max_blocks_per_sm(int device);
-size_t persistent_smem_bytes();
+}
+#undef SVT_PERSISTENT_DECLS
+using b256::launch_unpack_plain;
+using b256::launch_fit_plain;
+using b256::launch_export_roads;
+
+constexpr int PERSISTENT_BLOCKS[3] = {128, 256, 512};   // the block sizes built
+inline bool persistent_block_ok(int block) { return block == 128 || block == 256 || block == 512; }
+
+// the persistent kernel at `block` threads per CTA (128, 256 or 512)
+inline cudaError_t launch_persistent(int block, const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas,
+                                     int *n_launches)
+{
+    return block == 128   ? b128::launch_persistent(d, s, blocks_per_sm, max_ctas, n_launches)
+           : block == 512 ? b512::launch_persistent(d, s, blocks_per_sm, max_ctas, n_launches)
+                          : b256::launch_persistent(d, s, blocks_per_sm, max_ctas, n_launches);
+}
+inline int persistent_max_blocks_per_sm(int block, int device)
+{
+    return block == 128   ? b128::persistent_max_blocks_per_sm(device)
+           : block == 512 ? b512::persistent_max_blocks_per_sm(device)
+                          : b256::persistent_max_blocks_per_sm(device);
+}
 
 }  // namespace svt

@@ -27,11 +27,33 @@
 // is floor division by 4096, and floor(s / 4096) + k == floor((s + 4096 k) /
 // 4096).  chi2 < 2^38, so the track key (chi2 << 23 | road << 15 | comb)
 // is a 61-bit integer ordered like (chi2, road, comb).
+//
+// The block size of every kernel is SVT_BLOCK (256 unless the including
+// file sets it); each block size builds in a namespace of its own, and only
+// the 256-thread build holds the plain pipeline.
 #include <cstddef>
 
 #include "svt_internal.h"
 
+#ifndef SVT_BLOCK
+#define SVT_BLOCK 256
+#endif
+#if SVT_BLOCK == 128
+#define SVT_KNS b128
+#elif SVT_BLOCK == 256
+#define SVT_KNS b256
+#elif SVT_BLOCK == 512
+#define SVT_KNS b512
+#else
+#error "SVT_BLOCK must be 128, 256 or 512"
+#endif
+
 namespace svt {
+namespace SVT_KNS {
+
+constexpr int BLOCK = SVT_BLOCK;           // threads per CTA, every kernel of this build
+constexpr int WARPS = BLOCK / 32;
+constexpr int GRID_MAX = MAX_SPANS / WARPS < MAX_GRID ? MAX_SPANS / WARPS : MAX_GRID;
 
 #define FULL_MASK 0xffffffffu
 
@@ -346,7 +368,7 @@ __device__ __forceinline__ void stamp(const Dev &d, unsigned k)
 }
 
 // work-queue indices (Ctrl::q)
-enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT };
+enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT, Q_P2W };
 
 // ---------------------------------------------------------------------------
 // P0 / P1: the word stream, one warp per span.  The stream is cut into
@@ -569,6 +591,8 @@ __device__ __forceinline__ unsigned long long decode_batch(const Dev &d, P1Warp 
             d.roads[g] = r;
             if (ee && ev < d.max_events) {   // the event's last road
                 d.ev_road_end[ev] = g + 1;
+                if (rie + 1 > (unsigned)P2W_ROADS)   // P2 takes this event with a whole CTA
+                    d.ev_big[atomicAdd(&d.ctrl->n_big_ev, 1u)] = ev;
                 if (ev + 1 == n_events)
                     d.ctrl->n_roads = g + 1;
             }
@@ -735,6 +759,10 @@ __device__ bool scan_decode(const Dev &d, unsigned char *smem)
 // which marks the shared hits of both roads.  A road with a marked hit is a
 // cross-road candidate; its marked hits are the ones it publishes and looks
 // up.  The road records get the candidate bit and their fit path.
+//
+// Events of at most P2W_ROADS roads take one warp each instead (p2_warp),
+// with the same bitmaps, 32-bit signatures, and a lane per road that tests
+// its road against the others and marks its own hits.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned P2_PAIRS = 1024;   // road pairs queued for the exact test (more: tested in place)
@@ -957,7 +985,182 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned r0, unsigned nr, uns
     __syncthreads();   // the shared arrays are refilled for the next event
 }
 
-// P2 over the event queue; one combination-count atomic per CTA
+// One warp's state for an event of at most P2W_ROADS roads; the roads'
+// coordinate rows stay in global memory (L2), read a road at a time.
+struct P2Warp {
+    uint32_t seen[N_LAYERS][128];           // coordinate bitmaps of the event (12-bit coordinates)
+    uint32_t multi[N_LAYERS][128];          // coordinates present in two or more roads
+    uint32_t sig[P2W_ROADS][N_LAYERS];      // 32-bit signatures of a road's shared coordinates
+    uint32_t pk[P2W_ROADS];
+};
+constexpr size_t P2W_BYTES = (sizeof(P2Warp) + 15) / 16 * 16;
+
+// signature bit of a coordinate in a 32-bit signature
+__device__ __forceinline__ unsigned sig_bit32(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
+
+// coordinate x of a layer's row (eight 16-bit coordinates in a uint4); x is
+// a constant in the unrolled loops below
+__device__ __forceinline__ unsigned row_coord(const uint4 &q, unsigned x)
+{
+    const unsigned w = x < 2 ? q.x : x < 4 ? q.y : x < 6 ? q.z : q.w;
+    return (w >> (16 * (x & 1u))) & 0xFFFFu;
+}
+
+// Hits of road g that road h holds too (bit 8 l + x), when they hold common
+// coordinates on three layers or more; 0 otherwise.  pg, ph: their records'
+// pk words.
+__device__ unsigned long long pair_marks(const Dev &d, unsigned g, unsigned h, uint32_t pg, uint32_t ph)
+{
+    const uint4 *rg = reinterpret_cast<const uint4 *>(d.coords + (size_t)g * 40);
+    const uint4 *rh = reinterpret_cast<const uint4 *>(d.coords + (size_t)h * 40);
+    unsigned long long m = 0;
+    unsigned layers = 0;
+    for (unsigned l = 0; l < N_LAYERS; ++l) {
+        const unsigned ng = (pg >> (4 * l)) & 15u, nh = (ph >> (4 * l)) & 15u;   // <= MAX_HITS
+        const uint4 a = ldcg(rg + l), b = ldcg(rh + l);
+        unsigned br = 0;
+#pragma unroll
+        for (unsigned x = 0; x < MAX_HITS; ++x) {
+            const unsigned v = row_coord(a, x);
+            bool hit = false;
+#pragma unroll
+            for (unsigned y = 0; y < MAX_HITS; ++y)
+                hit = hit || (y < nh && row_coord(b, y) == v);
+            br |= (x < ng && hit) ? 1u << x : 0u;
+        }
+        layers += br != 0;
+        m |= (unsigned long long)br << (8 * l);
+    }
+    return layers >= 3 ? m : 0ull;
+}
+
+// P2 of the event of roads r0 .. r0 + nr - 1 (nr <= P2W_ROADS) by one warp
+// with state `w`; lane i owns roads i and i + 32.  The same steps as
+// p2_event: coordinates present in two roads (bitmaps), signatures of those
+// per road and layer, pairs whose signatures meet on >= 3 layers tested
+// exactly.  A lane tests its road against every other road and marks only
+// its own road's hits, so each pair is tested from both sides.
+__device__ void p2_warp(const Dev &d, unsigned r0, unsigned nr, P2Warp &w, unsigned long long &n_comb)
+{
+    const unsigned lane = lane_id();
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(&w.seen[0][0]);   // seen and multi
+        for (unsigned i = lane; i < 2 * N_LAYERS * 128 / 4; i += 32)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    bool rep[2] = {false, false};
+#pragma unroll
+    for (unsigned h = 0; h < 2; ++h) {
+        const unsigned k = lane + 32 * h;
+        if (k < nr)
+            w.pk[k] = ldcg(&d.roads[r0 + k].pk);
+    }
+    __syncwarp();
+    // each distinct coordinate of a road's layer marks the bitmap once; a
+    // second road with it sets the multi bit
+#pragma unroll
+    for (unsigned h = 0; h < 2; ++h) {
+        const unsigned k = lane + 32 * h;
+        if (k >= nr)
+            continue;
+        const uint4 *row = reinterpret_cast<const uint4 *>(d.coords + (size_t)(r0 + k) * 40);
+        const uint32_t pk = w.pk[k];
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned n = (pk >> (4 * l)) & 15u;
+            const uint4 q = ldcg(row + l);
+#pragma unroll
+            for (unsigned x = 0; x < MAX_HITS; ++x) {
+                const unsigned v = row_coord(q, x);
+                bool first = x < n;
+#pragma unroll
+                for (unsigned y = 0; y < x; ++y)
+                    first = first && row_coord(q, y) != v;
+                if (first) {
+                    const unsigned bit = 1u << (v & 31u);
+                    if (atomicOr(&w.seen[l][v >> 5], bit) & bit)
+                        atomicOr(&w.multi[l][v >> 5], bit);
+                }
+                rep[h] = rep[h] || (x < n && !first);
+            }
+        }
+    }
+    __syncwarp();
+    // signatures of the shared coordinates
+    unsigned elig = 0;   // bit h: the lane's road h has shared coordinates on >= 3 layers
+#pragma unroll
+    for (unsigned h = 0; h < 2; ++h) {
+        const unsigned k = lane + 32 * h;
+        if (k >= nr)
+            continue;
+        const uint4 *row = reinterpret_cast<const uint4 *>(d.coords + (size_t)(r0 + k) * 40);
+        const uint32_t pk = w.pk[k];
+        unsigned layers = 0;
+        for (unsigned l = 0; l < N_LAYERS; ++l) {
+            const unsigned n = (pk >> (4 * l)) & 15u;
+            const uint4 q = ldcg(row + l);
+            uint32_t sl = 0;
+#pragma unroll
+            for (unsigned x = 0; x < MAX_HITS; ++x) {
+                const unsigned v = row_coord(q, x);
+                if (x < n && ((w.multi[l][v >> 5] >> (v & 31u)) & 1u))
+                    sl |= 1u << sig_bit32(v);
+            }
+            w.sig[k][l] = sl;
+            layers += sl != 0u;
+        }
+        elig |= layers >= 3 ? 1u << h : 0u;
+    }
+    __syncwarp();
+    // every other road t against the lane's eligible roads (their signatures
+    // meet on >= 3 layers first)
+    unsigned long long xm[2] = {0ull, 0ull};
+    if (__any_sync(FULL_MASK, elig != 0u)) {
+        for (unsigned t = 0; t < nr; ++t) {
+#pragma unroll
+            for (unsigned h = 0; h < 2; ++h) {
+                const unsigned k = lane + 32 * h;
+                if (!((elig >> h) & 1u) || k == t)
+                    continue;
+                unsigned c = 0;
+#pragma unroll
+                for (unsigned l = 0; l < N_LAYERS; ++l)
+                    c += (w.sig[k][l] & w.sig[t][l]) != 0u;
+                if (c >= 3)
+                    xm[h] |= pair_marks(d, r0 + k, r0 + t, w.pk[k], w.pk[t]);
+            }
+        }
+    }
+#pragma unroll
+    for (unsigned h = 0; h < 2; ++h) {
+        const unsigned k = lane + 32 * h;
+        if (k >= nr)
+            continue;
+        const unsigned g = r0 + k;
+        RoadRec r = ldcg(d.roads + g);
+        const bool cand = xm[h] != 0ull;
+        unsigned N, N4;
+        road_sizes(r.pk, N, N4);
+        const bool big = N > 0 && (N4 > (unsigned)d.small_n4 || (cand && rep[h]));
+        r.pk |= cand ? (1u << 23) : 0u;
+        r.cta = (big ? 1 : 0) | (rep[h] ? 2 : 0);
+        d.roads[g] = r;
+        d.xmask[g] = xm[h];
+        d.surv_cnt[g] = 0;
+        if (big) {
+            unsigned i = atomicAdd(&d.ctrl->n_big, 1u);
+            if (i < d.max_roads)
+                d.big_list[i] = g;
+        }
+        if (N > 0 && cand)
+            atomicOr(&d.cand_bits[g >> 5], 1u << (g & 31u));
+        n_comb += N;
+    }
+    __syncwarp();   // the state is refilled for the next event
+}
+
+// P2 over the events: first the events of more than P2W_ROADS roads (listed
+// in P1), a CTA each from a queue; then every warp takes the other events
+// from a second queue, one at a time.  One combination-count atomic per CTA.
 __device__ void p2_phase(const Dev &d, unsigned char *smem)
 {
     if (ldcg(&d.ctrl->err_inv) != 0ull)
@@ -969,11 +1172,29 @@ __device__ void p2_phase(const Dev &d, unsigned char *smem)
         d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
     // the CTA's first event is its own index, the queue hands out the rest
-    for (unsigned e = blockIdx.x; e < n_events; e = grab_after_first(d, Q_P2)) {
+    const unsigned n_big_ev = min(ldcg(&d.ctrl->n_big_ev), n_events);
+    for (unsigned i = blockIdx.x; i < n_big_ev; i = grab_after_first(d, Q_P2)) {
+        const unsigned e = min(ldcg(d.ev_big + i), n_events - 1);
         const unsigned r0 = e == 0 ? 0u : min(ldcg(d.ev_road_end + e - 1), d.max_roads);
         const unsigned r1 = min(ldcg(d.ev_road_end + e), d.max_roads);
         // an event of more than MAX_ROADS_EV roads is a fault (reported in P1)
         p2_event(d, e, r0, min(r1 - min(r0, r1), (unsigned)MAX_ROADS_EV), smem, n_comb);
+    }
+    __syncthreads();   // the shared memory becomes the warps' regions
+    {
+        P2Warp &w = *reinterpret_cast<P2Warp *>(smem + warp_id() * P2W_BYTES);
+        const unsigned n_warps = gridDim.x * WARPS;
+        for (unsigned e = blockIdx.x * WARPS + warp_id(); e < n_events;) {
+            const unsigned r0 = e == 0 ? 0u : min(ldcg(d.ev_road_end + e - 1), d.max_roads);
+            const unsigned r1 = min(ldcg(d.ev_road_end + e), d.max_roads);
+            const unsigned nr = r1 - min(r0, r1);
+            if (nr <= (unsigned)P2W_ROADS)   // the others were listed
+                p2_warp(d, r0, nr, w, n_comb);
+            unsigned ne = 0;
+            if (lane_id() == 0)
+                ne = n_warps + atomicAdd(&d.ctrl->q[Q_P2W], 1u);
+            e = __shfl_sync(FULL_MASK, ne, 0);
+        }
     }
     n_comb = block_sum(n_comb);
     if (threadIdx.x == 0 && n_comb)
@@ -2172,9 +2393,10 @@ static_assert(sizeof(P3Box) <= P3_WARP_BYTES, "the box path uses a warp's region
 
 // The roads listed in P2 (more than small_n4 distinct fits, or a cross-road
 // candidate with a repeated coordinate) are fitted first, one warp each
-// (box_road); then every warp takes runs of WARP_ROADS consecutive roads and
-// fits the others itself (fit_run).  Each warp works in its own region of
-// shared memory, so no stage of P3 waits for the whole CTA.
+// (box_road); then every warp claims runs of d.run_roads consecutive roads
+// (4, 8 or 16) and fits the others itself, WARP_ROADS at a time (fit_run).
+// Each warp works in its own region of shared memory, so no stage of P3
+// waits for the whole CTA.
 template <bool PLAIN>
 __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall)
 {
@@ -2193,10 +2415,12 @@ __device__ void p3_phase(const Dev &d, unsigned char *smem, int qbig, int qsmall
     }
     __syncwarp();
     {
-        const unsigned n_runs = (n_roads + WARP_ROADS - 1) / WARP_ROADS;
+        const unsigned rr = (unsigned)d.run_roads;
+        const unsigned n_runs = (n_roads + rr - 1) / rr;
         for (unsigned c = blockIdx.x * WARPS + warp_id(); c < n_runs;) {
-            const unsigned g0 = c * WARP_ROADS;
-            fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, n_roads - g0), npass);
+            const unsigned ge = min(c * rr + rr, n_roads);
+            for (unsigned g0 = c * rr; g0 < ge; g0 += WARP_ROADS)
+                fit_run<PLAIN>(d, region, g0, min((unsigned)WARP_ROADS, ge - g0), npass);
             unsigned nc = 0;
             if (lane_id() == 0)
                 nc = n_warps + atomicAdd(&d.ctrl->q[qsmall], 1u);
@@ -2387,6 +2611,7 @@ __device__ __forceinline__ unsigned chunk_road(const unsigned *s_first, unsigned
     return lo;
 }
 
+#if SVT_BLOCK == 256   // the plain pipeline's output stage
 // Output of one chunk of ROAD_CHUNK roads (plain kernels): a block scan of
 // the survivor counts gives each road's first output slot; then each thread
 // takes survivors (not roads), so roads with many survivors are spread out.
@@ -2410,6 +2635,7 @@ __device__ void p5_item(const Dev &d, unsigned c, unsigned n_roads, unsigned *s_
     }
     __syncthreads();   // s_first is reused by the next chunk
 }
+#endif
 
 // P4 of the persistent kernel: the cross-road hit-warrior over the
 // candidate roads only (P2 sets their bits; the others keep their
@@ -2601,7 +2827,7 @@ __device__ void clear_hash(const Dev &d)
 // ---------------------------------------------------------------------------
 
 
-__global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_persistent(Dev d)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if (d.skip_arrival == 1 && blockIdx.x == 0)
@@ -2643,6 +2869,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_persistent(Dev d)
         atomicMax(&d.ctrl->t_phase[6], globaltimer_ns());
 }
 
+#if SVT_BLOCK == 256
 // ---------------------------------------------------------------------------
 // plain per-stage kernels
 // ---------------------------------------------------------------------------
@@ -2833,30 +3060,22 @@ __global__ void __launch_bounds__(BLOCK) k_export_roads(Dev d)
     }
 }
 
+#endif   // the plain per-stage kernels
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
 static size_t p1_smem() { return WARPS * sizeof(P1Warp); }
-static size_t p2_smem() { return sizeof(P2Smem); }
+static size_t p2_smem() { return sizeof(P2Smem) > WARPS * P2W_BYTES ? sizeof(P2Smem) : WARPS * P2W_BYTES; }
 static size_t p3_smem() { return WARPS * P3_WARP_BYTES; }
-
-static_assert(sizeof(P5Smem) <= WARPS * P3_WARP_BYTES, "the output stage needs no more shared memory than the fit");
 
 size_t persistent_smem_bytes()
 {
-    size_t a = p2_smem(), b = p3_smem(), c = p1_smem(), e = sizeof(P5Smem);
+    size_t a = p2_smem(), b = p3_smem(), c = p1_smem(), e = sizeof(P5Smem);   // p2_smem: both P2 paths
     a = a > b ? a : b;
     a = a > c ? a : c;
     return a > e ? a : e;
-}
-
-static int plain_grid()
-{
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms * 4;
 }
 
 static cudaError_t set_smem_attrs()
@@ -2868,6 +3087,7 @@ static cudaError_t set_smem_attrs()
     if ((e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)persistent_smem_bytes())))
         return e;
+#if SVT_BLOCK == 256
     if ((e = cudaFuncSetAttribute(k_p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2_smem())))
         return e;
     if ((e = cudaFuncSetAttribute(k_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem())))
@@ -2875,6 +3095,7 @@ static cudaError_t set_smem_attrs()
     if ((e = cudaFuncSetAttribute(k_warrior_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)p3_smem())))
         return e;
+#endif
     done = true;
     return cudaSuccess;
 }
@@ -2889,6 +3110,49 @@ int persistent_max_blocks_per_sm(int device)
                                                       persistent_smem_bytes()) != cudaSuccess)
         return 0;
     return nb;
+}
+
+cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas, int *n_launches)
+{
+    cudaError_t e = set_smem_attrs();
+    if (e)
+        return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int maxb = persistent_max_blocks_per_sm(dev);
+    if (maxb <= 0)
+        return cudaErrorInvalidConfiguration;
+    int bps = blocks_per_sm > 0 && blocks_per_sm < maxb ? blocks_per_sm : maxb;
+    Dev dd = d;
+    void *args[] = {&dd};
+    cudaLaunchConfig_t cfg = {};
+    int grid = sms * bps;
+    if (max_ctas > 0 && max_ctas < grid)
+        grid = max_ctas;
+    if (grid > GRID_MAX)   // the word spans (one per warp) and the per-CTA totals are sized for this
+        grid = GRID_MAX;
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.dynamicSmemBytes = persistent_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, (const void *)k_persistent, args);
+    *n_launches += 1;
+    return e;
+}
+
+#if SVT_BLOCK == 256
+static int plain_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * 4 < GRID_MAX ? sms * 4 : GRID_MAX;
 }
 
 cudaError_t launch_unpack_plain(const Dev &d, cudaStream_t s, int *n_launches)
@@ -2920,44 +3184,12 @@ cudaError_t launch_fit_plain(const Dev &d, cudaStream_t s, int *n_launches)
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const Dev &d, cudaStream_t s, int blocks_per_sm, int max_ctas, int *n_launches)
-{
-    cudaError_t e = set_smem_attrs();
-    if (e)
-        return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int maxb = persistent_max_blocks_per_sm(dev);
-    if (maxb <= 0)
-        return cudaErrorInvalidConfiguration;
-    int bps = blocks_per_sm > 0 && blocks_per_sm < maxb ? blocks_per_sm : maxb;
-    Dev dd = d;
-    void *args[] = {&dd};
-    cudaLaunchConfig_t cfg = {};
-    int grid = sms * bps;
-    if (max_ctas > 0 && max_ctas < grid)
-        grid = max_ctas;
-    if (grid > MAX_GRID)
-        grid = MAX_GRID;
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(BLOCK);
-    cfg.dynamicSmemBytes = persistent_smem_bytes();
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelExC(&cfg, (const void *)k_persistent, args);
-    *n_launches += 1;
-    return e;
-}
-
 cudaError_t launch_export_roads(const Dev &d, cudaStream_t s)
 {
     k_export_roads<<<plain_grid(), BLOCK, 0, s>>>(d);
     return cudaGetLastError();
 }
+#endif
 
+}  // namespace SVT_KNS
 }  // namespace svt

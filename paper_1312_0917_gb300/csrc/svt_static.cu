@@ -37,8 +37,8 @@ constexpr size_t OFF_CTRL = 0;
 constexpr size_t OFF_CONSTS = OFF_CTRL + up256(sizeof(Ctrl));
 constexpr unsigned S_SPANS = MAX_SPANS + MAX_GRID;   // per-warp word spans, then per-CTA totals
 constexpr size_t OFF_SPAN = OFF_CONSTS + up256(sizeof(svt_const_set) * N_SETS);    // 3 x [S_SPANS] u32
-constexpr size_t OFF_EV = OFF_SPAN + up256(3 * sizeof(uint32_t) * S_SPANS);         // [S_EVENTS] u32
-constexpr size_t OFF_ROADS = OFF_EV + up256(sizeof(uint32_t) * S_EVENTS);
+constexpr size_t OFF_EV = OFF_SPAN + up256(3 * sizeof(uint32_t) * S_SPANS);         // 2 x [S_EVENTS] u32
+constexpr size_t OFF_ROADS = OFF_EV + up256(2 * sizeof(uint32_t) * S_EVENTS);
 constexpr size_t OFF_COORDS = OFF_ROADS + up256(sizeof(RoadRec) * S_ROADS);
 constexpr size_t OFF_XMASK = OFF_COORDS + up256(sizeof(uint16_t) * 40 * S_ROADS);
 constexpr size_t OFF_BIG = OFF_XMASK + up256(sizeof(unsigned long long) * S_ROADS);
@@ -123,6 +123,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.span_ep = span + S_SPANS;
     d.span_seg = span + 2 * S_SPANS;
     d.ev_road_end = reinterpret_cast<uint32_t *>(b + OFF_EV);
+    d.ev_big = d.ev_road_end + S_EVENTS;
     d.roads = reinterpret_cast<RoadRec *>(b + OFF_ROADS);
     d.coords = reinterpret_cast<uint16_t *>(b + OFF_COORDS);
     d.xmask = reinterpret_cast<unsigned long long *>(b + OFF_XMASK);
@@ -143,6 +144,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
     d.tracks = d_tracks;
     d.cut = chi2_cut;
     d.small_n4 = N4_SMALL_MAX;
+    d.run_roads = WARP_ROADS;
     d.wait_ns = 2000000000ull;
 
     // what must start at zero: the control block every batch, the group
@@ -155,7 +157,7 @@ extern "C" int svt_run_static(const uint32_t *d_words, size_t n_words, const svt
         cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s) ||
         (da->hash_dirty && (cudaMemsetAsync(d.hash, 0, sizeof(HashSlot) * S_HASH, s) ||
                             cudaMemsetAsync(d.hash_bits, 0, sizeof(uint32_t) * (S_HASH / 32 + 1), s))) ||
-        launch_persistent(d, s, 0, 0, &launches))
+        launch_persistent(256, d, s, 0, 0, &launches))
         return SVT_E_CUDA;
     Ctrl h;
     if (cudaMemcpyAsync(&h, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s))

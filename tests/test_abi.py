@@ -44,6 +44,7 @@ def test_strerror_and_null_checks(lib):
     assert lib.svt_last_launch_count(None) == 0
     assert lib.svt_server_create(None, 0, None, None, 0, 0) == B.E_INVAL
     assert lib.svt_server_submit(None, None, 0, None) == B.E_INVAL
+    assert lib.svt_set_launch(None, None) == B.E_INVAL and lib.svt_get_launch(None, None) == B.E_INVAL
 
 
 def test_struct_layouts():
@@ -53,6 +54,7 @@ def test_struct_layouts():
     assert B.ROAD_DTYPE.itemsize == 100 and B.ROAD_DTYPE.fields["coord"][1] == 20
     assert C.sizeof(B.Limits) == 40 and C.sizeof(B.Stats) == 104
     assert C.sizeof(B.ServerConfig) == 56 and C.sizeof(B.ServerResult) == 48
+    assert C.sizeof(B.Launch) == 16 and C.sizeof(B.TunePoint) == 20
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):

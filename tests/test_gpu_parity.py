@@ -76,6 +76,25 @@ def test_shared_hits_cross_road(ctx, orc, consts, mode, seed):
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_event_sizes_around_the_warp_limit_of_the_flag_stage(ctx, orc, consts, mode):
+    """The cross-road flag stage takes events of at most 64 roads one warp
+    each and larger ones a CTA each: events of 1, 2, 63, 64, 65, 128 and 256
+    roads, interleaved, whose roads copy hits from each other, equal the
+    oracle, and cross-road groups are published."""
+    parts = []
+    for i, r in enumerate((64, 65, 1, 63, 256, 64, 128, 65, 2, 63)):
+        cfg = synth.Config("mix%d" % r, 3, ("fixed", r), ("uniform", 1, 3), shared_hits=0.6)
+        parts.append(synth.make_batch(cfg, seed=40 + i).words)
+    words = np.concatenate(parts)
+    rc, chi = orc.chi2_all(words, consts)
+    cut = int(np.sort(chi)[(9 * len(chi) + 9) // 10 - 1])
+    ctx.load_constants(consts, cut)
+    st, got, stats = run_gpu(ctx, words, mode)
+    assert st == B.OK and stats["n_groups"] > 0
+    assert_same_tracks(got, oracle_tracks(orc, words, consts, cut))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 def test_duplicate_coordinates_and_empty_layers(ctx, orc, consts, mode):
     """Coordinates drawn from a tiny range: equal values inside a layer and
     across roads everywhere; hits 0..3 per layer (empty layers)."""
@@ -222,16 +241,51 @@ def test_back_to_back_batches_and_modes(ctx, orc, consts, cuts):
         assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["small"]))
 
 
-@pytest.mark.parametrize("bps,small", [(1, 0), (2, 64), (0, 16), (3, 256)])
-def test_launch_settings_are_bit_equal(ctx, consts, cuts, bps, small):
+def launch_grid(ctx):
+    """Every configuration the autotuner measures (block size, CTAs per SM up
+    to that size's occupancy maximum, small_n4, roads per queue claim)."""
+    out = []
+    for block in (128, 256, 512):
+        ctx.set_launch(block=block)
+        for bps in range(1, ctx.get_launch()["blocks_per_sm"] + 1):
+            for small in (64, 128, 256):
+                for run in (4, 8, 16):
+                    out.append(dict(block=block, blocks_per_sm=bps, small_n4=small, run_roads=run))
+    ctx.set_launch()
+    return out
+
+
+def test_launch_settings_are_bit_equal(ctx, orc, consts, cuts):
+    """Every launch configuration of the autotuner's grid, and a few outside
+    it, give the same bytes as the default on an uneven batch (which equals
+    the oracle)."""
     b = synth.make_batch("uneven", seed=2, n_events=1500)
     ctx.load_constants(consts, cuts["uneven"])
-    ctx.set_launch(0, 0)
+    ctx.set_launch()
     st, ref, _ = run_gpu(ctx, b.words, B.PERSISTENT)
-    ctx.set_launch(bps, small)
-    st2, got, _ = run_gpu(ctx, b.words, B.PERSISTENT)
-    ctx.set_launch(0, 0)
-    assert st == st2 == B.OK and ref.tobytes() == got.tobytes()
+    assert st == B.OK
+    assert_same_tracks(ref, oracle_tracks(orc, b.words, consts, cuts["uneven"]))
+    grid = launch_grid(ctx)
+    assert {g["block"] for g in grid} == {128, 256, 512} and len(grid) >= 3 * 3 * 3 * 3
+    extra = [dict(block=256, blocks_per_sm=0, small_n4=16, run_roads=4),
+             dict(block=512, blocks_per_sm=0, small_n4=1, run_roads=16)]
+    for cfg in grid + extra:
+        ctx.set_launch(**cfg)
+        st2, got, _ = run_gpu(ctx, b.words, B.PERSISTENT)
+        assert st2 == B.OK and ref.tobytes() == got.tobytes(), cfg
+    ctx.set_launch()
+
+
+def test_launch_settings_are_checked(ctx):
+    for bad in (dict(block=64), dict(block=384), dict(run_roads=3), dict(run_roads=32),
+                dict(small_n4=257), dict(blocks_per_sm=-1)):
+        with pytest.raises(B.SvtError) as e:
+            ctx.set_launch(**bad)
+        assert e.value.code == B.E_INVAL
+    ctx.set_launch(block=512)
+    got = ctx.get_launch()
+    assert got["block"] == 512 and got["blocks_per_sm"] >= 1 and got["small_n4"] == 256 and got["run_roads"] == 8
+    ctx.set_launch()
 
 
 def test_graph_launch(ctx, consts, cuts):
@@ -381,14 +435,15 @@ def test_autotune_keeps_the_fastest_and_the_tracks(ctx, orc, consts, cuts):
     ctx.load_constants(consts, cuts["uneven"])
     d = torch_words(b.words)
     assert ctx.unpack(d, len(b.words)) == B.OK
+    grid = launch_grid(ctx)
     pts = ctx.autotune(reps=3)
-    assert len(pts) >= 3 and len(pts) % 3 == 0
-    assert {p[1] for p in pts} == {64, 128, 256}
-    assert all(p[2] > 0 for p in pts)
+    assert [p[0] for p in pts] == grid
+    assert all(p[1] > 0 for p in pts)
+    assert ctx.get_launch() == min(pts, key=lambda p: p[1])[0]   # the fastest is kept
     st, got, _ = run_gpu(ctx, b.words, B.PERSISTENT, d_words=d)
     assert st == B.OK
     assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cuts["uneven"]))
-    ctx.set_launch(0, 0)
+    ctx.set_launch()
 
 
 def test_two_contexts_taking_batches_in_turn(ctx, consts, cuts):
