@@ -293,10 +293,10 @@ typedef struct {
     uint32_t ctas_per_sm;      /* CTAs per SM of each request's persistent kernel (0 = 1) */
     uint32_t max_ctas;         /* grid cap of each request's kernel (0 = SMs x ctas_per_sm) */
     int32_t mode;              /* SVT_PERSISTENT or SVT_PLAIN (0 is SVT_PLAIN) */
-    uint64_t max_words;        /* words per request (0 = 1 << 21, below 1 << 31) */
-    uint32_t max_events;       /* events per request (0 = 4096) */
-    uint32_t max_roads;        /* roads per request (0 = 1 << 17) */
-    uint64_t max_tracks;       /* tracks per request (0 = 1 << 20) */
+    uint64_t max_words;        /* words per slot (0 = 1 << 21, below 1 << 31) */
+    uint32_t max_events;       /* events per slot (0 = 4096) */
+    uint32_t max_roads;        /* roads per slot (0 = 1 << 17) */
+    uint64_t max_tracks;       /* tracks per slot (0 = 1 << 20) */
     uint32_t hash_slots;       /* cross-road group table per slot, power of 2 (0 = 1 << 20) */
     uint32_t pad;
     uint64_t max_combinations; /* SVT_PLAIN combination buffers per slot (0 = 1 << 24) */
@@ -327,9 +327,14 @@ int svt_server_get_config(svt_server *srv, svt_server_config *out);
 
 /* Admit one request: `words` (HOST memory, n_words, copied before return) is a
  * packed word stream as for svt_unpack.  Blocks until a slot is free; returns
- * the request's id in *request_id.  SVT_E_CAPACITY if n_words exceeds
- * max_words (the request is not admitted).  Errors of the request itself
- * (format, limits, capacity, CUDA) are its result's status.  Thread-safe. */
+ * the request's id in *request_id.  A request with more words, events (EE
+ * words) or roads (EP words) than a slot holds is cut at event boundaries
+ * into chunks that fit, admitted one after the other as slots free up; its
+ * result (one id) joins the chunks' tracks in stream order with their event
+ * indices offset, and its status is that of the first chunk that failed.
+ * SVT_E_CAPACITY (nothing admitted) only if one event alone exceeds a slot's
+ * max_words or max_roads.  Errors of the request itself (format, limits,
+ * capacity, CUDA) are its result's status.  Thread-safe. */
 int svt_server_submit(svt_server *srv, const uint32_t *words, size_t n_words, uint64_t *request_id);
 
 /* Next completed request, in completion order: waits up to timeout_us

@@ -1905,9 +1905,12 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 // ---------------------------------------------------------------------------
 
 enum { T_AB = 0, T_CE, T_AC, T_BC, T_AE, T_BE, N_TAB };
+// table row stride: rows 9 entries (72 bytes) apart put the 64-bit entries
+// [u][v] of different u in different banks
+constexpr unsigned TS = 9;
 
 struct P3Box {
-    unsigned long long T[N_TAB][64];   // pair tables, [u * 8 + v] (u: the first role's hit); T_ce
+    unsigned long long T[N_TAB][8 * TS];   // pair tables, [u * TS + v] (u: the first role's hit); T_ce
                                        // only where needed (box_tce)
     int4 A[4][8];                      // slot j, canonical hit k: chi-square partial sums (x, y,
                                        // z) and comb part (w); slot 0 also carries curvature, phi,
@@ -2018,18 +2021,18 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
         }
         qab = umin64(qab, rz);
         if (act) {
-            atomicMin(&B.T[T_AC][x * 8 + z], rz);
-            atomicMin(&B.T[T_BC][y * 8 + z], rz);
+            atomicMin(&B.T[T_AC][x * TS + z], rz);
+            atomicMin(&B.T[T_BC][y * TS + z], rz);
         }
     }
     if (act)
-        B.T[T_AB][x * 8 + y] = qab;
+        B.T[T_AB][x * TS + y] = qab;
     if (act) {
 #pragma unroll
         for (unsigned w = 0; w < ME; ++w)
             if (w < me) {
-                atomicMin(&B.T[T_AE][x * 8 + w], rw[w]);
-                atomicMin(&B.T[T_BE][y * 8 + w], rw[w]);
+                atomicMin(&B.T[T_AE][x * TS + w], rw[w]);
+                atomicMin(&B.T[T_BE][y * TS + w], rw[w]);
             }
     }
     __syncwarp();
@@ -2078,7 +2081,7 @@ __device__ __forceinline__ unsigned box_tab(const BoxShape &sh, unsigned p, unsi
         r2 = tr;
         k2 = tk;
     }
-    idx = k1 * 8 + k2;
+    idx = k1 * TS + k2;
     // role pairs (0,1) ab, (2,3) ce, (0,2) ac, (1,2) bc, (0,3) ae, (1,3) be
     return r1 == 0 && r2 == 1 ? T_AB : r1 == 2 ? T_CE : r2 == 2 ? (r1 == 0 ? T_AC : T_BC) : (r1 == 0 ? T_AE : T_BE);
 }
@@ -2095,7 +2098,7 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
     __syncwarp();   // the region's previous user is done
     if (lane < N_LAYERS)   // 80 bytes of coordinates, five 16-byte words
         reinterpret_cast<uint4 *>(B.co)[lane] = ldcg(reinterpret_cast<const uint4 *>(d.coords + (size_t)g * 40) + lane);
-    for (unsigned i = lane; i < N_TAB * 64; i += 32)
+    for (unsigned i = lane; i < N_TAB * 8 * TS; i += 32)
         (&B.T[0][0])[i] = NO_KEY;
     __syncwarp();
 
@@ -2217,7 +2220,7 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
         const unsigned t = p * 32 + lane;
         if (p < passes && t < ma * mb) {
             const unsigned y = divm(t, c_magic[ma]), x = t - y * ma;
-            const unsigned long long key = B.T[T_AB][x * 8 + y];
+            const unsigned long long key = B.T[T_AB][x * TS + y];
             if (key != NO_KEY) {
                 // raw hits of the layers of slots c and e from the comb
                 unsigned rest = (unsigned)(key & 0x7FFFu), dc = 0, de = 0;
@@ -2232,8 +2235,8 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                     de = l == Le ? dl : de;
                 }
                 const unsigned z = B.rank[sh.rc][dc], w = B.rank[sh.re][de];
-                sv[p] = B.T[T_AC][x * 8 + z] == key && B.T[T_BC][y * 8 + z] == key &&
-                        B.T[T_AE][x * 8 + w] == key && B.T[T_BE][y * 8 + w] == key;
+                sv[p] = B.T[T_AC][x * TS + z] == key && B.T[T_BC][y * TS + z] == key &&
+                        B.T[T_AE][x * TS + w] == key && B.T[T_BE][y * TS + w] == key;
                 sk[p] = key;
                 zw[p] = z * 8 + w;
             }
@@ -2309,7 +2312,7 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                         const unsigned z = B.rank[sh.rc][__ffs(bc) - 1], w = B.rank[sh.re][__ffs(be) - 1];
                         const unsigned long long m = box_tce<PLAIN>(d, B, sh, z, w);
                         if (lane == 0)
-                            B.T[T_CE][z * 8 + w] = m;
+                            B.T[T_CE][z * TS + w] = m;
                     }
             __syncwarp();
         }

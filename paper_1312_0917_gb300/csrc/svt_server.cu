@@ -12,6 +12,14 @@
 // SMs).  A progress thread watches the slots' events; when a slot's control
 // block has arrived its tracks are already in host memory, and the result is
 // published.  Latency runs from svt_server_submit to that moment.
+//
+// A request larger than a slot (more words, events or roads than a slot's
+// limits) is cut at event boundaries into chunks that fit, and each chunk is
+// admitted like a request of its own as slots free up; the chunks' results
+// are joined in stream order (event indices offset) into the request's
+// result once the last chunk is done.  Events are independent (the
+// hit-warrior's scope is one event), so the joined result is the whole
+// request's.
 #include "svt_ctx.h"
 
 #include <algorithm>
@@ -48,6 +56,8 @@ struct Slot {
     cudaEvent_t ev_ctrl = nullptr;   // control block (and so the tracks) in host memory
     int state = SLOT_FREE;
     uint64_t id = 0;
+    uint64_t parent = 0;             // the split request this slot runs a chunk of (0 = none)
+    unsigned chunk = 0;
     size_t n_tracks = 0;
     int status = SVT_OK;
     Clock::time_point t_submit;
@@ -56,6 +66,17 @@ struct Slot {
 struct Result {
     svt_server_result info;
     std::vector<svt_track> tracks;
+};
+
+// A request split into chunks: their results until the last one is done.
+struct Parent {
+    uint64_t id = 0;
+    unsigned n_done = 0;
+    std::vector<uint32_t> ev_base;                 // event index of each chunk's first event
+    std::vector<int> status;                       // per chunk
+    std::vector<std::vector<svt_track>> tracks;    // per chunk
+    uint64_t n_events = 0, n_comb = 0;
+    Clock::time_point t_submit;
 };
 
 }  // namespace
@@ -69,6 +90,7 @@ struct svt_server {
     std::condition_variable cv_done;   // a result is ready
     std::deque<uint64_t> done_order;   // completed, not yet reported by svt_server_wait
     std::list<Result> results;         // completed, not yet taken
+    std::list<Parent> parents;         // split requests with chunks in flight
     std::thread progress;
     std::atomic<bool> stop{false};
     uint64_t next_id = 1;
@@ -77,8 +99,67 @@ struct svt_server {
 
 namespace {
 
+// The last chunk of split request p is done: its joined result.  Called
+// with s->mu held.
+void publish_parent(svt_server *s, std::list<Parent>::iterator p)
+{
+    Result r;
+    r.info.request_id = p->id;
+    r.info.status = SVT_OK;
+    for (int st : p->status)   // the first chunk that failed, in stream order
+        if (st != SVT_OK) {
+            r.info.status = st;
+            break;
+        }
+    r.info.pad = 0;
+    r.info.n_events = p->n_events;
+    r.info.n_combinations = p->n_comb;
+    if (r.info.status == SVT_OK) {
+        size_t n = 0;
+        for (const auto &t : p->tracks)
+            n += t.size();
+        r.tracks.reserve(n);
+        for (size_t k = 0; k < p->tracks.size(); ++k)
+            for (svt_track t : p->tracks[k]) {
+                t.event += p->ev_base[k];
+                r.tracks.push_back(t);
+            }
+    }
+    r.info.n_tracks = r.tracks.size();
+    r.info.latency_ns =
+        (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - p->t_submit).count();
+    s->results.push_back(std::move(r));
+    s->done_order.push_back(p->id);
+    s->parents.erase(p);
+    s->cv_done.notify_all();
+}
+
 void finish(svt_server *s, Slot &sl, int status, size_t n_tracks)
 {
+    if (sl.parent) {   // a chunk of a split request
+        const Ctrl &h = *sl.ctx->h_ctrl;
+        std::vector<svt_track> tr;
+        if (status == SVT_OK && n_tracks)
+            tr.assign(sl.h_tracks, sl.h_tracks + n_tracks);
+        if (h.flags & FLAG_TIMEOUT)
+            sl.ctx->hash_dirty = true;
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto it = s->parents.begin(); it != s->parents.end(); ++it)
+            if (it->id == sl.parent) {
+                it->status[sl.chunk] = status;
+                it->tracks[sl.chunk] = std::move(tr);
+                it->n_events += h.n_events;
+                it->n_comb += h.n_comb;
+                if (++it->n_done == it->status.size())
+                    publish_parent(s, it);
+                break;
+            }
+        sl.state = SLOT_FREE;
+        sl.parent = 0;
+        --s->in_flight;
+        s->cv_slot.notify_all();
+        return;
+    }
     Result r;
     r.info.request_id = sl.id;
     r.info.status = status;
@@ -292,14 +373,16 @@ int svt_server_get_config(svt_server *s, svt_server_config *out)
     return SVT_OK;
 }
 
-int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t *request_id)
+}  // extern "C"
+
+namespace {
+
+// Admit one request or chunk to the first free slot (waiting for one) and
+// enqueue its copy, kernel and control-block read.  parent != 0: chunk
+// `chunk` of that split request.
+void admit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t parent, unsigned chunk,
+           Clock::time_point t0, uint64_t *id)
 {
-    if (!s || !request_id || (n_words && !words))
-        return SVT_E_INVAL;
-    *request_id = 0;
-    if (n_words > s->cfg.max_words)
-        return SVT_E_CAPACITY;
-    const Clock::time_point t0 = Clock::now();
     Slot *sl = nullptr;
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -312,12 +395,15 @@ int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint
             return false;
         });
         sl->state = SLOT_RESERVED;
-        sl->id = s->next_id++;
+        sl->id = parent ? 0 : s->next_id++;
+        sl->parent = parent;
+        sl->chunk = chunk;
         sl->t_submit = t0;
         ++s->in_flight;
     }
     s->cv_slot.notify_all();   // wakes an idle progress thread
-    *request_id = sl->id;
+    if (id)
+        *id = sl->id;
     if (n_words)
         std::memcpy(sl->h_words, words, n_words * sizeof(uint32_t));
     int launches = 0;
@@ -334,13 +420,85 @@ int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint
     if (!ok) {
         cudaGetLastError();
         std::memset(sl->ctx->h_ctrl, 0, sizeof(Ctrl));
-        finish(s, *sl, SVT_E_CUDA, 0);
-        return SVT_OK;   // the failure is the request's status
+        finish(s, *sl, SVT_E_CUDA, 0);   // the failure is the request's status
+        return;
     }
     sl->ctx->ran = true;
     sl->ctx->last_launches = launches;
     std::lock_guard<std::mutex> lk(s->mu);
     sl->state = SLOT_RUNNING;
+}
+
+// Cut points of a request at event ends (EE words) into chunks of at most
+// the slot's words, events and roads (EP words); the words after the last EE
+// (a truncated event) go with the last chunk.  Empty if one event alone
+// exceeds a slot.
+std::vector<size_t> split_points(const svt_server_config &cfg, const uint32_t *w, size_t n)
+{
+    std::vector<size_t> cuts{0};   // chunk k: words [cuts[k], cuts[k + 1])
+    size_t ev_start = 0, chunk_ev = 0, chunk_roads = 0, ev_roads = 0;
+    for (size_t i = 0; i < n; ++i) {
+        ev_roads += (w[i] >> 30) & 1u;
+        if (!(w[i] >> 31) && i + 1 < n)
+            continue;
+        // an event ends at i (or the stream does)
+        const size_t ev_end = i + 1, ev_words = ev_end - ev_start;
+        if (ev_words > cfg.max_words || ev_roads > cfg.max_roads)
+            return {};
+        if (ev_end - cuts.back() > cfg.max_words || chunk_ev + 1 > cfg.max_events ||
+            chunk_roads + ev_roads > cfg.max_roads) {
+            cuts.push_back(ev_start);
+            chunk_ev = 0;
+            chunk_roads = 0;
+        }
+        ++chunk_ev;
+        chunk_roads += ev_roads;
+        ev_roads = 0;
+        ev_start = ev_end;
+    }
+    cuts.push_back(n);
+    return cuts;
+}
+
+}  // namespace
+
+extern "C" {
+
+int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t *request_id)
+{
+    if (!s || !request_id || (n_words && !words))
+        return SVT_E_INVAL;
+    *request_id = 0;
+    const Clock::time_point t0 = Clock::now();
+    const std::vector<size_t> cuts = split_points(s->cfg, words, n_words);
+    if (cuts.size() < 2)
+        return SVT_E_CAPACITY;   // one event alone exceeds a slot
+    const unsigned n_chunks = (unsigned)(cuts.size() - 1);
+    if (n_chunks == 1) {
+        admit(s, words, n_words, 0, 0, t0, request_id);
+        return SVT_OK;
+    }
+    // larger than a slot: chunks at event boundaries
+    uint64_t pid;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        pid = s->next_id++;
+        Parent p;
+        p.id = pid;
+        p.status.assign(n_chunks, SVT_OK);
+        p.tracks.resize(n_chunks);
+        p.t_submit = t0;
+        uint32_t ev = 0;
+        for (unsigned k = 0; k < n_chunks; ++k) {
+            p.ev_base.push_back(ev);
+            for (size_t i = cuts[k]; i < cuts[k + 1]; ++i)
+                ev += words[i] >> 31;
+        }
+        s->parents.push_back(std::move(p));
+    }
+    *request_id = pid;
+    for (unsigned k = 0; k < n_chunks; ++k)
+        admit(s, words + cuts[k], cuts[k + 1] - cuts[k], pid, k, t0, nullptr);
     return SVT_OK;
 }
 

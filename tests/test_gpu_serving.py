@@ -105,3 +105,53 @@ def test_admission_limits(consts, cuts):
         assert e.value.code == B.E_STATE
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("limits", [dict(max_words=8192), dict(max_events=7), dict(max_roads=300)],
+                         ids=["words", "events", "roads"])
+def test_a_request_larger_than_a_slot_is_split_at_event_boundaries(alone_ctx, orc, consts, cuts, limits):
+    """A request with more words, events or roads than a slot holds runs in
+    chunks on whichever slots free up; its one result equals the whole
+    request run alone (and the oracle), next to ordinary requests."""
+    big = synth.make_batch("scaled", seed=77, n_events=60).words      # about 60 k words
+    small = requests(4, 6, 5)
+    srv = B.Server(consts, cuts["scaled"], n_slots=2, **limits)
+    try:
+        got = serve_all(srv, small[:3] + [big] + small[3:])
+    finally:
+        srv.close()
+    alone_ctx.load_constants(consts, cuts["scaled"])
+    for i, w in enumerate(small[:3] + [big] + small[3:]):
+        r, tracks = got[i]
+        assert r["status"] == B.OK
+        st, alone, stats = run_gpu(alone_ctx, w, B.PERSISTENT)
+        assert st == B.OK and tracks.tobytes() == alone.tobytes(), i
+        assert r["n_events"] == stats["n_events"] and r["n_combinations"] == stats["n_combinations"]
+    rc, want = orc.run(big, consts, cuts["scaled"])
+    assert rc == 0 and got[3][0]["n_events"] == 60
+    assert_same_tracks(got[3][1], want)
+
+
+def test_a_split_request_reports_the_first_failing_chunk(consts, cuts):
+    """Status of a split request: the first chunk (in stream order) that
+    failed; no tracks then.  An event larger than a slot is refused."""
+    big = synth.make_batch("scaled", seed=78, n_events=40).words
+    bad = big.copy()
+    bad[len(bad) * 3 // 4] |= np.uint32(1 << 20)    # a reserved payload bit in a late chunk
+    trunc = big[:-5]                                # the last event loses its end
+    srv = B.Server(consts, cuts["scaled"], n_slots=2, max_words=4096)
+    try:
+        got = serve_all(srv, [bad, trunc, big])
+    finally:
+        srv.close()
+    assert got[0][0]["status"] == B.E_BADWORD and got[0][0]["n_tracks"] == 0
+    assert got[1][0]["status"] == B.E_TRUNCATED and got[1][0]["n_tracks"] == 0
+    assert got[2][0]["status"] == B.OK and got[2][0]["n_events"] == 40
+    one_event = int(np.diff(synth.make_batch("scaled", seed=78, n_events=2).event_offsets).max())
+    srv = B.Server(consts, cuts["scaled"], n_slots=1, max_words=one_event - 1)
+    try:
+        with pytest.raises(B.SvtError) as e:
+            srv.submit(big)
+        assert e.value.code == B.E_CAPACITY
+    finally:
+        srv.close()
