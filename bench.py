@@ -1,7 +1,7 @@
 """Benchmark of the SVT track-fitting chain on one GB300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload stress] [--no-cpu] [--no-plain] [--no-serve]
+                    [--workload stress] [--no-cpu] [--no-plain] [--no-serve] [--no-sweep]
                     [--no-tune] [--no-subs]
 
 One step = one batch of the headline workload through the whole chain:
@@ -28,6 +28,9 @@ roads x 8 hits on each of 5 layers (838,860,800 combinations).
          p99 per batch, device and end to end).
   serving  the serving runtime under Poisson arrivals at five offered event
          rates, p50 / p99 from arrival to tracks in host memory.
+  packet_sweep  end-to-end latency of one batch from 600 kB of words up,
+         with pageable, page-locked, and in-place (kernels read and write
+         page-locked host memory) buffers, and the transfer share of each.
   cpu_baseline  the oracle (test infrastructure) on the machine's host cores:
          its event-parallel driver on a bounded sample, per-stage times.
   --impl reference  the oracle as it stands, timed on the host cores.
@@ -68,6 +71,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparisons")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the packet-size sweep")
     ap.add_argument("--no-subs", action="store_true", help="skip the scaled and uneven sub-workloads")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch settings; for profiler runs)")
@@ -418,6 +422,69 @@ def sub_workload(B, torch, synth, name, consts, local, args):
     return out
 
 
+def packet_sweep(B, torch, synth, consts, local, sizes_kb=(600, 1200, 2400, 4800, 9600, 19200), reps=30):
+    """End-to-end latency of one batch against its size (kB of input words;
+    events shaped as the scaled workload, Sec. IV-C's packet sizes from 600 kB
+    up), with the host buffers in three kinds of memory: pageable (the copies
+    are staged by the driver), page-locked (DMA copies in and out), and
+    page-locked memory that the kernels read and write in place (no copies).
+    The transfer share is 1 - device time / end-to-end time."""
+    cut = load_cut("scaled")
+    per_event = 4 * (len(synth.make_batch("scaled", seed=0, n_events=64).words) / 64)
+    sizes = [(kb, max(1, int(round(kb * 1000 / per_event)))) for kb in sizes_kb]
+    n_max = max(e for _, e in sizes)
+    ctx = B.Context(local, max_words=int(n_max * per_event / 4) + 4096, max_events=n_max + 1,
+                    max_roads=64 * (n_max + 1), max_tracks=256 * (n_max + 1), max_combinations=1 << 10)
+    ctx.load_constants(consts, cut)
+    stream = torch.cuda.Stream()
+    rows = []
+    for i, (kb, n_ev) in enumerate(sizes):
+        batch = synth.make_batch("scaled", seed=500 + i, n_events=n_ev)
+        n_words = len(batch.words)
+        h_page = batch.words.view(np.int32).copy()
+        h_pin = torch.from_numpy(h_page).pin_memory()
+        d_words = torch.empty_like(h_pin, device="cuda")
+        d_words.copy_(h_pin)
+        torch.cuda.synchronize()
+        dev = run_device_steps(ctx, B, torch, d_words, n_words, B.PERSISTENT, reps, 3, stream)
+        n_tr = ctx.get_stats(stream)["n_tracks"]
+        out_page = np.empty(max(1, n_tr), dtype=B.TRACK_DTYPE)
+        out_pin = torch.empty(max(1, n_tr) * 40, dtype=torch.uint8).pin_memory()
+        out_map = torch.empty(max(1, n_tr) * 40, dtype=torch.uint8).pin_memory()
+        cap = max(1, n_tr)
+        row = {"kB": round(4 * n_words / 1e3, 1), "events": n_ev, "tracks": n_tr,
+               "device_p50_us": round(1e3 * float(np.percentile(dev, 50)), 1)}
+        for kind in ("pageable", "pinned", "in_place"):
+            if kind == "in_place":
+                ctx.set_track_output(out_map, cap)
+            lat = []
+            for r in range(3 + reps):
+                t0 = time.perf_counter()
+                if kind == "in_place":
+                    src = h_pin
+                else:
+                    with torch.cuda.stream(stream):
+                        d_words.copy_(torch.from_numpy(h_page) if kind == "pageable" else h_pin,
+                                      non_blocking=True)
+                    src = d_words
+                B.check(ctx.unpack(src, n_words, stream), "svt_unpack")
+                B.check(ctx.fit_events(B.PERSISTENT, stream), "svt_fit_events")
+                out = {"pageable": out_page, "pinned": out_pin, "in_place": out_map}[kind]
+                st, n = ctx.get_tracks(out=out, cap=cap, stream=stream)
+                B.check(st, "svt_get_tracks")
+                if r >= 3:
+                    lat.append(time.perf_counter() - t0)
+            if kind == "in_place":
+                ctx.set_track_output(None)
+            p50 = 1e6 * float(np.percentile(lat, 50))
+            row[kind] = {"p50_us": round(p50, 1), "p99_us": round(1e6 * float(np.percentile(lat, 99)), 1),
+                         "transfer_share": round(max(0.0, 1 - row["device_p50_us"] / p50), 3)}
+        rows.append(row)
+    ctx.close()
+    return {"events": "scaled-shaped (64 roads, 1-4 hits per layer)", "reps": reps,
+            "latency": "host wall time of one batch: words in, kernel, tracks out", "sizes": rows}
+
+
 def gpu_arm(args):
     import torch
     from paper_1312_0917_gb300 import binding as B, synth, build as nvbuild
@@ -549,6 +616,8 @@ def gpu_arm(args):
         for name in ("scaled", "uneven"):
             if name != args.workload:
                 line[name] = sub_workload(B, torch, synth, name, consts, local, args)
+    if not args.no_sweep and world == 1:
+        line["packet_sweep"] = packet_sweep(B, torch, synth, consts, local)
     if not args.no_serve and world == 1:
         line["serving"] = run_serving(B, synth, consts, load_cut("serving"),
                                       (1e4, 3e4, 1e5, 3e5, 1e6), args.serve_requests)

@@ -147,8 +147,11 @@ int svt_load_constants(svt_ctx *ctx, const svt_const_set *sets, uint32_t n_sets,
  * the same word); a stream not ending in EE is SVT_E_TRUNCATED.
  * The call binds the batch and schedules the unpack stage: in SVT_PLAIN mode
  * it runs as its own kernels inside svt_fit_events (or svt_get_roads), in
- * SVT_PERSISTENT mode inside the fused kernel.  n_words > max_words ->
- * SVT_E_CAPACITY. */
+ * SVT_PERSISTENT mode inside the fused kernel.  d_words is device memory or
+ * page-locked host memory (cudaHostAlloc / cudaMallocHost / registered),
+ * which the kernels then read in place over the CPU-GPU link; pageable host
+ * memory -> SVT_E_INVAL.  The caller keeps the words unchanged until the
+ * batch's svt_get_tracks returns.  n_words > max_words -> SVT_E_CAPACITY. */
 int svt_unpack(svt_ctx *ctx, const uint32_t *d_words, size_t n_words, void *stream);
 
 /* Sec. II, second and third functions, plus the selection: every combination
@@ -170,6 +173,15 @@ int svt_fit_events(svt_ctx *ctx, int mode, void *stream);
 int svt_get_tracks(svt_ctx *ctx, svt_track *out, size_t cap, size_t *n_out,
                    void *stream);
 
+/* Have the output stage write the surviving tracks straight into `host`
+ * (page-locked host memory, cap records, 8-byte aligned; the caller owns
+ * it), over the CPU-GPU link, instead of the context's device buffer;
+ * svt_get_tracks with out == host then copies nothing.  A batch with more
+ * than cap tracks ends with SVT_E_CAPACITY.  host = NULL returns to the
+ * device buffer.  SVT_E_INVAL for pageable or unaligned memory.  Takes effect
+ * from the next svt_fit_events (a captured graph is dropped). */
+int svt_set_track_output(svt_ctx *ctx, svt_track *host, size_t cap);
+
 /* Synchronise `stream` and return the unpacked roads of complete events in
  * stream order (runs the unpack stage first if it has not run yet).
  * *n_out = road count; SVT_E_CAPACITY if cap is too small. */
@@ -187,6 +199,7 @@ typedef struct {
                               * four fitted layers) take a warp of their own (the box path); the
                               * others are fitted in runs of roads (1 .. 256, 0 = 256) */
     int32_t run_roads;       /* roads per queue claim of those runs: 4, 8 or 16 (0 = 8) */
+    int32_t max_ctas;        /* cap on the grid (0 = SMs x blocks_per_sm); the autotuner keeps it */
 } svt_launch;
 
 /* Set the launch settings; they take effect from the next svt_fit_events
@@ -293,9 +306,9 @@ typedef struct {
     uint32_t ctas_per_sm;      /* CTAs per SM of each request's persistent kernel (0 = 1) */
     uint32_t max_ctas;         /* grid cap of each request's kernel (0 = SMs x ctas_per_sm) */
     int32_t mode;              /* SVT_PERSISTENT or SVT_PLAIN (0 is SVT_PLAIN) */
-    uint64_t max_words;        /* words per slot (0 = 1 << 21, below 1 << 31) */
-    uint32_t max_events;       /* events per slot (0 = 4096) */
-    uint32_t max_roads;        /* roads per slot (0 = 1 << 17) */
+    uint64_t max_words;        /* words per slot (0 = 1 << 20, below 1 << 31) */
+    uint32_t max_events;       /* events per slot (0 = max_words / 3 + 1: any stream of max_words) */
+    uint32_t max_roads;        /* roads per slot (0 = max_words / 3 + 1) */
     uint64_t max_tracks;       /* tracks per slot (0 = 1 << 20) */
     uint32_t hash_slots;       /* cross-road group table per slot, power of 2 (0 = 1 << 20) */
     uint32_t pad;

@@ -55,7 +55,7 @@ class Stats(C.Structure):
 
 class Launch(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("small_n4", C.c_int32),
-                ("run_roads", C.c_int32)]
+                ("run_roads", C.c_int32), ("max_ctas", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +91,7 @@ SIGNATURES = {
                                 C.c_void_p]),
     "svt_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_void_p]),
     "svt_set_launch": (C.c_int, [C.c_void_p, C.POINTER(Launch)]),
+    "svt_set_track_output": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "svt_get_launch": (C.c_int, [C.c_void_p, C.POINTER(Launch)]),
     "svt_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "svt_debug_wait": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int]),
@@ -219,6 +220,12 @@ class Context:
         st = lib().svt_get_tracks(self._h, ptr(out), cap, C.byref(n), stream_ptr(stream))
         return st, n.value
 
+    def set_track_output(self, host=None, cap: int = 0):
+        """Tracks written straight into `host` (page-locked memory: a pinned
+        torch tensor or its data pointer), or back to the device buffer (None)."""
+        check(lib().svt_set_track_output(self._h, ptr(host) if host is not None else None, cap),
+              "svt_set_track_output")
+
     def get_roads(self, stream=None):
         n = C.c_size_t()
         st = lib().svt_get_roads(self._h, None, 0, C.byref(n), stream_ptr(stream))
@@ -234,8 +241,9 @@ class Context:
         check(lib().svt_get_stats(self._h, C.byref(s), stream_ptr(stream)), "svt_get_stats")
         return s.as_dict()
 
-    def set_launch(self, block: int = 0, blocks_per_sm: int = 0, small_n4: int = 0, run_roads: int = 0):
-        cfg = Launch(block, blocks_per_sm, small_n4, run_roads)
+    def set_launch(self, block: int = 0, blocks_per_sm: int = 0, small_n4: int = 0, run_roads: int = 0,
+                   max_ctas: int = 0):
+        cfg = Launch(block, blocks_per_sm, small_n4, run_roads, max_ctas)
         check(lib().svt_set_launch(self._h, C.byref(cfg)), "svt_set_launch")
 
     def get_launch(self) -> dict:
@@ -245,7 +253,7 @@ class Context:
 
     def autotune(self, reps: int = 5, stream=None) -> list:
         """Measure every launch configuration on the bound batch and keep the
-        fastest; returns [({block, blocks_per_sm, small_n4, run_roads}, ms), ...]."""
+        fastest; returns [({block, blocks_per_sm, small_n4, run_roads, max_ctas}, ms), ...]."""
         pts = (TunePoint * 512)()
         n = C.c_uint32()
         check(lib().svt_autotune(self._h, reps, pts, 512, C.byref(n), stream_ptr(stream)), "svt_autotune")

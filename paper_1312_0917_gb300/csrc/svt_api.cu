@@ -183,6 +183,7 @@ int svt_create(svt_ctx **out, int device, const svt_limits *lim)
         cudaMemset(d.hash, 0, sizeof(HashSlot) * (size_t)L.hash_slots) == cudaSuccess &&
         cudaMemset(d.hash_bits, 0, sizeof(uint32_t) * (L.hash_slots / 32 + 1)) == cudaSuccess &&
         cudaMemset(d.ctrl, 0, sizeof(Ctrl)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    c->dev_tracks = d.tracks;
     if (!ok) {
         free_all(c);
         delete c;
@@ -222,6 +223,23 @@ int svt_load_constants(svt_ctx *c, const svt_const_set *sets, uint32_t n_sets, i
     return SVT_OK;
 }
 
+// The device's address of `p`: itself for device (or managed) memory, the
+// mapped alias for page-locked host memory; nullptr for memory the device
+// cannot address (pageable host memory) or on error.
+static const void *device_view(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return p;
+    if (a.type == cudaMemoryTypeHost)
+        return a.devicePointer;
+    return nullptr;
+}
+
 int svt_unpack(svt_ctx *c, const uint32_t *d_words, size_t n_words, void *stream)
 {
     (void)stream;
@@ -229,6 +247,11 @@ int svt_unpack(svt_ctx *c, const uint32_t *d_words, size_t n_words, void *stream
         return SVT_E_INVAL;
     if (n_words > c->lim.max_words)
         return SVT_E_CAPACITY;
+    if (n_words) {
+        d_words = static_cast<const uint32_t *>(device_view(d_words));
+        if (!d_words)
+            return SVT_E_INVAL;
+    }
     c->d.words = d_words;
     c->d.n_words = n_words;
     c->bound = true;
@@ -299,6 +322,30 @@ int svt_fit_events(svt_ctx *c, int mode, void *stream)
     return SVT_OK;
 }
 
+int svt_set_track_output(svt_ctx *c, svt_track *host, size_t cap)
+{
+    if (!c || (host && (!cap || ((uintptr_t)host & 7u))))
+        return SVT_E_INVAL;
+    svt_track *dev = c->dev_tracks;
+    size_t n = c->lim.max_tracks;
+    if (host) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, host) != cudaSuccess || a.type != cudaMemoryTypeHost ||
+            !a.devicePointer) {
+            cudaGetLastError();
+            return SVT_E_INVAL;
+        }
+        dev = static_cast<svt_track *>(a.devicePointer);
+        n = std::min(n, cap);
+    }
+    c->d.tracks = dev;
+    c->d.max_tracks = n;
+    c->host_out = host;
+    c->last_n_out = 0;
+    drop_graph(c);
+    return SVT_OK;
+}
+
 int svt_get_tracks(svt_ctx *c, svt_track *out, size_t cap, size_t *n_out, void *stream)
 {
     if (!c || !n_out)
@@ -312,9 +359,13 @@ int svt_get_tracks(svt_ctx *c, svt_track *out, size_t cap, size_t *n_out, void *
     // The status block and, speculatively, as many tracks as the previous
     // batch had go out together, so a batch like the one before takes one
     // synchronisation; the rest (if any) follows once the count is known.
-    const size_t spec = out ? std::min(cap, (size_t)c->last_n_out) : 0;
+    // With a host output buffer the tracks are there already: `out` equal to
+    // it takes no copy.
+    const bool in_place = c->host_out && out == c->host_out;
+    const svt_track *src = c->host_out ? c->host_out : c->d.tracks;
+    const size_t spec = out && !in_place ? std::min(cap, (size_t)c->last_n_out) : 0;
     if (cudaMemcpyAsync(c->h_ctrl, c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) ||
-        (spec && cudaMemcpyAsync(out, c->d.tracks, spec * sizeof(svt_track), cudaMemcpyDefault, s)) ||
+        (spec && cudaMemcpyAsync(out, src, spec * sizeof(svt_track), cudaMemcpyDefault, s)) ||
         cudaStreamSynchronize(s))
         return SVT_E_CUDA;
     if (c->h_ctrl->flags & FLAG_TIMEOUT)
@@ -327,7 +378,9 @@ int svt_get_tracks(svt_ctx *c, svt_track *out, size_t cap, size_t *n_out, void *
     c->last_n_out = n;
     if (n > cap)
         return SVT_E_CAPACITY;
-    if (n > spec && (!out || cudaMemcpyAsync(out + spec, c->d.tracks + spec, (n - spec) * sizeof(svt_track),
+    if (in_place)
+        return SVT_OK;
+    if (n > spec && (!out || cudaMemcpyAsync(out + spec, src + spec, (n - spec) * sizeof(svt_track),
                                              cudaMemcpyDefault, s) ||
                      cudaStreamSynchronize(s)))
         return out ? SVT_E_CUDA : SVT_E_INVAL;
@@ -396,7 +449,7 @@ static bool launch_ok(const svt_launch &L)
 {
     return (L.block == 0 || persistent_block_ok(L.block)) && L.blocks_per_sm >= 0 && L.small_n4 >= 0 &&
            L.small_n4 <= N4_SMALL_MAX && (L.run_roads == 0 || L.run_roads == 4 || L.run_roads == 8 ||
-                                          L.run_roads == RUN_ROADS_MAX);
+                                          L.run_roads == RUN_ROADS_MAX) && L.max_ctas >= 0;
 }
 
 static void apply_launch(svt_ctx *c, const svt_launch &L)
@@ -405,11 +458,12 @@ static void apply_launch(svt_ctx *c, const svt_launch &L)
     c->blocks_per_sm = L.blocks_per_sm;
     c->d.small_n4 = L.small_n4 ? L.small_n4 : N4_SMALL_MAX;
     c->d.run_roads = L.run_roads ? L.run_roads : WARP_ROADS;
+    c->max_ctas = L.max_ctas;
 }
 
 static svt_launch current_launch(const svt_ctx *c)
 {
-    return svt_launch{c->block, c->blocks_per_sm, c->d.small_n4, c->d.run_roads};
+    return svt_launch{c->block, c->blocks_per_sm, c->d.small_n4, c->d.run_roads, c->max_ctas};
 }
 
 int svt_set_launch(svt_ctx *c, const svt_launch *cfg)
@@ -468,7 +522,7 @@ int svt_autotune(svt_ctx *c, int reps, svt_tune_point *points, uint32_t cap, uin
                 for (int run : kRun) {
                     if (st != SVT_OK)
                         break;
-                    const svt_launch L{block, bps, small, run};
+                    const svt_launch L{block, bps, small, run, old.max_ctas};
                     apply_launch(c, L);
                     int nl = 0;
                     if (enqueue(c, SVT_PERSISTENT, s, &nl) || read_ctrl(c, s)) {   // warm-up

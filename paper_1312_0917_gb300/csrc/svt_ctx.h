@@ -23,6 +23,8 @@ struct svt_ctx {
     int skip_arrival = 0;
     bool hash_dirty = false;         // a batch stopped before clearing its group table
     unsigned long long last_n_out = 0;   // tracks of the last batch read (svt_get_tracks' first copy)
+    svt_track *dev_tracks = nullptr;     // the context's own track buffer (device memory)
+    svt_track *host_out = nullptr;       // host buffer the output stage writes (svt_set_track_output)
     // CUDA graph of one svt_fit_events enqueue
     bool use_graph = false;
     cudaGraphExec_t gexec = nullptr;

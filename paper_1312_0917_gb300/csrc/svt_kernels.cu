@@ -1158,9 +1158,14 @@ __device__ void p2_warp(const Dev &d, unsigned r0, unsigned nr, P2Warp &w, unsig
     __syncwarp();   // the state is refilled for the next event
 }
 
-// P2 over the events: first the events of more than P2W_ROADS roads (listed
-// in P1), a CTA each from a queue; then every warp takes the other events
-// from a second queue, one at a time.  One combination-count atomic per CTA.
+// P2 over the events.  A batch of at most P2_CTA_EVENTS events per CTA: a
+// CTA per event.  A larger one: first the events of more than P2W_ROADS
+// roads (listed in P1), a CTA each from a queue; then every warp takes the
+// other events from a second queue, one at a time (a warp takes longer over
+// an event than a CTA, but eight of them work at once).  One
+// combination-count atomic per CTA.
+constexpr unsigned P2_CTA_EVENTS = 4;
+
 __device__ void p2_phase(const Dev &d, unsigned char *smem)
 {
     if (ldcg(&d.ctrl->err_inv) != 0ull)
@@ -1171,7 +1176,20 @@ __device__ void p2_phase(const Dev &d, unsigned char *smem)
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n_chunks; i += gridDim.x * BLOCK)
         d.rchunk_sum[i] = 0;
     unsigned long long n_comb = 0;
-    // the CTA's first event is its own index, the queue hands out the rest
+    if (n_events <= P2_CTA_EVENTS * gridDim.x) {
+        // few events for the grid: every event a CTA (the shortest time per
+        // event); the CTA's first event is its own index, the queue hands
+        // out the rest
+        for (unsigned e = blockIdx.x; e < n_events; e = grab_after_first(d, Q_P2)) {
+            const unsigned r0 = e == 0 ? 0u : min(ldcg(d.ev_road_end + e - 1), d.max_roads);
+            const unsigned r1 = min(ldcg(d.ev_road_end + e), d.max_roads);
+            p2_event(d, e, r0, min(r1 - min(r0, r1), (unsigned)MAX_ROADS_EV), smem, n_comb);
+        }
+        n_comb = block_sum(n_comb);
+        if (threadIdx.x == 0 && n_comb)
+            atomicAdd(&d.ctrl->n_comb, n_comb);
+        return;
+    }
     const unsigned n_big_ev = min(ldcg(&d.ctrl->n_big_ev), n_events);
     for (unsigned i = blockIdx.x; i < n_big_ev; i = grab_after_first(d, Q_P2)) {
         const unsigned e = min(ldcg(d.ev_big + i), n_events - 1);

@@ -268,9 +268,11 @@ int svt_server_create(svt_server **out, int device, const svt_server_config *con
     *out = nullptr;
     svt_server_config cfg = config ? *config : svt_server_config{};
     if (!cfg.ctas_per_sm) cfg.ctas_per_sm = 1;
-    if (!cfg.max_words) cfg.max_words = 1ull << 21;
-    if (!cfg.max_events) cfg.max_events = 4096;
-    if (!cfg.max_roads) cfg.max_roads = 1u << 17;
+    // by default a slot holds any stream of max_words words (a road has three
+    // words at least), so only a request of more words is ever split
+    if (!cfg.max_words) cfg.max_words = 1ull << 20;
+    if (!cfg.max_events) cfg.max_events = (uint32_t)std::min<uint64_t>(cfg.max_words / 3 + 1, 1u << 30);
+    if (!cfg.max_roads) cfg.max_roads = (uint32_t)std::min<uint64_t>(cfg.max_words / 3 + 1, 1u << 30);
     if (!cfg.max_tracks) cfg.max_tracks = 1ull << 20;
     if (!cfg.hash_slots) cfg.hash_slots = 1u << 20;
     if ((cfg.mode != SVT_PERSISTENT && cfg.mode != SVT_PLAIN) || cfg.n_slots > 64 ||
@@ -315,19 +317,18 @@ int svt_server_create(svt_server **out, int device, const svt_server_config *con
             break;
         sl.ctx->blocks_per_sm = (int)cfg.ctas_per_sm;
         sl.ctx->max_ctas = (int)cfg.max_ctas;
-        void *d_tracks_host = nullptr;   // the device's address of the mapped track buffer
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&sl.copy, cudaStreamNonBlocking) != cudaSuccess ||
             cudaMallocHost(&sl.h_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
             cudaHostAlloc(&sl.h_tracks, sizeof(svt_track) * cfg.max_tracks, cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostGetDevicePointer(&d_tracks_host, sl.h_tracks, 0) != cudaSuccess ||
             cudaMalloc(&sl.d_words, sizeof(uint32_t) * cfg.max_words) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev_ctrl, cudaEventDisableTiming) != cudaSuccess) {
             st = SVT_E_CUDA;
             break;
         }
-        sl.ctx->d.tracks = static_cast<svt_track *>(d_tracks_host);   // the output stage writes host memory
+        if ((st = svt_set_track_output(sl.ctx, sl.h_tracks, cfg.max_tracks)) != SVT_OK)   // written in place
+            break;
         cudaMemGetInfo(&after, &tot);
         if (!n_slots && i == 0) {   // size the slot count from the first slot's footprint
             const size_t per = before > after ? before - after : 1;
@@ -377,10 +378,23 @@ int svt_server_get_config(svt_server *s, svt_server_config *out)
 
 namespace {
 
+// EE and EP words among n (a loop the compiler vectorises).
+void count_ends(const uint32_t *__restrict w, size_t n, size_t &ee, size_t &ep)
+{
+    uint64_t a = 0, b = 0;
+    for (size_t i = 0; i < n; ++i) {
+        a += w[i] >> 31;
+        b += (w[i] >> 30) & 1u;
+    }
+    ee = a;
+    ep = b;
+}
+
 // Admit one request or chunk to the first free slot (waiting for one) and
 // enqueue its copy, kernel and control-block read.  parent != 0: chunk
-// `chunk` of that split request.
-void admit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t parent, unsigned chunk,
+// `chunk` of that split request.  A request (not a chunk) with more events or
+// roads than the slot holds is not admitted: false (the slot is released).
+bool admit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t parent, unsigned chunk,
            Clock::time_point t0, uint64_t *id)
 {
     Slot *sl = nullptr;
@@ -402,10 +416,22 @@ void admit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t parent
         ++s->in_flight;
     }
     s->cv_slot.notify_all();   // wakes an idle progress thread
-    if (id)
-        *id = sl->id;
     if (n_words)
         std::memcpy(sl->h_words, words, n_words * sizeof(uint32_t));
+    // a road has three words at least: only a request of more than three
+    // times the slot's event or road limit in words can exceed them
+    size_t n_ee = 0, n_ep = 0;
+    if (!parent && n_words > 3 * (size_t)std::min(s->cfg.max_events, s->cfg.max_roads))
+        count_ends(sl->h_words, n_words, n_ee, n_ep);
+    if (!parent && (n_ee > s->cfg.max_events || n_ep > s->cfg.max_roads)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        sl->state = SLOT_FREE;
+        --s->in_flight;
+        s->cv_slot.notify_all();
+        return false;
+    }
+    if (id)
+        *id = sl->id;
     int launches = 0;
     bool ok = cudaSetDevice(s->device) == cudaSuccess &&
               (!n_words || cudaMemcpyAsync(sl->d_words, sl->h_words, n_words * sizeof(uint32_t),
@@ -421,12 +447,13 @@ void admit(svt_server *s, const uint32_t *words, size_t n_words, uint64_t parent
         cudaGetLastError();
         std::memset(sl->ctx->h_ctrl, 0, sizeof(Ctrl));
         finish(s, *sl, SVT_E_CUDA, 0);   // the failure is the request's status
-        return;
+        return true;
     }
     sl->ctx->ran = true;
     sl->ctx->last_launches = launches;
     std::lock_guard<std::mutex> lk(s->mu);
     sl->state = SLOT_RUNNING;
+    return true;
 }
 
 // Cut points of a request at event ends (EE words) into chunks of at most
@@ -470,15 +497,15 @@ int svt_server_submit(svt_server *s, const uint32_t *words, size_t n_words, uint
         return SVT_E_INVAL;
     *request_id = 0;
     const Clock::time_point t0 = Clock::now();
+    // the usual case: the request fits a slot (its words are counted as they
+    // are copied to the slot's staging buffer)
+    if (n_words <= s->cfg.max_words && admit(s, words, n_words, 0, 0, t0, request_id))
+        return SVT_OK;
+    // larger than a slot: chunks at event boundaries
     const std::vector<size_t> cuts = split_points(s->cfg, words, n_words);
     if (cuts.size() < 2)
         return SVT_E_CAPACITY;   // one event alone exceeds a slot
     const unsigned n_chunks = (unsigned)(cuts.size() - 1);
-    if (n_chunks == 1) {
-        admit(s, words, n_words, 0, 0, t0, request_id);
-        return SVT_OK;
-    }
-    // larger than a slot: chunks at event boundaries
     uint64_t pid;
     {
         std::lock_guard<std::mutex> lk(s->mu);

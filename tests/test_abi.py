@@ -54,7 +54,7 @@ def test_struct_layouts():
     assert B.ROAD_DTYPE.itemsize == 100 and B.ROAD_DTYPE.fields["coord"][1] == 20
     assert C.sizeof(B.Limits) == 40 and C.sizeof(B.Stats) == 104
     assert C.sizeof(B.ServerConfig) == 56 and C.sizeof(B.ServerResult) == 48
-    assert C.sizeof(B.Launch) == 16 and C.sizeof(B.TunePoint) == 20
+    assert C.sizeof(B.Launch) == 20 and C.sizeof(B.TunePoint) == 24
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):

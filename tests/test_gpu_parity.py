@@ -75,12 +75,15 @@ def test_shared_hits_cross_road(ctx, orc, consts, mode, seed):
     assert_same_tracks(got, oracle_tracks(orc, b.words, consts, cut))
 
 
-@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
-def test_event_sizes_around_the_warp_limit_of_the_flag_stage(ctx, orc, consts, mode):
-    """The cross-road flag stage takes events of at most 64 roads one warp
-    each and larger ones a CTA each: events of 1, 2, 63, 64, 65, 128 and 256
-    roads, interleaved, whose roads copy hits from each other, equal the
-    oracle, and cross-road groups are published."""
+@pytest.mark.parametrize("mode,max_ctas", [(B.PERSISTENT, 0), (B.PERSISTENT, 4), (B.PERSISTENT, 5),
+                                           (B.PLAIN, 0)], ids=["persistent", "persistent-4", "persistent-5",
+                                                               "plain"])
+def test_event_sizes_around_the_warp_limit_of_the_flag_stage(ctx, orc, consts, mode, max_ctas):
+    """The cross-road flag stage takes a batch of few events per CTA a CTA
+    per event; with more events (here: a grid of 4 or 5 CTAs), events of at
+    most 64 roads one warp each and larger ones a CTA each.  Events of 1, 2,
+    63, 64, 65, 128 and 256 roads, interleaved, whose roads copy hits from
+    each other, equal the oracle, and cross-road groups are published."""
     parts = []
     for i, r in enumerate((64, 65, 1, 63, 256, 64, 128, 65, 2, 63)):
         cfg = synth.Config("mix%d" % r, 3, ("fixed", r), ("uniform", 1, 3), shared_hits=0.6)
@@ -89,7 +92,11 @@ def test_event_sizes_around_the_warp_limit_of_the_flag_stage(ctx, orc, consts, m
     rc, chi = orc.chi2_all(words, consts)
     cut = int(np.sort(chi)[(9 * len(chi) + 9) // 10 - 1])
     ctx.load_constants(consts, cut)
-    st, got, stats = run_gpu(ctx, words, mode)
+    ctx.set_launch(max_ctas=max_ctas)
+    try:
+        st, got, stats = run_gpu(ctx, words, mode)
+    finally:
+        ctx.set_launch()
     assert st == B.OK and stats["n_groups"] > 0
     assert_same_tracks(got, oracle_tracks(orc, words, consts, cut))
 
@@ -250,7 +257,7 @@ def launch_grid(ctx):
         for bps in range(1, ctx.get_launch()["blocks_per_sm"] + 1):
             for small in (64, 128, 256):
                 for run in (4, 8, 16):
-                    out.append(dict(block=block, blocks_per_sm=bps, small_n4=small, run_roads=run))
+                    out.append(dict(block=block, blocks_per_sm=bps, small_n4=small, run_roads=run, max_ctas=0))
     ctx.set_launch()
     return out
 
@@ -278,7 +285,7 @@ def test_launch_settings_are_bit_equal(ctx, orc, consts, cuts):
 
 def test_launch_settings_are_checked(ctx):
     for bad in (dict(block=64), dict(block=384), dict(run_roads=3), dict(run_roads=32),
-                dict(small_n4=257), dict(blocks_per_sm=-1)):
+                dict(small_n4=257), dict(blocks_per_sm=-1), dict(max_ctas=-1)):
         with pytest.raises(B.SvtError) as e:
             ctx.set_launch(**bad)
         assert e.value.code == B.E_INVAL
@@ -304,6 +311,56 @@ def test_graph_launch(ctx, consts, cuts):
         assert st3 == B.OK and got3.tobytes() == ref.tobytes()
     finally:
         ctx.use_graph(False)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_words_and_tracks_in_page_locked_host_memory(ctx, orc, consts, cuts, mode):
+    """The kernels read words from page-locked host memory in place and the
+    output stage writes the tracks into a page-locked host buffer: the same
+    tracks as device buffers (and the oracle), with and without a graph; a
+    host buffer too small for the tracks is a capacity error."""
+    import torch
+    b = synth.make_batch("scaled", seed=21, n_events=200)
+    ctx.load_constants(consts, cuts["scaled"])
+    st, ref, _ = run_gpu(ctx, b.words, mode)
+    assert st == B.OK
+    assert_same_tracks(ref, oracle_tracks(orc, b.words, consts, cuts["scaled"]))
+    h_words = torch.from_numpy(b.words.view(np.int32)).pin_memory()
+    h_out = torch.zeros(len(ref) * 40 + 4000, dtype=torch.uint8).pin_memory()
+    cap = h_out.numel() // 40
+    try:
+        ctx.set_track_output(h_out, cap)
+        for graph in (False, True, True):
+            ctx.use_graph(graph and mode == B.PERSISTENT)
+            assert ctx.unpack(h_words, len(b.words)) == B.OK
+            B.check(ctx.fit_events(mode), "svt_fit_events")
+            st, n = ctx.get_tracks(out=h_out, cap=cap)
+            assert st == B.OK and n == len(ref)
+            assert h_out.numpy()[:n * 40].tobytes() == ref.tobytes()
+        ctx.use_graph(False)
+        st, other = ctx.get_tracks()   # a copy out of the host buffer
+        assert st == B.OK and other.tobytes() == ref.tobytes()
+        ctx.set_track_output(h_out, len(ref) - 1)
+        assert ctx.unpack(h_words, len(b.words)) == B.OK
+        B.check(ctx.fit_events(mode), "svt_fit_events")
+        st, n = ctx.get_tracks(out=h_out, cap=cap)
+        assert st == B.E_CAPACITY
+    finally:
+        ctx.use_graph(False)
+        ctx.set_track_output(None)
+    st, got, _ = run_gpu(ctx, b.words, mode)
+    assert st == B.OK and got.tobytes() == ref.tobytes()
+
+
+def test_pageable_host_memory_is_refused(ctx, consts, cuts):
+    b = synth.make_batch("small", seed=1)
+    ctx.load_constants(consts, cuts["small"])
+    words = np.ascontiguousarray(b.words)
+    assert ctx.unpack(words, len(words)) == B.E_INVAL
+    out = np.zeros(100, dtype=B.TRACK_DTYPE)
+    with pytest.raises(B.SvtError) as e:
+        ctx.set_track_output(out, len(out))
+    assert e.value.code == B.E_INVAL
 
 
 def test_capacity_errors(consts, cuts):
