@@ -72,6 +72,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparisons")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the packet-size sweep")
+    ap.add_argument("--launch", default="", help="block,blocks_per_sm,small_n4,run_roads of the headline's "
+                    "persistent kernel instead of the autotuner's choice (for profiler runs)")
     ap.add_argument("--no-subs", action="store_true", help="skip the scaled and uneven sub-workloads")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch settings; for profiler runs)")
@@ -514,7 +516,11 @@ def gpu_arm(args):
 
     # correctness of the timed configuration is checked by the tests (every
     # workload against the oracle); here the track count is recorded
-    tuned = None if args.no_tune else tune(ctx, B, d_words, n_words, stream)
+    tuned = None if args.no_tune or args.launch else tune(ctx, B, d_words, n_words, stream)
+    if args.launch:
+        blk, bps, small, run = (int(x) for x in args.launch.split(","))
+        ctx.set_launch(block=blk, blocks_per_sm=bps, small_n4=small, run_roads=run)
+        tuned = dict(ctx.get_launch(), note="set by --launch, not tuned")
     ctx.use_graph(True)
     clocks = ClockSampler(local).__enter__()
     atexit.register(clocks.__exit__)   # the sampler stops on an early exit too

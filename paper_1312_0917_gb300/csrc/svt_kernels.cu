@@ -1915,21 +1915,29 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 //               warp reduction, only where a candidate or a group needs it
 //   T_ac, T_bc  the lane's minimum over w at each z, folded over the lanes
 //   T_ae, T_be  the lane's minimum over z for each w, folded at the end
-// (the lane minima are folded by shared-memory atomics; folding them through
-// scratch rows or warp shuffles measured slower)
+// The lane minima are folded by 32-bit shared-memory atomics without a
+// return value, each pass into tables of its own: the high words first,
+// then, after the warp has synchronised, the low words of the lanes whose
+// high word is the minimum.  That is the exact minimum of the 64-bit keys
+// over the pass (every lane of the pass takes part in the same steps); the
+// survivor check takes the smaller of the two passes' entries.  (64-bit
+// atomic minima, and folds through scratch rows or warp shuffles, measured
+// slower.)
 // A fit survives the road-local warrior iff its key is the minimum of all
 // six (see the flat path); it is then the minimum of its pair (x, y), so a
 // pair has at most one candidate and a road at most 64 survivors.
 // ---------------------------------------------------------------------------
 
 enum { T_AB = 0, T_CE, T_AC, T_BC, T_AE, T_BE, N_TAB };
-// table row stride: rows 9 entries (72 bytes) apart put the 64-bit entries
-// [u][v] of different u in different banks
+// table row stride: rows 9 entries apart put the entries [u][v] of
+// different u in different banks
 constexpr unsigned TS = 9;
 
 struct P3Box {
-    unsigned long long T[N_TAB][8 * TS];   // pair tables, [u * TS + v] (u: the first role's hit); T_ce
+    unsigned long long T[2][8 * TS];   // T_ab, T_ce: [u * TS + v] (u: the first role's hit); T_ce
                                        // only where needed (box_tce)
+    unsigned H[2][4][8 * TS];          // T_ac, T_bc, T_ae, T_be of pass 0 and pass 1: high words
+    unsigned L[2][4][8 * TS];          // and low words (of the keys with the minimum high word)
     int4 A[4][8];                      // slot j, canonical hit k: chi-square partial sums (x, y,
                                        // z) and comb part (w); slot 0 also carries curvature, phi,
                                        // 4096 k and the road bits of the key
@@ -1943,6 +1951,30 @@ static_assert(offsetof(P3Box, A) % 16 == 0 && offsetof(P3Box, co) % 16 == 0, "16
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b)
 {
     return b < a ? b : a;
+}
+
+// entry idx of pair table tab: T_ab and T_ce as stored, the others the
+// smaller of the two passes' (high, low) entries
+__device__ __forceinline__ unsigned long long box_get(const P3Box &B, unsigned tab, unsigned idx)
+{
+    if (tab < 2)
+        return B.T[tab][idx];
+    const unsigned t = tab - 2;
+    return umin64(((unsigned long long)B.H[0][t][idx] << 32) | B.L[0][t][idx],
+                  ((unsigned long long)B.H[1][t][idx] << 32) | B.L[1][t][idx]);
+}
+
+// Fold v into entry idx of table t of pass q, stage 1 (high word); stage 2
+// (low word) runs after the warp has synchronised: only lanes whose high
+// word is then the minimum take part.
+__device__ __forceinline__ void fold_hi(P3Box &B, unsigned q, unsigned t, unsigned idx, unsigned long long v)
+{
+    atomicMin(&B.H[q][t][idx], (unsigned)(v >> 32));
+}
+__device__ __forceinline__ void fold_lo(P3Box &B, unsigned q, unsigned t, unsigned idx, unsigned long long v)
+{
+    if ((unsigned)(v >> 32) == B.H[q][t][idx])
+        atomicMin(&B.L[q][t][idx], (unsigned)v);
 }
 
 // hits of layer l of a road record (clamped to the format limit)
@@ -2038,19 +2070,35 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
             rw[w] = umin64(rw[w], key);
         }
         qab = umin64(qab, rz);
+        const unsigned q = p & 1u;
         if (act) {
-            atomicMin(&B.T[T_AC][x * TS + z], rz);
-            atomicMin(&B.T[T_BC][y * TS + z], rz);
+            fold_hi(B, q, T_AC - 2, x * TS + z, rz);
+            fold_hi(B, q, T_BC - 2, y * TS + z, rz);
+        }
+        __syncwarp();
+        if (act) {
+            fold_lo(B, q, T_AC - 2, x * TS + z, rz);
+            fold_lo(B, q, T_BC - 2, y * TS + z, rz);
         }
     }
     if (act)
         B.T[T_AB][x * TS + y] = qab;
+    const unsigned q = p & 1u;
     if (act) {
 #pragma unroll
         for (unsigned w = 0; w < ME; ++w)
             if (w < me) {
-                atomicMin(&B.T[T_AE][x * TS + w], rw[w]);
-                atomicMin(&B.T[T_BE][y * TS + w], rw[w]);
+                fold_hi(B, q, T_AE - 2, x * TS + w, rw[w]);
+                fold_hi(B, q, T_BE - 2, y * TS + w, rw[w]);
+            }
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+        for (unsigned w = 0; w < ME; ++w)
+            if (w < me) {
+                fold_lo(B, q, T_AE - 2, x * TS + w, rw[w]);
+                fold_lo(B, q, T_BE - 2, y * TS + w, rw[w]);
             }
     }
     __syncwarp();
@@ -2116,8 +2164,10 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
     __syncwarp();   // the region's previous user is done
     if (lane < N_LAYERS)   // 80 bytes of coordinates, five 16-byte words
         reinterpret_cast<uint4 *>(B.co)[lane] = ldcg(reinterpret_cast<const uint4 *>(d.coords + (size_t)g * 40) + lane);
-    for (unsigned i = lane; i < N_TAB * 8 * TS; i += 32)
+    for (unsigned i = lane; i < 2 * 8 * TS; i += 32)
         (&B.T[0][0])[i] = NO_KEY;
+    for (unsigned i = lane; i < 2 * 2 * 4 * 8 * TS; i += 32)   // H and L
+        (&B.H[0][0][0])[i] = 0xFFFFFFFFu;
     __syncwarp();
 
     // lane 8 j + h: raw hit h of fitted slot j.  Canonical hits, their ranks
@@ -2253,8 +2303,8 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                     de = l == Le ? dl : de;
                 }
                 const unsigned z = B.rank[sh.rc][dc], w = B.rank[sh.re][de];
-                sv[p] = B.T[T_AC][x * TS + z] == key && B.T[T_BC][y * TS + z] == key &&
-                        B.T[T_AE][x * TS + w] == key && B.T[T_BE][y * TS + w] == key;
+                sv[p] = box_get(B, T_AC, x * TS + z) == key && box_get(B, T_BC, y * TS + z) == key &&
+                        box_get(B, T_AE, x * TS + w) == key && box_get(B, T_BE, y * TS + w) == key;
                 sk[p] = key;
                 zw[p] = z * 8 + w;
             }
@@ -2397,7 +2447,7 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                 }
                 unsigned idx;
                 const unsigned tab = box_tab(sh, sa, B.rank[sa][da], sb, B.rank[sb][db], idx);
-                mn = B.T[tab][idx];
+                mn = box_get(B, tab, idx);
                 if (mn != NO_KEY)
                     mn += (unsigned long long)de * Se;
             }
