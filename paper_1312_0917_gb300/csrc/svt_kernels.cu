@@ -2022,6 +2022,15 @@ __device__ __forceinline__ unsigned long long box_key2(const int4 &s, unsigned c
     return ok ? ((unsigned long long)hi << 32) | lo : NO_KEY;
 }
 
+// The key of a fit without the cut: chi2 << 23 | cw (the cut is key < kb).
+__device__ __forceinline__ unsigned long long box_key_raw(const int4 &s, unsigned cw)
+{
+    const long long chi2 = sq(s.x >> 12) + sq(s.y >> 12) + sq(s.z >> 12);
+    const unsigned hi = (unsigned)((unsigned long long)chi2 >> 9);
+    const unsigned lo = ((unsigned)chi2 << 23) + cw;
+    return ((unsigned long long)hi << 32) | lo;
+}
+
 // One pass over the pairs (x, y) of slots a and b: lane t = 32 p + lane.
 // The inner loop over the hits of slot e has ME (4 or 8, at least me) steps,
 // unrolled and predicated, so a step has no branch.  DUP: the road has
@@ -2038,6 +2047,10 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
     const int4 pab = add4(B.A[sh.ra][x], B.A[sh.rb][y]);
     const unsigned wab = DUP ? (unsigned)B.mult[sh.ra][x] * B.mult[sh.rb][y] : 1u;
     const long long cut = d.cut;
+    // full passes compare raw keys with kb: chi2 <= cut iff key < kb; a
+    // minimum of kb or more means no passing fit (NO_KEY when stored)
+    const unsigned long long kb = cut < 0 ? 0ull : (unsigned long long)(min(cut, 1ll << 40) + 1) << 23;
+    const auto cut_min = [kb](unsigned long long v) { return FULLW && v >= kb ? NO_KEY : v; };
     const int4 *Ae = B.A[sh.re];
     bool live[ME];
 #pragma unroll
@@ -2059,17 +2072,23 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
                 key = live[w] ? ldcg(d.fit_key + sh.cb + (unsigned)(pz.w + aw.w)) : NO_KEY;
             } else {
                 const int4 s = make_int4(pz.x + aw.x, pz.y + aw.y, pz.z + aw.z, 0);
-                bool ok;
-                key = box_key2(s, (unsigned)pz.w + (unsigned)aw.w, cut, live[w], ok);
-                if (DUP)
-                    np += ok ? wz * B.mult[sh.re][w] : 0u;
-                else
-                    np += ok;
+                if (FULLW) {
+                    key = box_key_raw(s, (unsigned)pz.w + (unsigned)aw.w);
+                    np += key < kb;
+                } else {
+                    bool ok;
+                    key = box_key2(s, (unsigned)pz.w + (unsigned)aw.w, cut, live[w], ok);
+                    if (DUP)
+                        np += ok ? wz * B.mult[sh.re][w] : 0u;
+                    else
+                        np += ok;
+                }
             }
             rz = umin64(rz, key);
             rw[w] = umin64(rw[w], key);
         }
         qab = umin64(qab, rz);
+        rz = cut_min(rz);
         const unsigned q = p & 1u;
         if (act) {
             fold_hi(B, q, T_AC - 2, x * TS + z, rz);
@@ -2082,7 +2101,10 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
         }
     }
     if (act)
-        B.T[T_AB][x * TS + y] = qab;
+        B.T[T_AB][x * TS + y] = cut_min(qab);
+#pragma unroll
+    for (unsigned w = 0; w < ME; ++w)
+        rw[w] = cut_min(rw[w]);
     const unsigned q = p & 1u;
     if (act) {
 #pragma unroll
