@@ -340,8 +340,9 @@ def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=4, seed=0):
 # (kernels and their header) they were taken on: the bench line reports a
 # figure only while the sources are unchanged.
 NCU_TRAFFIC = {
-    "stress": {"kernels_sha256": "804da36d3a865235ba716effa494abb2e315d3bb934243f68b0ff5e79c44b8ee", "bytes": 5260544},   # 5.260 MB read + 256 B written
-    "scaled": {"kernels_sha256": "804da36d3a865235ba716effa494abb2e315d3bb934243f68b0ff5e79c44b8ee", "bytes": 12684288},  # 12.621 MB read + 63.7 KB written
+    "stress": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 5259520},    # 5.259 MB read + 512 B written
+    "scaled": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 12654848},   # 12.618 MB read + 36.4 KB written
+    "uneven": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 20110592},   # 17.692 MB read + 2.419 MB written
 }
 
 
@@ -417,6 +418,7 @@ def sub_workload(B, torch, synth, name, consts, local, args):
                       "gpu_launches_per_batch": ctx.last_launch_count(),
                       "tracks": stats["n_tracks"]}
         if mode == B.PERSISTENT:
+            out[label]["dram_bytes_per_batch"] = measured_traffic(name)
             out[label]["phase_us"] = dict(zip(
                 ["word_scan", "road_decode", "cross_road_flags", "fit_cut_local_warrior",
                  "cross_road_warrior", "output"], [round(x / 1e3, 1) for x in stats["phase_ns"]]))
