@@ -31,6 +31,9 @@ roads x 8 hits on each of 5 layers (838,860,800 combinations).
   packet_sweep  end-to-end latency of one batch from 600 kB of words up,
          with pageable, page-locked, and in-place (kernels read and write
          page-locked host memory) buffers, and the transfer share of each.
+  loopback  a transmitter process sends packets over loopback TCP to a
+         receiver process that runs the chain; round trip timed at the
+         transmitter (the paper's latency set-up, without a NIC).
   cpu_baseline  the oracle (test infrastructure) on the machine's host cores:
          its event-parallel driver on a bounded sample, per-stage times.
   --impl reference  the oracle as it stands, timed on the host cores.
@@ -489,6 +492,127 @@ def packet_sweep(B, torch, synth, consts, local, sizes_kb=(600, 1200, 2400, 4800
             "latency": "host wall time of one batch: words in, kernel, tracks out", "sizes": rows}
 
 
+def _recv_exact(sock, view):
+    """Fill the writable memoryview `view` from the socket."""
+    got = 0
+    while got < len(view):
+        n = sock.recv_into(view[got:])
+        if n == 0:
+            raise ConnectionError("peer closed")
+        got += n
+
+
+def loopback_receiver(pipe, device, consts, cut, max_words):
+    """The receiving process of the loopback loop (a separate process, as in
+    Sec. III's transmitter/receiver set-up, Fig. 1): accepts one TCP
+    connection on 127.0.0.1, then for every packet (8-byte word count, then
+    the words) copies the words to the device, runs the chain and sends back
+    a 24-byte header (status, track count, its own processing time in ns) and
+    the tracks.  A word count of 0 ends it."""
+    import socket
+    import struct
+    import torch
+    from paper_1312_0917_gb300 import binding as B
+    torch.cuda.set_device(device)
+    max_tracks = max_words
+    ctx = B.Context(device, max_words=max_words, max_events=max_words // 3 + 1, max_roads=max_words // 3 + 1,
+                    max_tracks=max_tracks, max_combinations=1 << 10)
+    ctx.load_constants(consts, cut)
+    stream = torch.cuda.Stream()
+    h_words = torch.empty(max_words, dtype=torch.int32).pin_memory()
+    d_words = torch.empty(max_words, dtype=torch.int32, device="cuda")
+    h_out = torch.empty(max_tracks * 40, dtype=torch.uint8).pin_memory()
+    wview = memoryview(h_words.numpy()).cast("B")
+    oview = memoryview(h_out.numpy())
+    srv = socket.socket(socket.AF_INET, socket.SOCK_STREAM)
+    srv.bind(("127.0.0.1", 0))
+    srv.listen(1)
+    pipe.send(srv.getsockname()[1])
+    sock, _ = srv.accept()
+    sock.setsockopt(socket.IPPROTO_TCP, socket.TCP_NODELAY, 1)
+    hdr = bytearray(8)
+    try:
+        while True:
+            _recv_exact(sock, memoryview(hdr))
+            (n_words,) = struct.unpack("<Q", hdr)
+            if n_words == 0:
+                break
+            _recv_exact(sock, wview[:4 * n_words])
+            t0 = time.perf_counter_ns()
+            with torch.cuda.stream(stream):
+                d_words[:n_words].copy_(h_words[:n_words], non_blocking=True)
+            B.check(ctx.unpack(d_words, n_words, stream), "svt_unpack")
+            B.check(ctx.fit_events(B.PERSISTENT, stream), "svt_fit_events")
+            st, n = ctx.get_tracks(out=h_out, cap=max_tracks, stream=stream)
+            dt = time.perf_counter_ns() - t0
+            sock.sendall(struct.pack("<qqq", st, n if st == B.OK else 0, dt))
+            if st == B.OK and n:
+                sock.sendall(oview[:40 * n])
+    finally:
+        sock.close()
+        srv.close()
+        ctx.close()
+
+
+def loopback_loop(synth, consts, local, sizes_kb=(600, 2400, 9600), reps=20):
+    """NEXT-3 of the hot-path plan: a transmitter (this process) sends packets
+    of words over host loopback TCP to a receiver process that runs the chain
+    on the GPU and sends the tracks back; the round trip is timed at the
+    transmitter (Sec. III, Fig. 1).  Reports per packet size the round trip
+    (p50 / p99), the receiver's own time (H2D, kernel, D2H), and the share of
+    the round trip spent outside it (socket transfers both ways)."""
+    import multiprocessing as mp
+    import socket
+    import struct
+    cut = load_cut("scaled")
+    per_event = 4 * (len(synth.make_batch("scaled", seed=0, n_events=64).words) / 64)
+    sizes = [(kb, max(1, int(round(kb * 1000 / per_event)))) for kb in sizes_kb]
+    max_words = int(max(e for _, e in sizes) * per_event / 4) + 4096
+    ctx_mp = mp.get_context("spawn")
+    parent, child = ctx_mp.Pipe()
+    proc = ctx_mp.Process(target=loopback_receiver, args=(child, local, consts, cut, max_words), daemon=True)
+    proc.start()
+    rows = []
+    try:
+        if not parent.poll(300):
+            raise RuntimeError("the loopback receiver did not start")
+        port = parent.recv()
+        sock = socket.create_connection(("127.0.0.1", port))
+        sock.setsockopt(socket.IPPROTO_TCP, socket.TCP_NODELAY, 1)
+        hdr = bytearray(24)
+        for i, (kb, n_ev) in enumerate(sizes):
+            words = synth.make_batch("scaled", seed=700 + i, n_events=n_ev).words
+            out = bytearray(40 * max_words)
+            rtt, proc_ns, n_tr = [], [], 0
+            for r in range(3 + reps):
+                t0 = time.perf_counter()
+                sock.sendall(struct.pack("<Q", len(words)))
+                sock.sendall(memoryview(words).cast("B"))
+                _recv_exact(sock, memoryview(hdr))
+                st, n_tr, dt = struct.unpack("<qqq", hdr)
+                if st != 0:
+                    raise RuntimeError("receiver status %d" % st)
+                _recv_exact(sock, memoryview(out)[:40 * n_tr])
+                t1 = time.perf_counter()
+                if r >= 3:
+                    rtt.append(t1 - t0)
+                    proc_ns.append(dt)
+            p50 = 1e6 * float(np.percentile(rtt, 50))
+            pr = float(np.percentile(proc_ns, 50)) / 1e3
+            rows.append({"kB": round(4 * len(words) / 1e3, 1), "events": n_ev, "tracks": n_tr,
+                         "round_trip_p50_us": round(p50, 1),
+                         "round_trip_p99_us": round(1e6 * float(np.percentile(rtt, 99)), 1),
+                         "receiver_p50_us": round(pr, 1), "socket_share": round(max(0.0, 1 - pr / p50), 3)})
+        sock.sendall(struct.pack("<Q", 0))
+        sock.close()
+    finally:
+        proc.join(timeout=30)
+        if proc.is_alive():
+            proc.terminate()
+    return {"transport": "TCP over 127.0.0.1, one connection, TCP_NODELAY", "reps": reps,
+            "receiver": "separate process: pinned H2D, persistent kernel, D2H of the tracks", "sizes": rows}
+
+
 def gpu_arm(args):
     import torch
     from paper_1312_0917_gb300 import binding as B, synth, build as nvbuild
@@ -626,6 +750,7 @@ def gpu_arm(args):
                 line[name] = sub_workload(B, torch, synth, name, consts, local, args)
     if not args.no_sweep and world == 1:
         line["packet_sweep"] = packet_sweep(B, torch, synth, consts, local)
+        line["loopback"] = loopback_loop(synth, consts, local)
     if not args.no_serve and world == 1:
         line["serving"] = run_serving(B, synth, consts, load_cut("serving"),
                                       (1e4, 3e4, 1e5, 3e5, 1e6), args.serve_requests)
