@@ -461,8 +461,8 @@ def packet_sweep(B, torch, synth, consts, local, sizes_kb=(600, 1200, 2400, 4800
         cap = max(1, n_tr)
         row = {"kB": round(4 * n_words / 1e3, 1), "events": n_ev, "tracks": n_tr,
                "device_p50_us": round(1e3 * float(np.percentile(dev, 50)), 1)}
-        for kind in ("pageable", "pinned", "in_place"):
-            if kind == "in_place":
+        for kind in ("pageable", "pinned", "in_place", "pinned_in_tracks_out_in_place"):
+            if kind in ("in_place", "pinned_in_tracks_out_in_place"):
                 ctx.set_track_output(out_map, cap)
             lat = []
             for r in range(3 + reps):
@@ -476,12 +476,12 @@ def packet_sweep(B, torch, synth, consts, local, sizes_kb=(600, 1200, 2400, 4800
                     src = d_words
                 B.check(ctx.unpack(src, n_words, stream), "svt_unpack")
                 B.check(ctx.fit_events(B.PERSISTENT, stream), "svt_fit_events")
-                out = {"pageable": out_page, "pinned": out_pin, "in_place": out_map}[kind]
+                out = out_page if kind == "pageable" else out_pin if kind == "pinned" else out_map
                 st, n = ctx.get_tracks(out=out, cap=cap, stream=stream)
                 B.check(st, "svt_get_tracks")
                 if r >= 3:
                     lat.append(time.perf_counter() - t0)
-            if kind == "in_place":
+            if kind in ("in_place", "pinned_in_tracks_out_in_place"):
                 ctx.set_track_output(None)
             p50 = 1e6 * float(np.percentile(lat, 50))
             row[kind] = {"p50_us": round(p50, 1), "p99_us": round(1e6 * float(np.percentile(lat, 99)), 1),
