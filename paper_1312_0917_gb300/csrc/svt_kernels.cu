@@ -750,7 +750,7 @@ __device__ bool scan_decode(const Dev &d, unsigned char *smem)
 }
 
 // ---------------------------------------------------------------------------
-// P2: the cross-road flags of each event (one CTA per event).  A track can
+// P2: the cross-road flags of each event (a CTA or a warp per event).  A track can
 // only be dropped by a track of another road that shares hits with it on
 // three layers, so only road pairs with a coordinate in common on >= 3
 // layers matter.  The coordinates of the event that appear in two or more
@@ -760,9 +760,10 @@ __device__ bool scan_decode(const Dev &d, unsigned char *smem)
 // cross-road candidate; its marked hits are the ones it publishes and looks
 // up.  The road records get the candidate bit and their fit path.
 //
-// Events of at most P2W_ROADS roads take one warp each instead (p2_warp),
-// with the same bitmaps, 32-bit signatures, and a lane per road that tests
-// its road against the others and marks its own hits.
+// In a batch of many events, events of at most P2W_ROADS roads take one warp
+// each instead (p2_warp), with the same bitmaps, 32-bit signatures, and a
+// lane per road that tests its road against the others and marks its own
+// hits (p2_phase chooses).
 // ---------------------------------------------------------------------------
 
 constexpr unsigned P2_PAIRS = 1024;   // road pairs queued for the exact test (more: tested in place)
