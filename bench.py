@@ -343,9 +343,9 @@ def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=4, seed=0):
 # (kernels and their header) they were taken on: the bench line reports a
 # figure only while the sources are unchanged.
 NCU_TRAFFIC = {
-    "stress": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 5259520},    # 5.259 MB read + 512 B written
-    "scaled": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 12654848},   # 12.618 MB read + 36.4 KB written
-    "uneven": {"kernels_sha256": "8b72a8ee28f1c7f00a1c8a9b7cc9279170bc1f19fa8ef58b64abcd58b5dcc045", "bytes": 20110592},   # 17.692 MB read + 2.419 MB written
+    "stress": {"kernels_sha256": "a31241f17f61353376c8896dff679e4fc3be3e6a6c78695c78061f9d12fa1037", "bytes": 5259520},    # 5.259 MB read + 512 B written
+    "scaled": {"kernels_sha256": "a31241f17f61353376c8896dff679e4fc3be3e6a6c78695c78061f9d12fa1037", "bytes": 12654848},   # 12.618 MB read + 36.4 KB written
+    "uneven": {"kernels_sha256": "a31241f17f61353376c8896dff679e4fc3be3e6a6c78695c78061f9d12fa1037", "bytes": 20110592},   # 17.692 MB read + 2.419 MB written
 }
 
 
