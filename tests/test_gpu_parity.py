@@ -170,6 +170,46 @@ def test_stress_every_event_against_the_oracle(orc, consts, cuts, mode):
     assert len(np.unique(got["event"])) == 200
 
 
+_FULL = {}
+
+
+@pytest.mark.parametrize("name", ["stress", "scaled", "uneven"])
+def test_every_batch_in_the_benchmarks_launch_configuration(orc, consts, cuts, name):
+    """The benchmark's timed configuration of each batch: autotuned on the
+    batch, then replayed from a CUDA graph; every track of every event
+    against the oracle.  On the stress batch also each block size's build at
+    its occupancy maximum."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    if name == "stress":
+        b, want = stress_oracle(orc, consts, cuts)
+    else:
+        if name not in _FULL:
+            b = synth.make_batch(name, seed=0)
+            _FULL[name] = (b, oracle_parallel(b, consts, cuts[name]))
+        b, want = _FULL[name]
+    c = B.Context(0, max_combinations=1 << 10)
+    try:
+        c.load_constants(consts, cuts[name])
+        d = torch_words(b.words)
+        assert c.unpack(d, len(b.words)) == B.OK
+        c.autotune(reps=1)
+        c.use_graph(True)
+        for _ in range(2):
+            st, got, _ = run_gpu(c, b.words, B.PERSISTENT, d_words=d)
+            assert st == B.OK
+            assert_same_tracks(got, want)
+        c.use_graph(False)
+        if name == "stress":
+            for block in (128, 256, 512):
+                c.set_launch(block=block)
+                st, other, _ = run_gpu(c, b.words, B.PERSISTENT, d_words=d)
+                assert st == B.OK and other.tobytes() == got.tobytes(), block
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 def test_unpack_roads(ctx, orc, consts, cuts, mode):
     b = synth.make_batch("uneven", seed=4, n_events=400)
