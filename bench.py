@@ -361,6 +361,31 @@ def measured_traffic(workload: str):
     return None
 
 
+# The plain pipeline stores every combination's key (8 bytes) and track
+# parameters (12 bytes) and its warrior reads the keys back: 28 bytes of HBM
+# traffic per combination that the persistent kernel never makes.
+PLAIN_BYTES_PER_COMB = 28
+
+
+def measured_hbm_gbs() -> float:
+    """The measured copy bandwidth of the GB300s (MEASURED_PEAKS.json,
+    written by the benchmark's driver), else the earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+def plain_hbm(n_fits: int, ms: float) -> dict:
+    """HBM roofline of the plain pipeline (bound by its per-combination stores)."""
+    gbs = PLAIN_BYTES_PER_COMB * n_fits / (ms / 1e3) / 1e9
+    peak = measured_hbm_gbs()
+    return {"bytes_per_batch": PLAIN_BYTES_PER_COMB * n_fits, "achieved_gbs": round(gbs, 1),
+            "peak_gbs": peak, "frac": round(gbs / peak, 3),
+            "note": "28 B per combination: key and track parameters stored, keys read back"}
+
+
 def max_over_ranks(x: float, world: int) -> float:
     """The largest x over all ranks (the job's time is its slowest rank's)."""
     if world <= 1:
@@ -422,6 +447,8 @@ def sub_workload(B, torch, synth, name, consts, local, args):
                       "tracks": stats["n_tracks"]}
         if mode == B.PERSISTENT:
             out[label]["dram_bytes_per_batch"] = measured_traffic(name)
+        else:
+            out[label]["hbm_roofline"] = plain_hbm(n_fits, statistics.mean(t))
             out[label]["phase_us"] = dict(zip(
                 ["word_scan", "road_decode", "cross_road_flags", "fit_cut_local_warrior",
                  "cross_road_warrior", "output"], [round(x / 1e3, 1) for x in stats["phase_ns"]]))
@@ -672,7 +699,8 @@ def gpu_arm(args):
         pt = run_device_steps(ctx, B, torch, d_words, n_words, B.PLAIN, max(5, args.steps // 3), 3, stream)
         plain = {"ms_per_step": statistics.mean(pt), "fits_per_s": n_fits / (statistics.mean(pt) / 1e3),
                  "p50_us": 1e3 * float(np.percentile(pt, 50)), "p99_us": 1e3 * float(np.percentile(pt, 99)),
-                 "gpu_launches_per_step": ctx.last_launch_count()}
+                 "gpu_launches_per_step": ctx.last_launch_count(),
+                 "hbm_roofline": plain_hbm(n_fits, statistics.mean(pt))}
         ctx.use_graph(True)
 
     # end to end through the public API: the latency of one batch at a time,
