@@ -447,11 +447,11 @@ def sub_workload(B, torch, synth, name, consts, local, args):
                       "tracks": stats["n_tracks"]}
         if mode == B.PERSISTENT:
             out[label]["dram_bytes_per_batch"] = measured_traffic(name)
-        else:
-            out[label]["hbm_roofline"] = plain_hbm(n_fits, statistics.mean(t))
             out[label]["phase_us"] = dict(zip(
                 ["word_scan", "road_decode", "cross_road_flags", "fit_cut_local_warrior",
                  "cross_road_warrior", "output"], [round(x / 1e3, 1) for x in stats["phase_ns"]]))
+        else:
+            out[label]["hbm_roofline"] = plain_hbm(n_fits, statistics.mean(t))
     ctx.close()
     return out
 
