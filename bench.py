@@ -274,14 +274,14 @@ def cpu_baseline(batch, consts, cut, target_s=12.0):
                         "note": "unpack serial; the others summed over threads"}}
 
 
-def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=4, seed=0):
+def run_serving(B, synth, consts, cut, rates, n_requests, n_slots=8, seed=0, **server_cfg):
     """Serving loop (svt_server) under Poisson arrivals of requests whose
     event counts are log-uniform in [1, 512) (scaled-shaped events), at each
     offered event rate.  Latency of a request: from its scheduled arrival to
     its tracks in host memory (admission wait, copies and kernel included)."""
     sizes = synth.request_sizes(seed, 64)
     pool = [synth.make_batch("scaled", seed=500 + i, n_events=int(k)).words for i, k in enumerate(sizes)]
-    srv = B.Server(consts, cut, n_slots=n_slots)
+    srv = B.Server(consts, cut, n_slots=n_slots, **server_cfg)
     try:
         for w in pool[:16]:                      # warm-up
             srv.submit(w)
