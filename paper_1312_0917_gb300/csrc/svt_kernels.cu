@@ -2057,10 +2057,7 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
 #pragma unroll
     for (unsigned w = 0; w < ME; ++w)
         live[w] = FULLW || (act && w < me);   // full passes of 8-hit slots e: every lane, every w
-    unsigned long long qab = NO_KEY, rw[ME];
-#pragma unroll
-    for (unsigned w = 0; w < ME; ++w)
-        rw[w] = NO_KEY;
+    unsigned long long qab = NO_KEY;
     for (unsigned z = 0; z < mc; ++z) {
         const int4 pz = add4(pab, B.A[sh.rc][z]);
         const unsigned wz = DUP ? wab * B.mult[sh.rc][z] : 1u;
@@ -2086,7 +2083,6 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
                 }
             }
             rz = umin64(rz, key);
-            rw[w] = umin64(rw[w], key);
         }
         qab = umin64(qab, rz);
         rz = cut_min(rz);
@@ -2103,42 +2099,27 @@ __device__ void box_pass(const Dev &d, P3Box &B, const BoxShape &sh, unsigned p,
     }
     if (act)
         B.T[T_AB][x * TS + y] = cut_min(qab);
-#pragma unroll
-    for (unsigned w = 0; w < ME; ++w)
-        rw[w] = cut_min(rw[w]);
-    const unsigned q = p & 1u;
-    if (act) {
-#pragma unroll
-        for (unsigned w = 0; w < ME; ++w)
-            if (w < me) {
-                fold_hi(B, q, T_AE - 2, x * TS + w, rw[w]);
-                fold_hi(B, q, T_BE - 2, y * TS + w, rw[w]);
-            }
-    }
-    __syncwarp();
-    if (act) {
-#pragma unroll
-        for (unsigned w = 0; w < ME; ++w)
-            if (w < me) {
-                fold_lo(B, q, T_AE - 2, x * TS + w, rw[w]);
-                fold_lo(B, q, T_BE - 2, y * TS + w, rw[w]);
-            }
-    }
     __syncwarp();
 }
 
-// T_ce[z][w]: the minimum key over every pair (x, y) at hits z, w of slots
-// c and e (every lane calls it with the same z, w; the result is the same in
-// every lane).
+// The minimum key over the fits with canonical hit kp of slot sp and kq of
+// slot sq (sp != sq), taken on demand by the warp: lanes over the canonical
+// hits of the other two slots (every lane calls it with the same arguments;
+// the result is the same in every lane).  Gives T_ae, T_be and T_ce, which
+// the passes do not fold.
 template <bool PLAIN>
-__device__ unsigned long long box_tce(const Dev &d, const P3Box &B, const BoxShape &sh, unsigned z, unsigned w)
+__device__ unsigned long long box_min2(const Dev &d, const P3Box &B, const BoxShape &sh, unsigned sp, unsigned kp,
+                                       unsigned sq, unsigned kq)
 {
     const unsigned lane = lane_id();
-    const int4 pzw = add4(B.A[sh.rc][z], B.A[sh.re][w]);
+    const unsigned rest = 0xFu & ~(1u << sp) & ~(1u << sq);
+    const unsigned su = __ffs(rest) - 1, sv = 31 - __clz(rest);
+    const unsigned mu = sh.m(su), mv = sh.m(sv);
+    const int4 pf = add4(B.A[sp][kp], B.A[sq][kq]);
     unsigned long long mn = NO_KEY;
-    for (unsigned t = lane; t < sh.ma * sh.mb; t += 32) {
-        const unsigned y = divm(t, c_magic[sh.ma]), x = t - y * sh.ma;
-        const int4 s = add4(pzw, add4(B.A[sh.ra][x], B.A[sh.rb][y]));
+    for (unsigned t = lane; t < mu * mv; t += 32) {
+        const unsigned iv = divm(t, c_magic[mu]), iu = t - iv * mu;
+        const int4 s = add4(pf, add4(B.A[su][iu], B.A[sv][iv]));
         unsigned long long key;
         if (PLAIN) {
             key = ldcg(d.fit_key + sh.cb + (unsigned)s.w);
@@ -2152,6 +2133,14 @@ __device__ unsigned long long box_tce(const Dev &d, const P3Box &B, const BoxSha
     const unsigned mh = __reduce_min_sync(FULL_MASK, hi);
     const unsigned ml = __reduce_min_sync(FULL_MASK, hi == mh ? (unsigned)mn : 0xFFFFFFFFu);
     return ((unsigned long long)mh << 32) | ml;
+}
+
+// T_ce[z][w]: the minimum key over every pair (x, y) at hits z, w of slots c and e
+template <bool PLAIN>
+__device__ __forceinline__ unsigned long long box_tce(const Dev &d, const P3Box &B, const BoxShape &sh, unsigned z,
+                                                      unsigned w)
+{
+    return box_min2<PLAIN>(d, B, sh, sh.rc, z, sh.re, w);
 }
 
 // the table holding the minima over slots p and q (p != q) and the index of
@@ -2326,10 +2315,9 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
                     de = l == Le ? dl : de;
                 }
                 const unsigned z = B.rank[sh.rc][dc], w = B.rank[sh.re][de];
-                sv[p] = box_get(B, T_AC, x * TS + z) == key && box_get(B, T_BC, y * TS + z) == key &&
-                        box_get(B, T_AE, x * TS + w) == key && box_get(B, T_BE, y * TS + w) == key;
+                sv[p] = box_get(B, T_AC, x * TS + z) == key && box_get(B, T_BC, y * TS + z) == key;
                 sk[p] = key;
-                zw[p] = z * 8 + w;
+                zw[p] = x | (y << 3) | (z << 6) | (w << 9);
             }
         }
     }
@@ -2338,9 +2326,15 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
         for (unsigned bits = __ballot_sync(FULL_MASK, sv[p]); bits; bits &= bits - 1) {
             const unsigned src = __ffs(bits) - 1;
             const unsigned e = __shfl_sync(FULL_MASK, zw[p], src);
-            const unsigned long long m = box_tce<PLAIN>(d, B, sh, e >> 3, e & 7u);
+            const unsigned long long key = __shfl_sync(FULL_MASK, sk[p], src);
+            const unsigned x = e & 7u, y = (e >> 3) & 7u, z = (e >> 6) & 7u, w = e >> 9;
+            // T_ae, T_be, T_ce of the candidate, on demand (each one only if
+            // the ones before hold the key)
+            bool ok = box_min2<PLAIN>(d, B, sh, sh.ra, x, sh.re, w) == key;
+            ok = ok && box_min2<PLAIN>(d, B, sh, sh.rb, y, sh.re, w) == key;
+            ok = ok && box_tce<PLAIN>(d, B, sh, z, w) == key;
             if (lane == src)
-                sv[p] = m == sk[p];
+                sv[p] = ok;
         }
     }
     // survivors in comb order: each finds its rank among the others
@@ -2394,17 +2388,29 @@ __device__ void box_road(const Dev &d, unsigned char *region, unsigned g, unsign
 #pragma unroll
         for (unsigned t = 0; t < 10; ++t)
             total += groups(t);
-        {   // the entries of T_ce that groups of (excluded layer, slot c, slot e) read
-            const unsigned Lc = sh.rc + (sh.rc >= excl), Le = sh.re + (sh.re >= excl);
-            const unsigned fc = fl(Lc), fe = fl(Le);
-            if (fl(excl))
-                for (unsigned bc = fc; bc; bc &= bc - 1)
-                    for (unsigned be = fe; be; be &= be - 1) {
-                        const unsigned z = B.rank[sh.rc][__ffs(bc) - 1], w = B.rank[sh.re][__ffs(be) - 1];
-                        const unsigned long long m = box_tce<PLAIN>(d, B, sh, z, w);
-                        if (lane == 0)
-                            B.T[T_CE][z * TS + w] = m;
-                    }
+        {   // the entries of the tables the passes do not fold (T_ae, T_be,
+            // T_ce) that groups of (excluded layer, slot p, slot e) read
+            if (fl(excl)) {
+                const unsigned Le = sh.re + (sh.re >= excl), fe = fl(Le);
+#pragma unroll
+                for (unsigned q = 0; q < 3; ++q) {
+                    const unsigned sp = q == 0 ? sh.ra : q == 1 ? sh.rb : sh.rc;
+                    const unsigned Lp = sp + (sp >= excl);
+                    for (unsigned bp = fl(Lp); bp; bp &= bp - 1)
+                        for (unsigned be = fe; be; be &= be - 1) {
+                            const unsigned kp = B.rank[sp][__ffs(bp) - 1], w = B.rank[sh.re][__ffs(be) - 1];
+                            const unsigned long long m = box_min2<PLAIN>(d, B, sh, sp, kp, sh.re, w);
+                            if (lane == 0) {
+                                if (q == 2) {
+                                    B.T[T_CE][kp * TS + w] = m;
+                                } else {   // read by box_get as the first pass's entry
+                                    B.H[0][q == 0 ? T_AE - 2 : T_BE - 2][kp * TS + w] = (unsigned)(m >> 32);
+                                    B.L[0][q == 0 ? T_AE - 2 : T_BE - 2][kp * TS + w] = (unsigned)m;
+                                }
+                            }
+                        }
+                }
+            }
             __syncwarp();
         }
         unsigned Se = 1;   // comb stride of the excluded layer
