@@ -1909,13 +1909,16 @@ constexpr size_t P3_WARP_BYTES = (sizeof(P3Flat) + 15) / 16 * 16;
 // coordinate), and the warp works on the box of canonical fits.  The four
 // fitted slots get roles (a, b, c, e); in pass p, lane t = 32 p + lane takes
 // the pair (x, y) = (t mod m_a, t div m_a) of slots a and b and loops over
-// (z, w) of slots c and e.  The six pair tables (minimum key over the fits
-// with the same canonical hits on two slots) come out of that one loop:
+// (z, w) of slots c and e.  Of the six pair tables (minimum key over the
+// fits with the same canonical hits on two slots) that loop makes three:
 //   T_ab[x][y]  the lane's minimum over its own fits
-//   T_ce[z][w]  the minimum over the lanes at (z, w): taken afterwards by a
-//               warp reduction, only where a candidate or a group needs it
 //   T_ac, T_bc  the lane's minimum over w at each z, folded over the lanes
-//   T_ae, T_be  the lane's minimum over z for each w, folded at the end
+// A pair's minimum that holds T_ac and T_bc (about one per road) is then
+// checked against the other three, taken on demand by a warp-wide minimum
+// over the other two slots' hits (box_min2), as are the entries the
+// publish step reads:
+//   T_ae, T_be, T_ce  (folding T_ae and T_be in the loop held sixteen more
+//               registers there and measured slower)
 // The lane minima are folded by 32-bit shared-memory atomics without a
 // return value, each pass into tables of its own: the high words first,
 // then, after the warp has synchronised, the low words of the lanes whose
@@ -1937,7 +1940,8 @@ constexpr unsigned TS = 9;
 struct P3Box {
     unsigned long long T[2][8 * TS];   // T_ab, T_ce: [u * TS + v] (u: the first role's hit); T_ce
                                        // only where needed (box_tce)
-    unsigned H[2][4][8 * TS];          // T_ac, T_bc, T_ae, T_be of pass 0 and pass 1: high words
+    unsigned H[2][4][8 * TS];          // T_ac, T_bc of pass 0 and pass 1: high words; T_ae, T_be:
+                                       // the entries taken on demand for the publish step (pass 0)
     unsigned L[2][4][8 * TS];          // and low words (of the keys with the minimum high word)
     int4 A[4][8];                      // slot j, canonical hit k: chi-square partial sums (x, y,
                                        // z) and comb part (w); slot 0 also carries curvature, phi,
