@@ -460,7 +460,7 @@ def packet_sweep(B, torch, synth, consts, local, sizes_kb=(600, 1200, 2400, 4800
     """End-to-end latency of one batch against its size (kB of input words;
     events shaped as the scaled workload, Sec. IV-C's packet sizes from 600 kB
     up), with the host buffers in three kinds of memory: pageable (the copies
-    are staged by the driver), page-locked (DMA copies in and out), and
+    are staged by the CUDA runtime), page-locked (DMA copies in and out), and
     page-locked memory that the kernels read and write in place (no copies).
     The transfer share is 1 - device time / end-to-end time."""
     cut = load_cut("scaled")
