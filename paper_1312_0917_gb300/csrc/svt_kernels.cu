@@ -791,6 +791,39 @@ __device__ __forceinline__ bool is_multi(const P2Smem &s, unsigned l, unsigned v
     return (s.multi[l][v >> 5] >> (v & 31u)) & 1u;
 }
 
+// coordinate x of a layer's row (eight 16-bit coordinates in a uint4); x is
+// a constant in the unrolled loops below
+__device__ __forceinline__ unsigned row_coord(const uint4 &q, unsigned x)
+{
+    const unsigned w = x < 2 ? q.x : x < 4 ? q.y : x < 6 ? q.z : q.w;
+    return (w >> (16 * (x & 1u))) & 0xFFFFu;
+}
+
+// Hits of one layer of a road (row q) whose coordinate was already in the
+// event's bitmap when the hit set its bit (bit x of `again`): a coordinate
+// of an earlier slot of the same row is a repeat; any other was set by
+// another road and gets the multi bit.  So a coordinate gets the multi bit
+// exactly when two roads hold it.  True when the row repeats a coordinate.
+__device__ __noinline__ bool seen_again(uint32_t *multi, const uint4 &q, unsigned again)
+{
+    bool rep = false;
+#pragma unroll
+    for (unsigned x = 0; x < MAX_HITS; ++x) {
+        if (!((again >> x) & 1u))
+            continue;
+        const unsigned v = row_coord(q, x);
+        bool dup = false;
+#pragma unroll
+        for (unsigned y = 0; y < x; ++y)
+            dup = dup || row_coord(q, y) == v;
+        if (dup)
+            rep = true;
+        else
+            atomicOr(&multi[v >> 5], 1u << (v & 31u));
+    }
+    return rep;
+}
+
 // Roads r and t of the event: the layers on which they hold a common
 // coordinate and the hits involved; with three or more such layers, the
 // shared hits of both roads are marked.  Only coordinates present in two
@@ -898,20 +931,15 @@ __device__ void p2_event(const Dev &d, unsigned e, unsigned r0, unsigned nr, uns
     for (unsigned i = threadIdx.x; i < nr * N_LAYERS; i += BLOCK) {
         const unsigned k = i / N_LAYERS, l = i - k * N_LAYERS;
         const unsigned n = (s.rec[k].pk >> (4 * l)) & 15u;
-        bool rep = false;
-        for (unsigned x = 0; x < n; ++x) {
-            const unsigned v = s.coord[k][l * 8 + x];
-            bool first = true;
-            for (unsigned y = 0; y < x; ++y)
-                first = first && s.coord[k][l * 8 + y] != v;
-            if (first) {
-                const unsigned bit = 1u << (v & 31u);
-                if (atomicOr(&s.seen[l][v >> 5], bit) & bit)
-                    atomicOr(&s.multi[l][v >> 5], bit);
-            }
-            rep = rep || !first;
+        const uint4 q = *reinterpret_cast<const uint4 *>(&s.coord[k][l * 8]);
+        unsigned again = 0;   // bit x: hit x found its bit set
+#pragma unroll
+        for (unsigned x = 0; x < MAX_HITS; ++x) {
+            const unsigned v = row_coord(q, x), bit = 1u << (v & 31u);
+            if (x < n && (atomicOr(&s.seen[l][v >> 5], bit) & bit))
+                again |= 1u << x;
         }
-        if (rep)
+        if (again && seen_again(s.multi[l], q, again))
             s.rep[k] = 1;
     }
     __syncthreads();
@@ -999,14 +1027,6 @@ constexpr size_t P2W_BYTES = (sizeof(P2Warp) + 15) / 16 * 16;
 // signature bit of a coordinate in a 32-bit signature
 __device__ __forceinline__ unsigned sig_bit32(unsigned v) { return (v * 0x9E3779B1u) >> 27; }
 
-// coordinate x of a layer's row (eight 16-bit coordinates in a uint4); x is
-// a constant in the unrolled loops below
-__device__ __forceinline__ unsigned row_coord(const uint4 &q, unsigned x)
-{
-    const unsigned w = x < 2 ? q.x : x < 4 ? q.y : x < 6 ? q.z : q.w;
-    return (w >> (16 * (x & 1u))) & 0xFFFFu;
-}
-
 // Hits of road g that road h holds too (bit 8 l + x), when they hold common
 // coordinates on three layers or more; 0 otherwise.  pg, ph: their records'
 // pk words.
@@ -1039,8 +1059,9 @@ __device__ unsigned long long pair_marks(const Dev &d, unsigned g, unsigned h, u
 // with state `w`; lane i owns roads i and i + 32.  The same steps as
 // p2_event: coordinates present in two roads (bitmaps), signatures of those
 // per road and layer, pairs whose signatures meet on >= 3 layers tested
-// exactly.  A lane tests its road against every other road and marks only
-// its own road's hits, so each pair is tested from both sides.
+// exactly.  A lane tests its eligible road against every other eligible road
+// (a pair whose signatures meet on >= 3 layers has two) and marks only its
+// own road's hits, so each pair is tested from both sides.
 __device__ void p2_warp(const Dev &d, unsigned r0, unsigned nr, P2Warp &w, unsigned long long &n_comb)
 {
     const unsigned lane = lane_id();
@@ -1112,11 +1133,14 @@ __device__ void p2_warp(const Dev &d, unsigned r0, unsigned nr, P2Warp &w, unsig
         elig |= layers >= 3 ? 1u << h : 0u;
     }
     __syncwarp();
-    // every other road t against the lane's eligible roads (their signatures
-    // meet on >= 3 layers first)
+    // the other eligible roads t against the lane's eligible roads (their
+    // signatures meet on >= 3 layers first)
     unsigned long long xm[2] = {0ull, 0ull};
-    if (__any_sync(FULL_MASK, elig != 0u)) {
-        for (unsigned t = 0; t < nr; ++t) {
+    unsigned long long em = ((unsigned long long)__ballot_sync(FULL_MASK, (elig >> 1) & 1u) << 32) |
+                            __ballot_sync(FULL_MASK, elig & 1u);
+    if (__popcll(em) >= 2) {
+        for (; em; em &= em - 1) {
+            const unsigned t = (unsigned)__ffsll((long long)em) - 1;
 #pragma unroll
             for (unsigned h = 0; h < 2; ++h) {
                 const unsigned k = lane + 32 * h;
