@@ -524,7 +524,7 @@ __device__ __forceinline__ unsigned long long decode_batch(const Dev &d, P1Warp 
         const unsigned start = q.pos[off + lane], ev = q.ev[off + lane], rie = q.rie[off + lane];
         g = q.g[off + lane];
         uint16_t *row = q.row[lane];
-        unsigned long long cnt8 = 0;   // hits so far, layer l in bits 8 l .. 8 l + 7
+        unsigned cnt4 = 0;   // hits so far, layer l in bits 4 l .. 4 l + 3 (at most MAX_HITS)
         uint32_t hdr = 0, cw = 0, pw = 0;
         bool ee = false;
         for (unsigned k0 = 0; k0 < MAX_ROAD_WORDS && !done && err == ~0ull; k0 += 8) {
@@ -558,12 +558,13 @@ __device__ __forceinline__ unsigned long long decode_batch(const Dev &d, P1Warp 
                 } else {
                     bad = type > 4;
                     if (!bad) {
-                        const unsigned r = (unsigned)(cnt8 >> (8 * type)) & 0xFFu;
-                        if (r >= (unsigned)MAX_HITS)
+                        const unsigned r = (cnt4 >> (4 * type)) & 15u;
+                        if (r >= (unsigned)MAX_HITS) {
                             err = (p << 8) | RANK_LIMIT;
-                        else
+                        } else {
                             row[type * 8 + r] = (uint16_t)(w & 0xFFFu);
-                        cnt8 += 1ull << (8 * type);
+                            cnt4 += 1u << (4 * type);
+                        }
                     }
                 }
                 if (bad)
@@ -575,10 +576,7 @@ __device__ __forceinline__ unsigned long long decode_batch(const Dev &d, P1Warp 
             }
         }
         if (done && g < d.max_roads) {   // a complete road: its record
-            unsigned pk = 0;
-#pragma unroll
-            for (unsigned l = 0; l < N_LAYERS; ++l)
-                pk |= min((unsigned)(cnt8 >> (8 * l)) & 0xFFu, (unsigned)MAX_HITS) << (4 * l);
+            const unsigned pk = cnt4;   // the hit counts, four bits per layer
             const unsigned wedge = min(hdr & 15u, 11u), barrel = min((hdr >> 4) & 7u, 5u);
             const unsigned excl = min((hdr >> 7) & 7u, 4u);
             RoadRec r;
