@@ -376,11 +376,12 @@ enum { Q_P0 = 0, Q_P1, Q_P2, Q_BIG, Q_SMALL, Q_P4, Q_P5, Q_CNT, Q_CSC, Q_FIT, Q_
 // b * WARPS + w.  P0 counts each span's EE and EP words and the EP words after
 // its last EE, and checks every word's fields.  P1 gives each warp the counts
 // of the spans before its own (every CTA sums them itself, no CTA scans for
-// the others) and decodes the roads whose header lies in the warp's span, a
-// window at a time: lane i holds word i of the window, and ballots over the
-// EP, EE and type bits give each word its road, its position in the road,
-// its event, its road's place in the event and its hit's rank in its layer.
-// A warp follows its last road past the end of its span.
+// the others) and decodes the roads whose header lies in the warp's span.
+// Ballots over the EP and EE bits of a window (lane i: word i) find the roads
+// that start in it, with their road index, event and place in the event;
+// each road is then walked by one lane from its header to its EP word,
+// which checks the grammar and ranks each hit in its layer.  A warp follows
+// its last road past the end of its span.
 // ---------------------------------------------------------------------------
 
 constexpr unsigned WIN = 32;               // words per window: one per lane
