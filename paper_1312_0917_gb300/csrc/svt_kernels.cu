@@ -2801,6 +2801,7 @@ constexpr unsigned P5_PER_THREAD = 8;
 constexpr unsigned P5_ROADS = BLOCK * P5_PER_THREAD;
 constexpr unsigned P5_GROUP = P5_ROADS / ROAD_CHUNK;   // chunks per pass
 static_assert(P5_ROADS % ROAD_CHUNK == 0, "whole chunks per pass");
+static_assert(P5_GROUP <= 32, "a lane per chunk of a pass");
 
 constexpr unsigned P5_STAGE = 448;   // roads whose records and coordinates are staged at once
 
@@ -2886,13 +2887,15 @@ __device__ void p5_phase(const Dev &d, unsigned char *smem)
             s.first[threadIdx.x * P5_PER_THREAD + k] = run;
             run += (unsigned)(cnt8 >> (8 * k)) & 0xFFu;
         }
-        if (threadIdx.x == 0) {
-            s.first[P5_ROADS] = (unsigned)tot;
-            unsigned long long chk = 0;   // the counts and the chunk totals agree
-            for (unsigned k = 0; k < P5_GROUP && c + k < n_chunks; ++k)
-                chk += ldcg(d.rchunk_sum + c + k);
-            if (chk != tot)
-                raise_flag(d, FLAG_INTERNAL);
+        if (warp_id() == 0) {   // the counts and the chunk totals agree (a lane per chunk)
+            const unsigned k = lane_id();
+            const unsigned long long chk =
+                warp_sum(k < P5_GROUP && c + k < n_chunks ? ldcg(d.rchunk_sum + c + k) : 0ull);
+            if (k == 0) {
+                s.first[P5_ROADS] = (unsigned)tot;
+                if (chk != tot)
+                    raise_flag(d, FLAG_INTERNAL);
+            }
         }
         __syncthreads();
         const unsigned long long a = lo > pre ? lo : pre, b = hi < pre + tot ? hi : pre + tot;
@@ -2904,16 +2907,26 @@ __device__ void p5_phase(const Dev &d, unsigned char *smem)
             const unsigned r_lo = p5_road(s.first, 0, P5_ROADS, ka), r_hi = p5_road(s.first, 0, P5_ROADS, kb);
             for (unsigned rb = r_lo; rb <= r_hi; rb += P5_STAGE) {
                 const unsigned re = min(rb + P5_STAGE, r_hi + 1), nr = re - rb;
+                // the thread's first survivor of the stage: its key is loaded
+                // together with the stage
+                const unsigned k0 = max(ka, s.first[rb]), k1 = min(kb + 1, s.first[re]);
+                const unsigned kf = k0 + threadIdx.x;
+                unsigned rf = 0;
+                unsigned long long keyf = 0;
+                if (kf < k1) {
+                    rf = p5_road(s.first, rb, re, kf);
+                    keyf = ldcg(d.surv_pool + surv_at(d, g0 + rf, kf - s.first[rf]));
+                }
                 for (unsigned j = threadIdx.x; j < nr; j += BLOCK)
                     s.rec[j] = ldcg(d.roads + g0 + rb + j);
                 const uint4 *rows = reinterpret_cast<const uint4 *>(d.coords + (size_t)(g0 + rb) * 40);
                 for (unsigned j = threadIdx.x; j < nr * N_LAYERS; j += BLOCK)
                     s.row[j] = ldcg(rows + j);
                 __syncthreads();
-                const unsigned k0 = max(ka, s.first[rb]), k1 = min(kb + 1, s.first[re]);
-                for (unsigned k = k0 + threadIdx.x; k < k1; k += BLOCK) {
-                    const unsigned r = p5_road(s.first, rb, re, k), g = g0 + r;
-                    const unsigned long long key = ldcg(d.surv_pool + surv_at(d, g, k - s.first[r]));
+                for (unsigned k = kf; k < k1; k += BLOCK) {
+                    const unsigned r = k == kf ? rf : p5_road(s.first, rb, re, k), g = g0 + r;
+                    const unsigned long long key =
+                        k == kf ? keyf : ldcg(d.surv_pool + surv_at(d, g, k - s.first[r]));
                     uint4 rw[N_LAYERS];
 #pragma unroll
                     for (unsigned l = 0; l < N_LAYERS; ++l)
